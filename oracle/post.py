@@ -1,0 +1,29 @@
+"""Post-processing of rho*: H* and the von Neumann entropy.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+* ``mean_force``: -(1/beta) ln(rho*) through the eigendecomposition of rho*
+  (Sec. 3.2: transform eigenvalues instead of taking a matrix logarithm). With
+  ``ln_z_star`` given it returns the absolute H* = -(1/beta) ln(Z* rho*) (eq. 6-7);
+  without it, H* up to the additive constant -(1/beta) ln Z*.
+* ``entropy``: S = -tr(rho ln rho) = -sum p ln p with 0 ln 0 = 0 (Sec. 5.3.1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def mean_force(rho: np.ndarray, beta: float, ln_z_star: float | None = None) -> np.ndarray:
+    w, u = np.linalg.eigh(0.5 * (rho + rho.T))
+    if np.any(w <= 0):
+        raise ValueError("rho* is not positive definite; ln is undefined")
+    lw = np.log(w)
+    if ln_z_star is not None:
+        lw = lw + ln_z_star
+    return -(u * lw) @ u.T / beta
+
+
+def entropy(rho: np.ndarray) -> float:
+    w = np.linalg.eigvalsh(0.5 * (rho + rho.T))
+    w = w[w > 0]
+    return float(-np.sum(w * np.log(w)))
