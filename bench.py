@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the estimator's hot path: rho*_s solves/s on GB300.
+
+Workload (one "step" = one solve = one rdm_estimate call over the whole hot path):
+long-range transverse-field Ising model H = sum_{i<j} |i-j|^-1.5 Z_i Z_j + g sum X_i,
+N = 22 spins (D = 2^22), N_s = 2 (d_s = 4), lambda = 1, g swept over 16 values in
+[0.2, 2.0] (step i uses g-index i mod 16), beta = 1, n_v = 32 normalised Gaussian
+bath vectors (block of 128 float32 columns), k = 60 Lanczos steps, two passes.
+Synthetic, seeded inputs; every Krylov block (2.1 GB) is larger than the 129 MB L2,
+so no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the CPU oracle instead.
+Multi-GPU (torchrun): each rank runs its own solves (independent g values, no
+data-path collective), value = all ranks' solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "rho* solves/s and SpMM GB/s vs roofline; p50/p99 latency, vs plain FP64 form"
+WORKLOAD = "lr_tfim_N22_Ns2_nv32_k60_beta1_fp32"
+N_G = 16
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=16)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 one-vector form")
+    return p.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle sample (CPU)
+
+_ORACLE_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import lanczos, spin_ops
+c = W.config_c2(0)
+t0 = time.perf_counter()
+ham = spin_ops.TensorHamiltonian(c["spec"])
+ham.diagonal()
+t_setup = time.perf_counter() - t0
+est = lanczos.Estimator(c["spec"], apply_h=ham, hnorm=ham.norm_bound())
+v = est.starting_block(0, c["seed"], c["dist"])
+steps = {steps}
+t0 = time.perf_counter()
+for j, q, a, b in lanczos.block_lanczos(ham, v, steps, est.hnorm):
+    pass
+t_steps = time.perf_counter() - t0
+print(json.dumps(dict(t_setup=t_setup, t_step=t_steps / steps, steps=steps)))
+"""
+
+
+def oracle_sample(steps: int) -> dict:
+    """Runs `steps` Lanczos steps of one bath vector of the workload with the oracle,
+    single-threaded, in a fresh interpreter (no CUDA in it)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _ORACLE_SAMPLE.format(root=ROOT, steps=steps)],
+                       capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_solves_per_s(sample: dict) -> float:
+    """One solve = n_v vectors x (k steps of pass 1 + k steps of the Gram-form rerun)."""
+    c = W.config_c2(0)
+    per_solve = sample["t_setup"] + sample["t_step"] * c["n_v"] * 2 * c["k"]
+    return 1.0 / per_solve
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(a.warmup):
+        oracle_sample(1)
+    t0 = time.perf_counter()
+    samples = [oracle_sample(2) for _ in range(a.steps)]
+    wall = time.perf_counter() - t0
+    rates = [oracle_solves_per_s(s) for s in samples]
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: 2 Lanczos steps of bath vector 0 at full size "
+                                   "(D=2^22, 4 columns, float64 NumPy), scaled to 32 vectors x "
+                                   "2 x 60 steps per solve", "wall_s": wall},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU clocks
+
+class Clocks:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and self.uuid not in parts[0]:
+                    continue
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+
+    cpu_sample = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu_sample = oracle_sample(5)  # before any CUDA work in this process
+
+    from paper_2204_08147_gb300 import rdm
+    ctx = rdm.Context(local)
+    cfgs = [W.config_c2(g) for g in range(N_G)]
+    hams = [rdm.Hamiltonian(ctx, c["spec"]) for c in cfgs]
+    c0 = cfgs[0]
+
+    def solve(i):
+        c = cfgs[i % N_G]
+        return hams[i % N_G].estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32",
+                                      dist=c["dist"])
+
+    base = rank * (a.warmup + a.steps)
+    for i in range(a.warmup):
+        solve(base + i)
+    ctx.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "")) or None
+    clocks = Clocks(uuid)
+    # The context runs on torch's current stream, so these events bracket its work.
+    ctx.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    lat = []
+    for i in range(a.steps):
+        t0 = time.perf_counter()
+        solve(base + a.warmup + i)
+        lat.append(time.perf_counter() - t0)
+    ev1.record()
+    torch.cuda.synchronize()
+    ctx.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    stats = ctx.profile_stats()
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_solves = a.steps * world
+    value = total_solves / (ms / 1000.0)
+
+    # End to end through the public API from host buffers: build the Hamiltonian
+    # from the host model (descriptor upload), estimate, read the result back.
+    e2e_steps = max(2, min(a.steps, 4))
+    if dist:
+        dist.barrier()
+    ctx.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for i in range(e2e_steps):
+        c = cfgs[(base + i) % N_G]
+        h = rdm.Hamiltonian(ctx, c["spec"])
+        info = h.info()
+        out = h.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32", dist=c["dist"])
+        h.close()
+        h2d += out["h2d_bytes"] + 24 * info["n_flip"] + 16 * info["n_diag"]
+        d2h += out["d2h_bytes"]
+    ctx.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = e2e_steps * world / e2e_s
+
+    # Plain FP64 form: the same method one bath vector at a time (block width d_s).
+    plain = None
+    if rank == 0 and not a.no_plain:
+        t0 = time.perf_counter()
+        c = cfgs[0]
+        for l_ in range(c["n_v"]):
+            hams[0].estimate(c["betas"], 1, c["k"], c["seed"] + 7919 * l_, precision="fp64", dist=c["dist"])
+        plain = {"value": 1.0 / (time.perf_counter() - t0), "unit": "solves/s",
+                 "form": "float64, one bath vector per call (32 calls = one solve), no batching"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    sp = [stats["spmm_pass1"], stats["spmm_pass2"]]
+    sp_ms = sum(s["ms"] for s in sp)
+    sp_launch = sum(s["launches"] for s in sp)
+    sp_bytes = sum(s["bytes"] for s in sp)
+    dev_ms_total = sum(s["ms"] for s in stats.values())
+    achieved = (sp_bytes / sp_launch) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None
+    n_flip = hams[0].info()["n_flip"]
+    blk = (1 << 22) * 128 * 4
+    roof = {"kernel": "k_spmm (pass 1 + pass 2)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": _traffic_from_profiles(), "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": sp_bytes / max(1, sp_launch),
+            "avg_launch_ms": sp_ms / max(1, sp_launch),
+            "operand_gbs": ((n_flip + 2) * blk) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None,
+            "share_of_timed_kernels": sp_ms / dev_ms_total if dev_ms_total else None}
+    launches = sum(s["launches"] for s in stats.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_sites": 22, "n_sys": 2, "n_v": 32, "k": 60,
+                   "beta": [1.0], "g_values": 16, "block_columns": 128, "l2": "inputs larger than L2",
+                   "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99))},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps},
+        "gpu_launches": launches,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["launches"]},
+        "roofline": roof,
+        "plain_fp64": plain,
+    }
+    if cpu_sample is not None:
+        line["cpu_baseline"] = {"value": oracle_solves_per_s(cpu_sample), "unit": "solves/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "5 Lanczos steps of bath vector 0 at full size (D=2^22, "
+                                          "float64 NumPy, 1 thread), scaled to 32 vectors x 2 x 60 "
+                                          "steps per solve"}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _traffic_from_profiles():
+    """DRAM bytes per k_spmm launch from the committed ncu summary, if it was taken
+    on the current kernel source (else null)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_spmm_lr_tfim_N22.md")
+    src = os.path.join(ROOT, "paper_2204_08147_gb300", "csrc", "kernels.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                val, _, tag = line.split(":", 1)[1].strip().partition(" kernels.cu sha256 ")
+                return float(val) if tag.strip() == h else None
+    except Exception:
+        return None
+    return None
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

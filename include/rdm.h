@@ -1,0 +1,251 @@
+/*
+ * rdm.h -- C ABI of the GB300 library for the equilibrium-reduced density matrix
+ * rho*_s = tr_b(exp(-beta H_t)) / Z_t and the mean-force Hamiltonian
+ * H* = -ln(rho*_s)/beta of strongly coupled spin systems, computed with the
+ * typicality + block-Lanczos estimator of Chen & Cheng, "Numerical computation of
+ * the equilibrium-reduced density matrix for strongly coupled open quantum
+ * systems" (arXiv:2204.08147).
+ *
+ * Conventions (Sec. 2.2, eq. Ht):
+ *   - spins 1/2, sigma = Pauli matrices; sites 0..N-1, site 0 is the leftmost
+ *     Kronecker factor, i.e. site q is bit (N-1-q) of a basis-state index s, and a
+ *     0 bit is spin up (Z = +1);
+ *   - the system is sites 0..N_s-1 (the top N_s bits of s), the bath the rest:
+ *     s = i*d_b + b with system index i < d_s = 2^N_s and bath index b < d_b;
+ *   - couplings are given once per unordered pair a < b.
+ *
+ * Every function returns an rdm_status; no C++ exception crosses this boundary.
+ * On failure, rdm_last_error() returns a thread-local message describing it.
+ * All host arrays are owned by the caller. Handles and the device memory the
+ * library allocates for them are owned by the library.
+ */
+#ifndef RDM_H
+#define RDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rdm_ctx rdm_ctx;
+typedef struct rdm_ham rdm_ham;
+
+typedef enum {
+  RDM_OK = 0,
+  RDM_EINVAL = -1,   /* invalid argument or unsupported size */
+  RDM_ENOMEM = -2,   /* device or host memory exhausted, or workspace too small */
+  RDM_ECUDA = -3,    /* a CUDA runtime call failed */
+  RDM_ENUMERIC = -4, /* a non-finite Lanczos coefficient or Gram entry */
+  RDM_ETIMEOUT = -5, /* rdm_wait gave up before the request finished */
+  RDM_EBUSY = -6,    /* request still pending (rdm_poll) */
+  RDM_ENOTPD = -7,   /* rho is not positive definite: ln(rho) undefined */
+  RDM_ENOTFOUND = -8 /* unknown request ticket */
+} rdm_status;
+
+/* Arithmetic of the Lanczos vectors and the matrix-free SpMM. Recurrence
+ * scalars, the eigendecomposition of T, exp(-beta T/2), the Gram and ln Z are
+ * float64 in both modes. */
+enum { RDM_FP64 = 0, RDM_FP32 = 1 };
+
+/* Distribution of the bath vectors |v_l> (Sec. 3.1, eq. trace_est), drawn from a
+ * counter-based generator: the n-th output of SplitMix64 (Steele, Lea & Flood
+ * 2014) seeded with `seed`, mix(seed + n*0x9E3779B97F4A7C15), at counter
+ * n = ((l << 40) | b) + 1 for element b of vector l (Gaussian: counters for 2b
+ * and 2b+1).
+ *   RDM_RADEMACHER: +-1/sqrt(d_b), sign = top bit of the draw;
+ *   RDM_GAUSS:      Box-Muller cos(2 pi u2) sqrt(-2 ln u1), u = ((draw>>11)+0.5)/2^53,
+ *                   then normalised to unit Euclidean norm;
+ *   RDM_BASIS:      v_l = e_l; with n_v = d_b the average is the exact partial
+ *                   trace (Sec. 2.1), used for exactness tests. */
+enum { RDM_RADEMACHER = 0, RDM_GAUSS = 1, RDM_BASIS = 2 };
+
+/* Which estimator form fills rdm_result.rho (the other fills rho_other).
+ *   RDM_GRAM:       psi_l = Q_l exp(-beta (T_l - E0)/2) E1, G_l = psi_l^T psi_l
+ *                   (the function-application form of the sqrt(rho) construction
+ *                   of Sec. 2.1);
+ *   RDM_QUADRATURE: G_l = E1^T exp(-beta (T_l - E0)) E1 (eq. fT, trB_est).
+ * Both are normalised as eq. rho_est. They agree while Q_l^T Q_l = I. */
+enum { RDM_GRAM = 0, RDM_QUADRATURE = 1 };
+
+/* rdm_result.flags bits */
+#define RDM_FLAG_DEFLATED 1u   /* a Lanczos column was dropped (Krylov breakdown) */
+#define RDM_FLAG_PADDED 2u     /* n_v was padded with zero vectors for alignment */
+
+/* A real spin-1/2 Hamiltonian (eq. Ht):
+ *   H = sum_{a<b} s_ab (jx[a,b] X_a X_b + jy[a,b] Y_a Y_b + jz[a,b] Z_a Z_b)
+ *     + sum_q (hz[q] Z_q + gx[q] X_q),
+ * s_ab = lambda_sb if exactly one of a, b is a system site, else 1 (the
+ * epsilon-scaled coupling of Sec. 5.5). jx, jy, jz are n_sites*n_sites row-major
+ * arrays of which entries [a*n_sites + b] with a < b are read; hz, gx have
+ * n_sites entries (hz is the paper's h/2). Any pointer may be NULL (all zero).
+ * Limits: 1 <= n_sites <= 30, 0 <= n_sys <= 2, n_sys < n_sites. */
+typedef struct {
+  int n_sites;
+  int n_sys;
+  const double* jx;
+  const double* jy;
+  const double* jz;
+  const double* hz;
+  const double* gx;
+  double lambda_sb;
+} rdm_model;
+
+typedef struct {
+  int precision; /* RDM_FP64 | RDM_FP32 */
+  int vec_dist;  /* RDM_RADEMACHER | RDM_GAUSS | RDM_BASIS */
+  int form;      /* RDM_GRAM | RDM_QUADRATURE */
+  int reserved;  /* must be 0 */
+} rdm_opts;
+
+/* Outputs of rdm_estimate; every pointer is a caller-owned host array. rho is
+ * required, the rest may be NULL. Per-vector arrays are indexed [beta][l][i][j]
+ * or [l][step][i][j], row-major, with d_s = 2^n_sys. */
+typedef struct {
+  double* rho;       /* n_beta*d_s*d_s: rho*_s(beta) in the chosen form (eq. rho_est) */
+  double* ln_z;      /* n_beta: ln Z_t estimate, ln(d_b tr(sum_l G_l)/n_v) - beta E0 */
+  double* rho_other; /* n_beta*d_s*d_s: rho* in the other form (diagnostic) */
+  double* gram_l;    /* n_beta*n_v*d_s*d_s: un-normalised Gram-form G_l */
+  double* quad_l;    /* n_beta*n_v*d_s*d_s: un-normalised quadrature-form G_l */
+  double* t_a;       /* n_v*k*d_s*d_s: A_j of Algorithm 1 */
+  double* t_b;       /* n_v*k*d_s*d_s: B_j of Algorithm 1 (upper triangular) */
+  double e0;         /* out: the shift E0 = min_l lambda_min(T_l) (Sec. 3.2) */
+  uint32_t flags;    /* out: RDM_FLAG_* */
+  uint64_t h2d_bytes; /* out: host->device bytes this call copied (coefficients) */
+  uint64_t d2h_bytes; /* out: device->host bytes this call copied (T, Gram, flags) */
+} rdm_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`. `stream` is a cudaStream_t owned by
+ * the caller (NULL = the context creates and owns its own stream). Device work of
+ * every call on this context is ordered on that stream. */
+rdm_status rdm_create(rdm_ctx** out, int device, void* stream);
+void rdm_destroy(rdm_ctx* ctx);
+
+/* Attaches caller-owned device memory (e.g. a framework tensor) that rdm_estimate
+ * carves its scratch from instead of allocating; NULL/0 detaches. The memory must
+ * stay valid and unused by others while calls on this context run. */
+rdm_status rdm_set_workspace(rdm_ctx* ctx, void* device_ptr, size_t bytes);
+
+/* Bytes of device scratch rdm_estimate needs for these sizes (3 Krylov blocks,
+ * the psi accumulators of one beta chunk, reduction partials, coefficients). */
+rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v, int k,
+                              const rdm_opts* opts, size_t* bytes);
+
+/* Waits for all device work issued on the context's stream. */
+rdm_status rdm_synchronize(rdm_ctx* ctx);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* rdm_last_error(void);
+
+/* Per-kernel statistics of the work issued through a context: launches, device
+ * time (CUDA events recorded on the launching stream around each launch of the
+ * timed kernels) and algorithmic bytes (the compulsory device-memory traffic of
+ * each launch: blocks read and written once). */
+typedef struct {
+  char name[32];
+  uint64_t launches;
+  double ms;     /* summed event time; 0 for kernels that are only counted */
+  double bytes;  /* summed algorithmic bytes */
+} rdm_kernel_stat;
+
+/* enable != 0 starts recording (and clears earlier statistics); 0 stops. */
+rdm_status rdm_profile(rdm_ctx* ctx, int enable);
+/* Copies up to `max` entries into out; *n = number of kernel kinds recorded. */
+rdm_status rdm_profile_stats(rdm_ctx* ctx, rdm_kernel_stat* out, int max, int* n);
+
+/* ---------------------------------------------------------------- model */
+
+/* Compiles a model into compact term descriptors (flip masks with their
+ * aligned/anti-aligned coefficients, Z-parity masks, fields) and uploads them to
+ * the context's device. The handle keeps a pointer to ctx; destroy it first. */
+rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_ham** out);
+void rdm_destroy_hamiltonian(rdm_ham* ham);
+
+/* Sizes and the bound ||H||_2 <= sum of |term coefficients| used to scale the
+ * Lanczos breakdown tolerance. Any output pointer may be NULL. */
+rdm_status rdm_hamiltonian_info(const rdm_ham* ham, int* n_sites, int* n_sys,
+                                int* n_flip_terms, int* n_diag_terms, double* norm_bound);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* The estimator (eq. trB_est with eq. rho_est and the E0 shift of Sec. 3.2):
+ * n_v bath vectors, each running k steps of block Lanczos (Algorithm 1) with
+ * block size d_s from V_l = I_s (x) |v_l>, all n_v recurrences batched into one
+ * matrix-free block SpMM; then exp(-beta (T_l - E0)/2) for every beta of the grid
+ * and the bath-traced d_s x d_s Gram, averaged over l and trace-normalised.
+ * betas: n_beta >= 1 values >= 0 (host). 1 <= n_v <= 4096, 1 <= k <= 512.
+ * Blocking: returns when the results are in `out` (host). */
+rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta, int n_v, int k,
+                        uint64_t seed, const rdm_opts* opts, rdm_result* out);
+
+/* Y = H X for a caller-owned device block of n_cols columns stored state-major,
+ * vector-minor (element (s, c) at s*n_cols + c), float64 (RDM_FP64) or float32
+ * (RDM_FP32). n_cols must be 2^m times 4 (FP32) or 2 (FP64), at most 32 (FP32) or
+ * 16 (FP64). X and Y must not overlap. Asynchronous on the context's stream. This
+ * is the SpMM of the hot path (the matrix-vector products of Sec. 2.4), exposed
+ * for verification. */
+rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const void* x, void* y,
+                                 int n_cols);
+
+/* Fills a caller-owned device block (state-major, d_s*n_v columns, same column
+ * rules as rdm_apply_hamiltonian) with the starting block V = [I_s (x) |v_l>]_l:
+ * element (s, l*d_s + i) = [s >> N_b == i] * v_l[s & (d_b - 1)] (Sec. 3.1).
+ * Asynchronous on the context's stream. */
+rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, uint64_t seed,
+                              int vec_dist, void* x);
+
+/* ---------------------------------------------------------------- post-processing
+ * Host float64, no device work. rho is d_s x d_s row-major, symmetric. */
+
+/* H_out = -(1/beta) ln(rho) through the eigendecomposition of rho (Sec. 3.2 end:
+ * transform eigenvalues, no matrix logarithm): H* up to the additive constant
+ * -(1/beta) ln Z*. RDM_ENOTPD if an eigenvalue of rho is <= 0. 1 <= d_s <= 64,
+ * beta > 0. */
+rdm_status rdm_mean_force(const double* rho, int d_s, double beta, double* h_out);
+
+/* S = -tr(rho ln rho) = -sum_i p_i ln p_i with 0 ln 0 = 0 (Sec. 5.3.1). */
+rdm_status rdm_entropy(const double* rho, int d_s, double* s_out);
+
+/* Eigendecomposition of a dense symmetric n x n matrix (row-major a), used by
+ * the small dense step of the estimator: w ascending (n), v (n*n, row-major,
+ * column j = eigenvector j; NULL for values only). Host float64. */
+rdm_status rdm_symmetric_eig(int n, const double* a, double* w, double* v);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop on the context: requests are queued, admitted while their
+ * device footprint fits the context's budget, and run concurrently (each on its
+ * own stream), so requests that arrive while others run overlap with them. The
+ * result arrays of a request must stay valid until rdm_poll/rdm_wait reports
+ * completion. */
+
+/* hbm_budget_bytes: device bytes the loop may hold for requests at once;
+ * max_inflight: how many requests may run concurrently (>= 1). */
+rdm_status rdm_serve_start(rdm_ctx* ctx, size_t hbm_budget_bytes, int max_inflight);
+rdm_status rdm_serve_stop(rdm_ctx* ctx);
+
+/* Queues a copy of the request (the model is copied; betas are copied) and
+ * returns a ticket. `out` is written when the request completes. */
+rdm_status rdm_submit(rdm_ctx* ctx, const rdm_model* model, const double* betas, int n_beta,
+                      int n_v, int k, uint64_t seed, const rdm_opts* opts, rdm_result* out,
+                      uint64_t* ticket);
+
+/* RDM_OK with *status_out the request's own status when it has finished,
+ * RDM_EBUSY while pending, RDM_ENOTFOUND for an unknown ticket. Finished tickets
+ * stay queryable until rdm_serve_stop. */
+rdm_status rdm_poll(rdm_ctx* ctx, uint64_t ticket, rdm_status* status_out);
+
+/* As rdm_poll but waits up to timeout_ms (< 0: forever); RDM_ETIMEOUT on expiry. */
+rdm_status rdm_wait(rdm_ctx* ctx, uint64_t ticket, int timeout_ms, rdm_status* status_out);
+
+/* Wall-clock seconds from submission to completion of a finished ticket and the
+ * part of it spent queued before admission. RDM_EBUSY while pending. */
+rdm_status rdm_request_times(rdm_ctx* ctx, uint64_t ticket, double* latency_s, double* queued_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDM_H */

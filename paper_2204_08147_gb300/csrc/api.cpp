@@ -1,0 +1,801 @@
+// Host side of the C ABI: contexts, Hamiltonian descriptors, workspace planning and
+// the orchestration of the estimator (Algorithm 1 twice, the small dense step in
+// between, the Gram at the end).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rdm_api_internal.h"
+
+namespace rdm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+bool sym_eig(int n, const double* a, double* w, double* vt);
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RDM_ECUDA;                                                              \
+    }                                                                                \
+  } while (0)
+
+// ---------------------------------------------------------------- descriptors
+
+static uint32_t site_bit(int n, int q) { return 1u << (n - 1 - q); }
+
+rdm_status compile_model(const rdm_model* m, HostModel* out) {
+  if (!m) {
+    set_error("model is NULL");
+    return RDM_EINVAL;
+  }
+  const int n = m->n_sites;
+  if (n < 1 || n > 30 || m->n_sys < 0 || m->n_sys > 2 || m->n_sys >= n) {
+    set_error("unsupported sizes: n_sites=%d n_sys=%d (need 1<=n_sites<=30, 0<=n_sys<=2, n_sys<n_sites)",
+              n, m->n_sys);
+    return RDM_EINVAL;
+  }
+  if (!std::isfinite(m->lambda_sb)) {
+    set_error("lambda_sb is not finite");
+    return RDM_EINVAL;
+  }
+  HostModel h;
+  h.n = n;
+  h.ns = m->n_sys;
+  h.lambda = m->lambda_sb;
+  auto at = [&](const double* t, int a, int b) { return t ? t[(size_t)a * n + b] : 0.0; };
+  double bound = 0.0;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      const bool sb = (a < h.ns) != (b < h.ns);
+      const double s = sb ? m->lambda_sb : 1.0;
+      const double jx = at(m->jx, a, b), jy = at(m->jy, a, b), jz = at(m->jz, a, b);
+      if (!std::isfinite(jx) || !std::isfinite(jy) || !std::isfinite(jz)) {
+        set_error("non-finite coupling at (%d,%d)", a, b);
+        return RDM_EINVAL;
+      }
+      bound += std::fabs(s * jx) + std::fabs(s * jy) + std::fabs(s * jz);
+      const uint32_t mask = site_bit(n, a) | site_bit(n, b);
+      if (jx != 0.0 || jy != 0.0) {
+        FlipTerm t{mask, 0u, s * (jx + jy), s * (jx - jy)};
+        if (t.c_odd != 0.0 || t.c_even != 0.0) h.flips.push_back(t);
+      }
+      if (jz != 0.0 && s != 0.0) h.diags.push_back(DiagTerm{mask, 0u, s * jz});
+    }
+  for (int q = 0; q < n; ++q) {
+    const double hz = m->hz ? m->hz[q] : 0.0, gx = m->gx ? m->gx[q] : 0.0;
+    if (!std::isfinite(hz) || !std::isfinite(gx)) {
+      set_error("non-finite field at site %d", q);
+      return RDM_EINVAL;
+    }
+    bound += std::fabs(hz) + std::fabs(gx);
+    if (gx != 0.0) h.flips.push_back(FlipTerm{site_bit(n, q), 0u, gx, gx});
+    if (hz != 0.0) h.diags.push_back(DiagTerm{site_bit(n, q), 0u, hz});
+  }
+  h.hnorm = bound;
+  *out = std::move(h);
+  return RDM_OK;
+}
+
+// ---------------------------------------------------------------- layout
+
+static int ilog2_exact(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return (int64_t(1) << r) == x ? r : -1;
+}
+
+// Chooses the slice geometry for n_v bath vectors of block size d_s.
+rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad) {
+  if (precision != RDM_FP32 && precision != RDM_FP64) {
+    set_error("precision must be RDM_FP32 or RDM_FP64");
+    return RDM_EINVAL;
+  }
+  Layout l{};
+  l.n_bits = h.n;
+  l.n_bath_bits = h.n - h.ns;
+  l.D = int64_t(1) << h.n;
+  l.DS = 1 << h.ns;
+  l.precision = precision;
+  l.elem = precision == RDM_FP32 ? 4 : 8;
+  l.VW = precision == RDM_FP32 ? 4 : (l.DS == 4 ? 4 : 2);
+  const int slice_cols = 128 / l.elem;  // 128-byte rows per slice
+  int cols = l.DS * n_v;
+  int bcols;
+  if (cols >= slice_cols) {
+    bcols = (cols + slice_cols - 1) / slice_cols * slice_cols;
+    l.Bs = slice_cols;
+  } else {
+    bcols = l.VW;
+    while (bcols < cols) bcols *= 2;
+    l.Bs = bcols;
+  }
+  l.B = bcols;
+  l.n_slices = l.B / l.Bs;
+  l.TPR = l.Bs / l.VW;
+  const int rpb = kThreads / l.TPR;
+  int64_t gx = (l.D + rpb - 1) / rpb;
+  const int64_t cap = std::max<int64_t>(1, 1216 / l.n_slices);
+  l.gridx = (int)std::min(gx, cap);
+  *L = l;
+  *n_v_pad = l.B / l.DS;
+  return RDM_OK;
+}
+
+// Layout of a caller's single-slice block of n_cols columns (apply / starting block).
+static rdm_status plan_single(const HostModel& h, int n_cols, int precision, int ds, Layout* L) {
+  Layout l{};
+  l.n_bits = h.n;
+  l.n_bath_bits = h.n - h.ns;
+  l.D = int64_t(1) << h.n;
+  l.DS = ds;
+  l.precision = precision;
+  l.elem = precision == RDM_FP32 ? 4 : 8;
+  l.VW = precision == RDM_FP32 ? 4 : (ds == 4 ? 4 : 2);
+  const int maxc = 128 / l.elem;
+  if (n_cols < l.VW || n_cols > maxc || ilog2_exact(n_cols / l.VW) < 0 || n_cols % l.VW) {
+    set_error("n_cols=%d unsupported: need %d * 2^m columns, at most %d", n_cols, l.VW, maxc);
+    return RDM_EINVAL;
+  }
+  l.B = l.Bs = n_cols;
+  l.n_slices = 1;
+  l.TPR = n_cols / l.VW;
+  const int rpb = kThreads / l.TPR;
+  l.gridx = (int)std::min<int64_t>((l.D + rpb - 1) / rpb, 1216);
+  *L = l;
+  return RDM_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    const size_t a = 256;
+    off = (off + a - 1) / a * a;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Plan {
+  Layout L;
+  int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
+};
+
+static size_t plan_bytes(const Plan& p) {
+  Arena a;  // dry run: only offsets
+  const Layout& L = p.L;
+  const size_t ng = L.n_groups(), nv = (size_t)L.DS * L.DS;
+  a.take<char>(L.block_bytes());
+  a.take<char>(L.block_bytes());
+  a.take<char>(L.block_bytes());
+  a.take<char>(L.block_bytes() * p.nbc);
+  a.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv);
+  a.take<double>((size_t)(p.k + 2) * ng * nv * 3);
+  a.take<double>((size_t)p.k * ng * nv * 2);
+  a.take<double>((size_t)p.k * p.nbc * ng * nv);
+  a.take<double>((size_t)p.nbc * ng * nv);
+  a.take<double>((size_t)p.n_v_pad * 65);
+  a.take<uint32_t>(4);
+  return a.off + 256;
+}
+
+static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, const rdm_opts* o,
+                            size_t avail, Plan* out) {
+  if (n_beta < 1 || n_v < 1 || n_v > 4096 || k < 1 || k > 512) {
+    set_error("need n_beta >= 1, 1 <= n_v <= 4096, 1 <= k <= 512 (got %d, %d, %d)", n_beta, n_v, k);
+    return RDM_EINVAL;
+  }
+  Plan p{};
+  rdm_status st = plan_layout(hm, n_v, o->precision, &p.L, &p.n_v_pad);
+  if (st != RDM_OK) return st;
+  p.n_v = n_v;
+  p.k = k;
+  p.n_beta = n_beta;
+  p.nbc = 1;
+  if (plan_bytes(p) > avail) {
+    set_error("estimate needs %zu bytes of device memory, %zu available", plan_bytes(p), avail);
+    return RDM_ENOMEM;
+  }
+  while (p.nbc < n_beta) {
+    Plan q = p;
+    q.nbc = p.nbc + 1;
+    if (plan_bytes(q) > avail) break;
+    p = q;
+  }
+  *out = p;
+  return RDM_OK;
+}
+
+size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int nbc) {
+  rdm_opts o{precision, RDM_RADEMACHER, RDM_GRAM, 0};
+  Plan p;
+  if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
+  p.nbc = std::max(1, std::min(nbc, n_beta));
+  return plan_bytes(p);
+}
+
+}  // namespace rdm
+
+using namespace rdm;
+
+// ---------------------------------------------------------------- ABI: context
+
+extern "C" const char* rdm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" rdm_status rdm_create(rdm_ctx** out, int device, void* stream) {
+  if (!out) {
+    set_error("rdm_create: out is NULL");
+    return RDM_EINVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    set_error("rdm_create: device %d out of range (%d devices)", device, ndev);
+    return RDM_EINVAL;
+  }
+  CK(cudaSetDevice(device));
+  std::unique_ptr<rdm_ctx> c(new rdm_ctx());
+  c->device = device;
+  if (stream) {
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->owns_stream = false;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->owns_stream = true;
+  }
+  *out = c.release();
+  return RDM_OK;
+}
+
+extern "C" void rdm_destroy(rdm_ctx* ctx) {
+  if (!ctx) return;
+  rdm_serve_stop(ctx);
+  cudaSetDevice(ctx->device);
+  if (ctx->owns_stream) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+extern "C" rdm_status rdm_set_workspace(rdm_ctx* ctx, void* ptr, size_t bytes) {
+  if (!ctx) {
+    set_error("rdm_set_workspace: ctx is NULL");
+    return RDM_EINVAL;
+  }
+  if (ptr && (reinterpret_cast<uintptr_t>(ptr) % 256 != 0)) {
+    set_error("rdm_set_workspace: pointer must be 256-byte aligned");
+    return RDM_EINVAL;
+  }
+  ctx->ws = ptr ? reinterpret_cast<char*>(ptr) : nullptr;
+  ctx->ws_bytes = ptr ? bytes : 0;
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_synchronize(rdm_ctx* ctx) {
+  if (!ctx) {
+    set_error("rdm_synchronize: ctx is NULL");
+    return RDM_EINVAL;
+  }
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RDM_OK;
+}
+
+// ---------------------------------------------------------------- ABI: model
+
+extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_ham** out) {
+  if (!ctx || !out) {
+    set_error("rdm_build_hamiltonian: ctx and out must be non-NULL");
+    return RDM_EINVAL;
+  }
+  *out = nullptr;
+  HostModel hm;
+  rdm_status st = compile_model(model, &hm);
+  if (st != RDM_OK) return st;
+  std::unique_ptr<rdm_ham> h(new rdm_ham());
+  h->ctx = ctx;
+  h->model = std::move(hm);
+  CK(cudaSetDevice(ctx->device));
+  const size_t fb = std::max<size_t>(1, h->model.flips.size()) * sizeof(FlipTerm);
+  const size_t db = std::max<size_t>(1, h->model.diags.size()) * sizeof(DiagTerm);
+  CK(cudaMalloc(&h->d_terms, fb + db));
+  h->d_flips = reinterpret_cast<FlipTerm*>(h->d_terms);
+  h->d_diags = reinterpret_cast<DiagTerm*>(reinterpret_cast<char*>(h->d_terms) + fb);
+  if (!h->model.flips.empty())
+    CK(cudaMemcpyAsync(h->d_flips, h->model.flips.data(), h->model.flips.size() * sizeof(FlipTerm),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (!h->model.diags.empty())
+    CK(cudaMemcpyAsync(h->d_diags, h->model.diags.data(), h->model.diags.size() * sizeof(DiagTerm),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = h.release();
+  return RDM_OK;
+}
+
+extern "C" void rdm_destroy_hamiltonian(rdm_ham* ham) {
+  if (!ham) return;
+  cudaSetDevice(ham->ctx->device);
+  if (ham->d_terms) cudaFree(ham->d_terms);
+  delete ham;
+}
+
+extern "C" rdm_status rdm_hamiltonian_info(const rdm_ham* ham, int* n_sites, int* n_sys,
+                                           int* n_flip, int* n_diag, double* norm_bound) {
+  if (!ham) {
+    set_error("rdm_hamiltonian_info: ham is NULL");
+    return RDM_EINVAL;
+  }
+  if (n_sites) *n_sites = ham->model.n;
+  if (n_sys) *n_sys = ham->model.ns;
+  if (n_flip) *n_flip = (int)ham->model.flips.size();
+  if (n_diag) *n_diag = (int)ham->model.diags.size();
+  if (norm_bound) *norm_bound = ham->model.hnorm;
+  return RDM_OK;
+}
+
+// ---------------------------------------------------------------- ABI: kernels
+
+extern "C" rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const void* x, void* y,
+                                            int n_cols) {
+  if (!ham || !x || !y) {
+    set_error("rdm_apply_hamiltonian: NULL argument");
+    return RDM_EINVAL;
+  }
+  if (precision != RDM_FP32 && precision != RDM_FP64) {
+    set_error("rdm_apply_hamiltonian: bad precision %d", precision);
+    return RDM_EINVAL;
+  }
+  Layout L;
+  rdm_status st = plan_single(ham->model, n_cols, precision, 1, &L);
+  if (st != RDM_OK) return st;
+  const size_t bytes = L.block_bytes();
+  const char* xb = reinterpret_cast<const char*>(x);
+  const char* yb = reinterpret_cast<const char*>(y);
+  if (xb < yb + bytes && yb < xb + bytes) {
+    set_error("rdm_apply_hamiltonian: x and y overlap");
+    return RDM_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 16) {
+    set_error("rdm_apply_hamiltonian: x and y must be 16-byte aligned");
+    return RDM_EINVAL;
+  }
+  CK(cudaSetDevice(ham->ctx->device));
+  SpmmArgs a{};
+  a.flips = ham->d_flips;
+  a.n_flip = (int)ham->model.flips.size();
+  a.diags = ham->d_diags;
+  a.n_diag = (int)ham->model.diags.size();
+  a.w = x;
+  a.z = y;
+  Profiler& pr = ham->ctx->prof;
+  const int ev = pr.begin(kKApply, ham->ctx->stream, true);
+  CK(launch_spmm(L, kModeApply, a, ham->ctx->stream));
+  pr.end(kKApply, ev, ham->ctx->stream, 2.0 * (double)bytes);
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, uint64_t seed,
+                                         int dist, void* x) {
+  if (!ham || !x || n_v < 1) {
+    set_error("rdm_starting_block: NULL argument or n_v < 1");
+    return RDM_EINVAL;
+  }
+  if (dist != RDM_RADEMACHER && dist != RDM_GAUSS && dist != RDM_BASIS) {
+    set_error("rdm_starting_block: bad distribution %d", dist);
+    return RDM_EINVAL;
+  }
+  const int ds = 1 << ham->model.ns;
+  if (dist == RDM_BASIS && (int64_t)n_v > (int64_t(1) << (ham->model.n - ham->model.ns))) {
+    set_error("rdm_starting_block: RDM_BASIS needs n_v <= d_b");
+    return RDM_EINVAL;
+  }
+  Layout L;
+  rdm_status st = plan_single(ham->model, ds * n_v, precision, ds, &L);
+  if (st != RDM_OK) return st;
+  CK(cudaSetDevice(ham->ctx->device));
+  cudaStream_t s = ham->ctx->stream;
+  double* norms = nullptr;
+  if (dist == RDM_GAUSS) {
+    CK(cudaMallocAsync(&norms, sizeof(double) * (size_t)n_v * 65, s));
+    CK(launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, norms + n_v, norms, s));
+  }
+  CK(launch_init_block(L, dist, seed, n_v, norms, x, s));
+  if (norms) CK(cudaFreeAsync(norms, s));
+  return RDM_OK;
+}
+
+// ---------------------------------------------------------------- ABI: estimate
+
+extern "C" rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v, int k,
+                                         const rdm_opts* opts, size_t* bytes) {
+  if (!ham || !opts || !bytes) {
+    set_error("rdm_workspace_size: NULL argument");
+    return RDM_EINVAL;
+  }
+  Plan p;
+  rdm_status st = make_plan(ham->model, n_beta, n_v, k, opts, SIZE_MAX, &p);
+  if (st != RDM_OK) return st;
+  p.nbc = 1;
+  *bytes = plan_bytes(p);
+  return RDM_OK;
+}
+
+namespace rdm {
+
+// Host part of the small dense step for one bath vector: eigenpairs of T_l.
+struct TEig {
+  std::vector<double> w, vt;  // vt: rows are eigenvectors
+  bool ok = true;
+};
+
+static void build_t(int ds, int k, int ng, int l, const std::vector<double>& ta,
+                    const std::vector<double>& tb, std::vector<double>& t) {
+  const int n = k * ds, nv = ds * ds;
+  t.assign((size_t)n * n, 0.0);
+  for (int j = 0; j < k; ++j) {
+    const double* A = &ta[((size_t)j * ng + l) * nv];
+    for (int a = 0; a < ds; ++a)
+      for (int b = 0; b < ds; ++b) t[(size_t)(j * ds + a) * n + j * ds + b] = A[a * ds + b];
+    if (j + 1 < k) {
+      const double* Bm = &tb[((size_t)j * ng + l) * nv];
+      for (int a = 0; a < ds; ++a)
+        for (int b = 0; b < ds; ++b) {
+          t[(size_t)((j + 1) * ds + a) * n + j * ds + b] = Bm[a * ds + b];
+          t[(size_t)(j * ds + b) * n + (j + 1) * ds + a] = Bm[a * ds + b];
+        }
+    }
+  }
+}
+
+template <typename F>
+static void parallel_for(int n, F&& f) {
+  int nt = (int)std::thread::hardware_concurrency();
+  nt = std::max(1, std::min(nt, n));
+  if (nt == 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (int i; (i = next.fetch_add(1)) < n;) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
+                         const double* betas, int n_beta, int n_v, int k, uint64_t seed,
+                         const rdm_opts* o, rdm_result* out, Profiler* prof) {
+  const HostModel& hm = ham->model;
+  Plan p;
+  rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws ? ws_bytes : SIZE_MAX, &p);
+  if (st != RDM_OK) return st;
+  const Layout& L = p.L;
+  const int ds = L.DS, nv = ds * ds, ng = L.n_groups();
+  const int64_t d_b = int64_t(1) << L.n_bath_bits;
+  if (o->vec_dist == RDM_BASIS && (int64_t)n_v > d_b) {
+    set_error("RDM_BASIS needs n_v <= d_b = %lld", (long long)d_b);
+    return RDM_EINVAL;
+  }
+  // Pass-2 chunk: as many psi blocks as fit in the device memory we may use.
+  bool own = false;
+  if (!ws) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t usable = (size_t)(0.85 * (double)free_b);
+    st = make_plan(hm, n_beta, n_v, k, o, usable, &p);
+    if (st != RDM_OK) return st;
+    ws_bytes = plan_bytes(p);
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&ws), ws_bytes, s));
+    own = true;
+  }
+  struct Free {
+    char* p;
+    cudaStream_t s;
+    bool own;
+    ~Free() {
+      if (own && p) cudaFreeAsync(p, s);
+    }
+  } guard{ws, s, own};
+
+  Arena ar;
+  ar.base = ws;
+  ar.cap = ws_bytes;
+  char* blk[3];
+  for (int i = 0; i < 3; ++i) blk[i] = ar.take<char>(L.block_bytes());
+  char* psi = ar.take<char>(L.block_bytes() * p.nbc);
+  double* partials = ar.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv);
+  double* coef = ar.take<double>((size_t)(k + 2) * ng * nv * 3);
+  double* d_ta = ar.take<double>((size_t)k * ng * nv);
+  double* d_tb = ar.take<double>((size_t)k * ng * nv);
+  double* d_e = ar.take<double>((size_t)k * p.nbc * ng * nv);
+  double* d_gram = ar.take<double>((size_t)p.nbc * ng * nv);
+  double* d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
+  uint32_t* d_flags = ar.take<uint32_t>(4);
+  const size_t cstride = (size_t)ng * nv;
+  auto MZ = [&](int j) { return coef + (size_t)j * cstride; };                   // j = 1..k+1
+  auto CP = [&](int j) { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; };
+  auto CW = [&](int j) { return coef + (size_t)2 * (k + 2) * cstride + (size_t)j * cstride; };
+
+  CK(cudaMemsetAsync(d_flags, 0, 4 * sizeof(uint32_t), s));
+  const double tau_abs = o->precision == RDM_FP64 ? 1e-12 : 1e-6;
+  const double tau_rel = o->precision == RDM_FP64 ? 1e-7 : 1e-5;
+  const double thr_abs_sq = (tau_abs * hm.hnorm) * (tau_abs * hm.hnorm);
+  const double thr_rel_sq = tau_rel * tau_rel;
+
+  SpmmArgs sa{};
+  sa.flips = ham->d_flips;
+  sa.n_flip = (int)hm.flips.size();
+  sa.diags = ham->d_diags;
+  sa.n_diag = (int)hm.diags.size();
+
+  const double blk_b = (double)L.block_bytes();
+  // Launch wrappers: count every launch; time the block-sized kernels with events.
+  auto timed = [&](int kind, double bytes, auto&& launch) -> cudaError_t {
+    const int ev = prof ? prof->begin(kind, s, true) : -1;
+    const cudaError_t e = launch();
+    if (prof) prof->end(kind, ev, s, bytes);
+    return e;
+  };
+  auto counted = [&](auto&& launch) -> cudaError_t {
+    if (prof) prof->begin(kKSmall, s, false);
+    return launch();
+  };
+  uint64_t h2d = 0, d2h = 0;
+
+  auto init_block = [&](char* w) -> rdm_status {
+    if (o->vec_dist == RDM_GAUSS) {
+      CK(counted([&] { return launch_gauss_norms(d_b, n_v, seed, d_norm + p.n_v_pad, d_norm, s); }));
+      if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
+    }
+    CK(timed(kKInit, blk_b, [&] { return launch_init_block(L, o->vec_dist, seed, n_v, d_norm, w, s); }));
+    return RDM_OK;
+  };
+
+  // ---- pass 1: Algorithm 1, keeping only A_j, B_j and the mixing coefficients.
+  st = init_block(blk[0]);
+  if (st != RDM_OK) return st;
+  CK(counted([&] { return launch_coef_init(L, StepCoefs{MZ(1), CP(1), nullptr}, s); }));
+  int cur = 0, prv = -1, nxt = 1;
+  for (int j = 1; j <= k; ++j) {
+    sa.w = blk[cur];
+    sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
+    sa.z = blk[nxt];
+    sa.mz = MZ(j);
+    sa.cp = CP(j);
+    sa.partials = partials;
+    CK(timed(kKSpmm1, blk_b * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(L, kModePass1, sa, s); }));
+    CK(counted([&] {
+      return launch_small_a(L, partials, MZ(j), d_ta + (size_t)(j - 1) * cstride, CW(j), d_flags, s);
+    }));
+    CK(timed(kKOrth1, blk_b * 3, [&] { return launch_orth(L, blk[cur], blk[nxt], CW(j), partials, s); }));
+    CK(counted([&] {
+      return launch_small_b(L, partials, MZ(j), d_tb + (size_t)(j - 1) * cstride, MZ(j + 1), CP(j + 1),
+                            thr_abs_sq, thr_rel_sq, n_v, d_flags, s);
+    }));
+    const int old_prev = prv;
+    prv = cur;
+    cur = nxt;
+    nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+  }
+  std::vector<double> ta((size_t)k * cstride), tb((size_t)k * cstride), mz((size_t)(k + 1) * cstride);
+  uint32_t flags[4];
+  CK(cudaMemcpyAsync(ta.data(), d_ta, ta.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(tb.data(), d_tb, tb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(mz.data(), MZ(1), mz.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  d2h += (ta.size() + tb.size() + mz.size()) * sizeof(double) + sizeof flags;
+  if (flags[0] & kFlagNonFinite) {
+    set_error("non-finite Lanczos coefficient (overflow or invalid model)");
+    return RDM_ENUMERIC;
+  }
+
+  // ---- small dense step (host float64): eigenpairs of each T_l, E0, f(T_l) E1.
+  const int n = k * ds;
+  std::vector<TEig> eig(n_v);
+  parallel_for(n_v, [&](int l) {
+    std::vector<double> t;
+    build_t(ds, k, ng, l, ta, tb, t);
+    eig[l].w.resize(n);
+    eig[l].vt.resize((size_t)n * n);
+    eig[l].ok = sym_eig(n, t.data(), eig[l].w.data(), eig[l].vt.data());
+  });
+  double e0 = INFINITY;
+  for (int l = 0; l < n_v; ++l) {
+    if (!eig[l].ok) {
+      set_error("eigensolver did not converge on T_%d", l);
+      return RDM_ENUMERIC;
+    }
+    e0 = std::min(e0, eig[l].w[0]);
+  }
+  // c[beta][l] = V f(Theta) V[0:ds,:]^T  (k*ds x ds), quad = c^T c
+  auto coef_c = [&](int l, double beta, std::vector<double>& c) {
+    const TEig& E = eig[l];
+    c.assign((size_t)n * ds, 0.0);
+    for (int m = 0; m < n; ++m) {
+      const double f = std::exp(-0.5 * beta * (E.w[m] - e0));
+      const double* vm = &E.vt[(size_t)m * n];
+      for (int i = 0; i < ds; ++i) {
+        const double fv = f * vm[i];
+        if (fv == 0.0) continue;
+        for (int r = 0; r < n; ++r) c[(size_t)r * ds + i] += vm[r] * fv;
+      }
+    }
+  };
+  std::vector<double> quad((size_t)n_beta * n_v * nv, 0.0), gram((size_t)n_beta * n_v * nv, 0.0);
+  const bool want_gram = true;
+  std::vector<double> hE((size_t)k * p.nbc * cstride);
+  std::vector<double> hg((size_t)p.nbc * cstride);
+  for (int b0 = 0; b0 < n_beta; b0 += p.nbc) {
+    const int nb = std::min(p.nbc, n_beta - b0);
+    std::fill(hE.begin(), hE.end(), 0.0);
+    parallel_for(n_v, [&](int l) {
+      std::vector<double> c;
+      for (int bi = 0; bi < nb; ++bi) {
+        coef_c(l, betas[b0 + bi], c);
+        double* q = &quad[((size_t)(b0 + bi) * n_v + l) * nv];
+        for (int a = 0; a < ds; ++a)
+          for (int b = 0; b < ds; ++b) {
+            double sacc = 0.0;
+            for (int r = 0; r < n; ++r) sacc += c[(size_t)r * ds + a] * c[(size_t)r * ds + b];
+            q[a * ds + b] = sacc;
+          }
+        // E_{j,beta} = M_j c_{j,beta}
+        for (int j = 0; j < k; ++j) {
+          const double* M = &mz[(size_t)j * cstride + (size_t)l * nv];
+          double* Ej = &hE[(((size_t)j * p.nbc + bi) * ng + l) * nv];
+          for (int a = 0; a < ds; ++a)
+            for (int b = 0; b < ds; ++b) {
+              double sacc = 0.0;
+              for (int m = 0; m < ds; ++m) sacc += M[a * ds + m] * c[(size_t)(j * ds + m) * ds + b];
+              Ej[a * ds + b] = sacc;
+            }
+        }
+      }
+    });
+    if (!want_gram) continue;
+    // ---- pass 2: recompute W_j (bit-identical) and accumulate psi.
+    CK(cudaMemcpyAsync(d_e, hE.data(), hE.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    h2d += hE.size() * sizeof(double);
+    st = init_block(blk[0]);
+    if (st != RDM_OK) return st;
+    CK(timed(kKPsiInit, blk_b * (1 + nb), [&] { return launch_psi_init(L, blk[0], psi, d_e, nb, s); }));
+    cur = 0;
+    prv = -1;
+    nxt = 1;
+    for (int j = 1; j < k; ++j) {
+      sa.w = blk[cur];
+      sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
+      sa.z = blk[nxt];
+      sa.mz = MZ(j);
+      sa.cp = CP(j);
+      sa.partials = nullptr;
+      CK(timed(kKSpmm2, blk_b * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(L, kModePass2, sa, s); }));
+      CK(timed(kKOrth2, blk_b * (3 + 2 * nb), [&] {
+        return launch_orth_psi(L, blk[cur], blk[nxt], CW(j), psi, d_e + (size_t)j * p.nbc * cstride, nb, s);
+      }));
+      const int old_prev = prv;
+      prv = cur;
+      cur = nxt;
+      nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+    }
+    for (int bi = 0; bi < nb; ++bi) {
+      CK(timed(kKGram, blk_b, [&] { return launch_final_gram(L, psi + (size_t)bi * L.block_bytes(), partials, s); }));
+      CK(counted([&] { return launch_reduce_gram(L, partials, d_gram + (size_t)bi * cstride, s); }));
+    }
+    CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cstride * sizeof(double),
+                       cudaMemcpyDeviceToHost, s));
+    d2h += (size_t)nb * cstride * sizeof(double);
+    CK(cudaStreamSynchronize(s));
+    for (int bi = 0; bi < nb; ++bi)
+      for (int l = 0; l < n_v; ++l)
+        for (int v = 0; v < nv; ++v)
+          gram[((size_t)(b0 + bi) * n_v + l) * nv + v] = hg[((size_t)bi * ng + l) * nv + v];
+  }
+  CK(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  d2h += sizeof flags;
+  if (prof) prof->collect();
+
+  // ---- normalisation (eq. rho_est) and ln Z_t.
+  auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {
+    bool ok = true;
+    for (int bi = 0; bi < n_beta; ++bi) {
+      std::vector<double> sum(nv, 0.0);
+      for (int l = 0; l < n_v; ++l)
+        for (int v = 0; v < nv; ++v) sum[v] += g[((size_t)bi * n_v + l) * nv + v];
+      double tr = 0.0;
+      for (int i = 0; i < ds; ++i) tr += sum[i * ds + i];
+      ok = ok && std::isfinite(tr) && tr > 0;
+      for (int i = 0; i < ds; ++i)
+        for (int jj = 0; jj < ds; ++jj)
+          rho[(size_t)bi * nv + i * ds + jj] = 0.5 * (sum[i * ds + jj] + sum[jj * ds + i]) / tr;
+      if (lnz) lnz[bi] = std::log((double)d_b * tr / n_v) - betas[bi] * e0;
+    }
+    return ok;
+  };
+  const bool gram_main = o->form == RDM_GRAM;
+  bool ok = finish(gram_main ? gram : quad, out->rho, out->ln_z);
+  if (out->rho_other) finish(gram_main ? quad : gram, out->rho_other, nullptr);
+  if (out->gram_l) std::copy(gram.begin(), gram.end(), out->gram_l);
+  if (out->quad_l) std::copy(quad.begin(), quad.end(), out->quad_l);
+  if (out->t_a || out->t_b)
+    for (int l = 0; l < n_v; ++l)
+      for (int j = 0; j < k; ++j)
+        for (int v = 0; v < nv; ++v) {
+          if (out->t_a) out->t_a[((size_t)l * k + j) * nv + v] = ta[((size_t)j * ng + l) * nv + v];
+          if (out->t_b) out->t_b[((size_t)l * k + j) * nv + v] = tb[((size_t)j * ng + l) * nv + v];
+        }
+  out->e0 = e0;
+  out->h2d_bytes = h2d;
+  out->d2h_bytes = d2h;
+  out->flags = (flags[0] & RDM_FLAG_DEFLATED) | (p.n_v_pad != n_v ? RDM_FLAG_PADDED : 0u);
+  if (!ok) {
+    set_error("the estimated tr(sum_l G_l) is not a positive finite number (underflow or breakdown)");
+    return RDM_ENUMERIC;
+  }
+  return RDM_OK;
+}
+
+}  // namespace rdm
+
+static bool valid_opts(const rdm_opts* o) {
+  return o && (o->precision == RDM_FP32 || o->precision == RDM_FP64) &&
+         (o->vec_dist == RDM_RADEMACHER || o->vec_dist == RDM_GAUSS || o->vec_dist == RDM_BASIS) &&
+         (o->form == RDM_GRAM || o->form == RDM_QUADRATURE) && o->reserved == 0;
+}
+
+rdm_status rdm::check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,
+                                    const rdm_opts* opts, const rdm_result* out) {
+  if (!ham || !betas || !out || !out->rho) {
+    set_error("rdm_estimate: ham, betas, out and out->rho must be non-NULL");
+    return RDM_EINVAL;
+  }
+  if (!valid_opts(opts)) {
+    set_error("rdm_estimate: invalid opts");
+    return RDM_EINVAL;
+  }
+  for (int i = 0; i < n_beta; ++i)
+    if (!(betas[i] >= 0) || !std::isfinite(betas[i])) {
+      set_error("rdm_estimate: beta[%d] must be finite and >= 0", i);
+      return RDM_EINVAL;
+    }
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta, int n_v, int k,
+                                   uint64_t seed, const rdm_opts* opts, rdm_result* out) {
+  rdm_status st = check_estimate_args(ham, betas, n_beta, opts, out);
+  if (st != RDM_OK) return st;
+  CK(cudaSetDevice(ham->ctx->device));
+  return estimate_impl(ham, ham->ctx->stream, ham->ctx->ws, ham->ctx->ws_bytes, betas, n_beta,
+                       n_v, k, seed, opts, out, &ham->ctx->prof);
+}

@@ -1,0 +1,228 @@
+// Host float64 dense symmetric eigensolver and the post-processing of rho*.
+//
+// The small dense step of the estimator (eq. fT: f(T_l) from the eigen-
+// decomposition of the block tridiagonal T_l, Sec. 3.1 "T_l can be diagonalized
+// exactly") and H* through the eigenvalues of rho* (end of Sec. 3.2) both need
+// eigenpairs of small symmetric matrices. Method (textbook, Golub & Van Loan,
+// "Matrix Computations", Sec. 8.3): Householder reduction to tridiagonal form with
+// the orthogonal factor accumulated, then implicit symmetric QR steps with the
+// Wilkinson shift, rotations accumulated into the eigenvector matrix.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "rdm_internal.h"
+
+namespace rdm {
+void set_error(const char* fmt, ...);
+
+// Eigen-decomposition of the symmetric n x n row-major matrix `a`.
+// w: ascending eigenvalues; vt (optional): n*n with ROW j = eigenvector j.
+// Returns false if the QR iteration did not converge.
+bool sym_eig(int n, const double* a_in, double* w, double* vt) {
+  if (n <= 0) return true;
+  if (n == 1) {
+    w[0] = a_in[0];
+    if (vt) vt[0] = 1.0;
+    return true;
+  }
+  std::vector<double> a(a_in, a_in + (size_t)n * n);
+  const bool want = vt != nullptr;
+  // qt[j*n + r] = Q[r][j]: column j of Q stored contiguously.
+  std::vector<double> qt;
+  if (want) {
+    qt.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) qt[(size_t)i * n + i] = 1.0;
+  }
+  std::vector<double> v(n), p(n), wv(n), t(n);
+  auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+
+  // ---- Householder tridiagonalisation: Q^T A Q = tridiag.
+  for (int k = 0; k + 2 < n; ++k) {
+    double tail = 0.0;
+    for (int i = k + 2; i < n; ++i) tail += A(i, k) * A(i, k);
+    if (tail == 0.0) continue;
+    const double x0 = A(k + 1, k);
+    const double nrm = std::sqrt(tail + x0 * x0);
+    const double alpha = x0 > 0 ? -nrm : nrm;
+    v[k + 1] = x0 - alpha;
+    double vv = v[k + 1] * v[k + 1];
+    for (int i = k + 2; i < n; ++i) {
+      v[i] = A(i, k);
+      vv += v[i] * v[i];
+    }
+    const double beta = 2.0 / vv;
+    double vp = 0.0;
+    for (int i = k + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += A(i, j) * v[j];
+      p[i] = beta * s;
+      vp += v[i] * p[i];
+    }
+    const double kk = 0.5 * beta * vp;
+    for (int i = k + 1; i < n; ++i) wv[i] = p[i] - kk * v[i];
+    for (int i = k + 1; i < n; ++i)
+      for (int j = k + 1; j < n; ++j) A(i, j) -= v[i] * wv[j] + wv[i] * v[j];
+    A(k + 1, k) = A(k, k + 1) = alpha;
+    for (int i = k + 2; i < n; ++i) A(i, k) = A(k, i) = 0.0;
+    if (want) {
+      // Q <- Q (I - beta v v^T) on columns k+1..n-1.
+      std::fill(t.begin(), t.end(), 0.0);
+      for (int j = k + 1; j < n; ++j) {
+        const double vj = v[j];
+        const double* qj = &qt[(size_t)j * n];
+        for (int r = 0; r < n; ++r) t[r] += qj[r] * vj;
+      }
+      for (int j = k + 1; j < n; ++j) {
+        const double f = beta * v[j];
+        double* qj = &qt[(size_t)j * n];
+        for (int r = 0; r < n; ++r) qj[r] -= f * t[r];
+      }
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = A(i + 1, i);
+
+  // ---- implicit symmetric QR with Wilkinson shift on (d, e).
+  const double eps = DBL_EPSILON;
+  int hi = n - 1;
+  long iters = 0;
+  const long max_iters = 60L * n;
+  while (hi > 0) {
+    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi])) ||
+        std::fabs(e[hi - 1]) < DBL_MIN) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo])) &&
+           std::fabs(e[lo - 1]) >= DBL_MIN)
+      --lo;
+    if (++iters > max_iters) return false;
+    const double delta = 0.5 * (d[hi - 1] - d[hi]);
+    const double eh = e[hi - 1];
+    const double denom = delta + (delta >= 0 ? 1.0 : -1.0) * std::hypot(delta, eh);
+    const double mu = d[hi] - eh * eh / denom;
+    double x = d[lo] - mu;
+    double z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r;
+      const double s = r == 0.0 ? 0.0 : -z / r;
+      if (k > lo) e[k - 1] = r;
+      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+      d[k] = c * c * dk - 2.0 * c * s * ek + s * s * dk1;
+      d[k + 1] = s * s * dk + 2.0 * c * s * ek + c * c * dk1;
+      e[k] = c * s * (dk - dk1) + (c * c - s * s) * ek;
+      if (k + 1 < hi) {
+        x = e[k];
+        z = -s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+      }
+      if (want) {
+        double* qa = &qt[(size_t)k * n];
+        double* qb = &qt[(size_t)(k + 1) * n];
+        for (int rr = 0; rr < n; ++rr) {
+          const double ya = qa[rr], yb = qb[rr];
+          qa[rr] = c * ya - s * yb;
+          qb[rr] = s * ya + c * yb;
+        }
+      }
+    }
+  }
+  // ---- sort ascending.
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x1, int x2) { return d[x1] < d[x2]; });
+  for (int j = 0; j < n; ++j) w[j] = d[idx[j]];
+  if (want)
+    for (int j = 0; j < n; ++j)
+      std::copy(&qt[(size_t)idx[j] * n], &qt[(size_t)idx[j] * n] + n, &vt[(size_t)j * n]);
+  return true;
+}
+
+}  // namespace rdm
+
+using rdm::set_error;
+
+extern "C" rdm_status rdm_symmetric_eig(int n, const double* a, double* w, double* v) {
+  if (n < 1 || n > 8192 || !a || !w) {
+    set_error("rdm_symmetric_eig: need 1 <= n <= 8192 and non-NULL a, w");
+    return RDM_EINVAL;
+  }
+  std::vector<double> vt;
+  if (v) vt.resize((size_t)n * n);
+  if (!rdm::sym_eig(n, a, w, v ? vt.data() : nullptr)) {
+    set_error("rdm_symmetric_eig: QR iteration did not converge");
+    return RDM_ENUMERIC;
+  }
+  if (v)
+    for (int r = 0; r < n; ++r)
+      for (int j = 0; j < n; ++j) v[(size_t)r * n + j] = vt[(size_t)j * n + r];
+  return RDM_OK;
+}
+
+static bool symmetrised(const double* rho, int d, std::vector<double>& out) {
+  out.resize((size_t)d * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double x = 0.5 * (rho[i * d + j] + rho[j * d + i]);
+      if (!std::isfinite(x)) return false;
+      out[i * d + j] = x;
+    }
+  return true;
+}
+
+extern "C" rdm_status rdm_mean_force(const double* rho, int d_s, double beta, double* h_out) {
+  if (!rho || !h_out || d_s < 1 || d_s > 64 || !(beta > 0) || !std::isfinite(beta)) {
+    set_error("rdm_mean_force: need rho, h_out, 1 <= d_s <= 64 and finite beta > 0");
+    return RDM_EINVAL;
+  }
+  std::vector<double> a, w(d_s), vt((size_t)d_s * d_s);
+  if (!symmetrised(rho, d_s, a)) {
+    set_error("rdm_mean_force: rho has non-finite entries");
+    return RDM_ENUMERIC;
+  }
+  if (!rdm::sym_eig(d_s, a.data(), w.data(), vt.data())) {
+    set_error("rdm_mean_force: eigensolver did not converge");
+    return RDM_ENUMERIC;
+  }
+  for (int j = 0; j < d_s; ++j)
+    if (!(w[j] > 0)) {
+      set_error("rdm_mean_force: rho has eigenvalue %.3e <= 0, ln(rho) undefined", w[j]);
+      return RDM_ENOTPD;
+    }
+  // H = -(1/beta) U diag(ln p) U^T
+  for (int r = 0; r < d_s; ++r)
+    for (int c = 0; c < d_s; ++c) {
+      double s = 0.0;
+      for (int j = 0; j < d_s; ++j) s += vt[j * d_s + r] * std::log(w[j]) * vt[j * d_s + c];
+      h_out[r * d_s + c] = -s / beta;
+    }
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_entropy(const double* rho, int d_s, double* s_out) {
+  if (!rho || !s_out || d_s < 1 || d_s > 64) {
+    set_error("rdm_entropy: need rho, s_out and 1 <= d_s <= 64");
+    return RDM_EINVAL;
+  }
+  std::vector<double> a, w(d_s);
+  if (!symmetrised(rho, d_s, a)) {
+    set_error("rdm_entropy: rho has non-finite entries");
+    return RDM_ENUMERIC;
+  }
+  if (!rdm::sym_eig(d_s, a.data(), w.data(), nullptr)) {
+    set_error("rdm_entropy: eigensolver did not converge");
+    return RDM_ENUMERIC;
+  }
+  double s = 0.0;
+  for (int j = 0; j < d_s; ++j)
+    if (w[j] > 0) s -= w[j] * std::log(w[j]);
+  *s_out = s;
+  return RDM_OK;
+}

@@ -1,0 +1,758 @@
+// CUDA kernels of the estimator's hot path (sm_103a).
+//
+//   k_init_block   the starting block V = [I_s (x) |v_l>]_l (Sec. 3.1, eq. trace_est)
+//                  from the counter-based generator (SplitMix64 on a counter)
+//   k_spmm         Z = (H W_j) M_j + W_{j-1} Cp_j: the matrix-free spin-Hamiltonian
+//                  block SpMM (eq. Ht) fused with the first line of Algorithm 1's
+//                  loop, and the partial sums of W_j^T Z for A_j
+//   k_orth         W_{j+1} = Z + W_j Cw_j (Algorithm 1, Z - Q_j A_j) with the
+//                  partial sums of W_{j+1}^T W_{j+1} for the QR (pass 1), or the
+//                  accumulation psi_beta += W_{j+1} E_{j+1,beta} (pass 2)
+//   k_small_a/b    per bath vector, float64: A_j, Cholesky QR with breakdown
+//                  deflation, the next step's mixing coefficients
+//   k_final_gram   the bath-traced Gram psi_l^T psi_l per bath vector
+//
+// The Krylov block of every bath vector l is never normalised in memory: the
+// stored W_j relates to the orthonormal Q_j of Algorithm 1 by Q_j = W_j M_j with
+// a d_s x d_s matrix M_j (the inverse Cholesky factor), applied on the fly.
+// Reductions are deterministic: per-thread partial sums, a fixed-order block
+// reduction into per-block partials, and a fixed-order sum over blocks.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rdm_internal.h"
+
+namespace rdm {
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+__device__ __forceinline__ double gauss_raw(uint64_t seed, uint64_t l, uint64_t b) {
+  const uint64_t base = l << 40;
+  const uint64_t z1 = splitmix64(seed, (base | (2 * b)) + 1);
+  const uint64_t z2 = splitmix64(seed, (base | (2 * b + 1)) + 1);
+  const double u1 = ((double)(z1 >> 11) + 0.5) * 0x1.0p-53;
+  const double u2 = ((double)(z2 >> 11) + 0.5) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+}
+
+// ---- VW-wide vector access (VW * sizeof(T) is 8, 16 or 32 bytes).
+template <typename T, int VW>
+struct VecIO;
+template <>
+struct VecIO<float, 4> {
+  __device__ static void ld(float* r, const float* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+  __device__ static void ld_rw(float* r, const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+  __device__ static void st(float* p, const float* r) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+};
+template <>
+struct VecIO<double, 2> {
+  __device__ static void ld(double* r, const double* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    r[0] = v.x; r[1] = v.y;
+  }
+  __device__ static void ld_rw(double* r, const double* p) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  }
+  __device__ static void st(double* p, const double* r) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+  }
+};
+template <>
+struct VecIO<double, 4> {
+  __device__ static void ld(double* r, const double* p) {
+    VecIO<double, 2>::ld(r, p);
+    VecIO<double, 2>::ld(r + 2, p + 2);
+  }
+  __device__ static void ld_rw(double* r, const double* p) {
+    VecIO<double, 2>::ld_rw(r, p);
+    VecIO<double, 2>::ld_rw(r + 2, p + 2);
+  }
+  __device__ static void st(double* p, const double* r) {
+    VecIO<double, 2>::st(p, r);
+    VecIO<double, 2>::st(p + 2, r + 2);
+  }
+};
+
+// Mask of the lanes of this thread's row group inside its warp.
+__device__ __forceinline__ unsigned group_mask(int tpr) {
+  if (tpr >= 32) return 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  return ((1u << tpr) - 1u) << (lane & ~(unsigned)(tpr - 1));
+}
+
+// Fixed-order block reduction of NV float64 values per thread into per-block
+// partials: partials[((slice*gridx + bx)*G_s + lane*NG + g)*NVG + v] where
+// vals[g*NVG + v] belongs to group g of the thread.
+template <int NG, int NVG>
+__device__ void block_reduce_store(const double* vals, int tpr, double* partials, int gs) {
+  constexpr int NV = NG * NVG;
+  __shared__ double red[kThreads * NV];
+  for (int v = 0; v < NV; ++v) red[threadIdx.x * NV + v] = vals[v];
+  __syncthreads();
+  const int rpb = kThreads / tpr;
+  if ((int)threadIdx.x < tpr) {
+    const int lane = threadIdx.x;
+    const size_t base =
+        ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * gs + (size_t)lane * NG) * NVG;
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+      for (int r = 0; r < rpb; ++r) s += red[(r * tpr + lane) * NV + v];
+      partials[base + v] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- init
+
+__global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, double* part) {
+  __shared__ double sh[kThreads];
+  const int l = blockIdx.y;
+  const int64_t chunk = (d_b + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < d_b ? lo + chunk : d_b;
+  double acc = 0.0;
+  for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+    const double g = gauss_raw(seed, (uint64_t)l, (uint64_t)b);
+    acc += g * g;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)l * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void k_gauss_finish(int n_v, int gx, const double* part, double* inv_norm) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_v) return;
+  double s = 0.0;
+  for (int i = 0; i < gx; ++i) s += part[(size_t)l * gx + i];
+  inv_norm[l] = 1.0 / sqrt(s);
+}
+
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uint64_t seed,
+                                                         int nvr, const double* inv_norm, T* W) {
+  constexpr int NG = VW / DS;
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  T* base = W + (size_t)slice * L.D * L.Bs + lane * VW;
+  const int g0 = (slice * L.Bs + lane * VW) / DS;
+  const uint64_t bmask = (1ull << L.n_bath_bits) - 1ull;
+  const double rad = 1.0 / sqrt((double)(1ull << L.n_bath_bits));
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    const int i = (int)(s >> L.n_bath_bits);
+    const uint64_t b = (uint64_t)s & bmask;
+    T v[VW];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int l = g0 + g;
+      double val = 0.0;
+      if (l < nvr) {
+        if (dist == RDM_RADEMACHER) {
+          const uint64_t z = splitmix64(seed, (((uint64_t)l << 40) | b) + 1);
+          val = (z >> 63) ? -rad : rad;
+        } else if (dist == RDM_GAUSS) {
+          val = gauss_raw(seed, (uint64_t)l, b) * inv_norm[l];
+        } else {
+          val = (b == (uint64_t)l) ? 1.0 : 0.0;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < DS; ++a) v[g * DS + a] = (a == i) ? (T)val : (T)0;
+    }
+    VecIO<T, VW>::st(base + (size_t)s * L.Bs, v);
+  }
+}
+
+// ---------------------------------------------------------------- SpMM step
+
+template <typename T>
+struct TermsSmem {
+  uint32_t* fmask;
+  T* fodd;
+  T* feven;
+  uint32_t* dmask;
+  T* dc;
+};
+
+template <typename T>
+__device__ TermsSmem<T> load_terms(const FlipTerm* flips, int nf, const DiagTerm* diags, int nd) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TermsSmem<T> t;
+  T* tp = reinterpret_cast<T*>(smem_raw);
+  t.fodd = tp;
+  t.feven = tp + nf;
+  t.dc = tp + 2 * nf;
+  uint32_t* up = reinterpret_cast<uint32_t*>(tp + 2 * nf + nd);
+  t.fmask = up;
+  t.dmask = up + nf;
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    t.fmask[i] = flips[i].mask;
+    t.fodd[i] = (T)flips[i].c_odd;
+    t.feven[i] = (T)flips[i].c_even;
+  }
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    t.dmask[i] = diags[i].mask;
+    t.dc[i] = (T)diags[i].c;
+  }
+  __syncthreads();
+  return t;
+}
+
+template <typename T, int DS, int VW, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  const TermsSmem<T> terms = load_terms<T>(a.flips, a.n_flip, a.diags, a.n_diag);
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  const T* __restrict__ W = reinterpret_cast<const T*>(a.w) + soff;
+  const T* __restrict__ Wp = a.w_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
+  T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
+  const int g0 = (slice * L.Bs + lane * VW) / DS;
+  const unsigned gmask = group_mask(tpr);
+
+  T mz[NG][DS][DS], cp[NG][DS][DS];
+  if (MODE != kModeApply) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) {
+          mz[g][i][j] = (T)a.mz[(size_t)(g0 + g) * NVG + i * DS + j];
+          cp[g][i][j] = Wp ? (T)a.cp[(size_t)(g0 + g) * NVG + i * DS + j] : (T)0;
+        }
+  }
+  T acc[NG][DS][DS];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < DS; ++i)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
+
+  const int nf = a.n_flip, nd = a.n_diag;
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    const uint32_t su = (uint32_t)s;
+    T x[VW];
+    VecIO<T, VW>::ld(x, W + (size_t)s * L.Bs);
+    // Diagonal: sum_t c_t (1 - 2 parity(s & m_t)), split over the row group.
+    T dg = (T)0;
+    for (int t = lane; t < nd; t += tpr) {
+      const T c = terms.dc[t];
+      dg += (__popc(su & terms.dmask[t]) & 1) ? -c : c;
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1) dg += __shfl_xor_sync(gmask, dg, off, tpr);
+    T y[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) y[v] = dg * x[v];
+    // Off-diagonal: y += c(parity(s & m)) x[s ^ m].
+    for (int t = 0; t < nf; ++t) {
+      const uint32_t m = terms.fmask[t];
+      const T c = (__popc(su & m) & 1) ? terms.fodd[t] : terms.feven[t];
+      if (c != (T)0) {
+        T xp[VW];
+        VecIO<T, VW>::ld(xp, W + (size_t)(su ^ m) * L.Bs);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[v] = fma(c, xp[v], y[v]);
+      }
+    }
+    if (MODE == kModeApply) {
+      VecIO<T, VW>::st(Z + (size_t)s * L.Bs, y);
+      continue;
+    }
+    T z[VW];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) {
+        T t = (T)0;
+#pragma unroll
+        for (int i = 0; i < DS; ++i) t = fma(y[g * DS + i], mz[g][i][j], t);
+        z[g * DS + j] = t;
+      }
+    if (Wp) {
+      T xp[VW];
+      VecIO<T, VW>::ld(xp, Wp + (size_t)s * L.Bs);
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) {
+          T t = z[g * DS + j];
+#pragma unroll
+          for (int i = 0; i < DS; ++i) t = fma(xp[g * DS + i], cp[g][i][j], t);
+          z[g * DS + j] = t;
+        }
+    }
+    VecIO<T, VW>::st(Z + (size_t)s * L.Bs, z);
+    if (MODE == kModePass1) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int i = 0; i < DS; ++i)
+#pragma unroll
+          for (int j = 0; j < DS; ++j) acc[g][i][j] = fma(x[g * DS + i], z[g * DS + j], acc[g][i][j]);
+    }
+  }
+  if (MODE == kModePass1) {
+    double vals[NG * NVG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
+    block_reduce_store<NG, NVG>(vals, tpr, a.partials, L.groups_per_slice());
+  }
+}
+
+// ---------------------------------------------------------------- orthogonalisation
+
+template <typename T, int DS, int VW, bool PASS1>
+__global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict__ Wg,
+                                                   T* __restrict__ Zg, const double* cw,
+                                                   double* partials, T* psi, const double* e,
+                                                   int nb) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  const T* W = Wg + soff;
+  T* Z = Zg + soff;
+  const int g0 = (slice * L.Bs + lane * VW) / DS;
+  const size_t bstride = (size_t)L.D * L.B;  // elements per psi block
+  T c[NG][DS][DS];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < DS; ++i)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) c[g][i][j] = (T)cw[(size_t)(g0 + g) * NVG + i * DS + j];
+  T acc[NG][DS][DS];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < DS; ++i)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
+  const int ngs = L.n_groups();
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    T x[VW], z[VW];
+    VecIO<T, VW>::ld(x, W + (size_t)s * L.Bs);
+    VecIO<T, VW>::ld_rw(z, Z + (size_t)s * L.Bs);
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) {
+        T t = z[g * DS + j];
+#pragma unroll
+        for (int i = 0; i < DS; ++i) t = fma(x[g * DS + i], c[g][i][j], t);
+        z[g * DS + j] = t;
+      }
+    VecIO<T, VW>::st(Z + (size_t)s * L.Bs, z);
+    if (PASS1) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int i = 0; i < DS; ++i)
+#pragma unroll
+          for (int j = 0; j < DS; ++j) acc[g][i][j] = fma(z[g * DS + i], z[g * DS + j], acc[g][i][j]);
+    } else {
+      for (int bi = 0; bi < nb; ++bi) {
+        T* P = psi + bi * bstride + soff + (size_t)s * L.Bs;
+        T p[VW];
+        VecIO<T, VW>::ld_rw(p, P);
+        const double* eb = e + (size_t)bi * ngs * NVG;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int j = 0; j < DS; ++j) {
+            T t = p[g * DS + j];
+#pragma unroll
+            for (int i = 0; i < DS; ++i)
+              t = fma(z[g * DS + i], (T)eb[(size_t)(g0 + g) * NVG + i * DS + j], t);
+            p[g * DS + j] = t;
+          }
+        VecIO<T, VW>::st(P, p);
+      }
+    }
+  }
+  if (PASS1) {
+    double vals[NG * NVG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
+    block_reduce_store<NG, NVG>(vals, tpr, partials, L.groups_per_slice());
+  }
+}
+
+// psi_beta = W_1 E_{1,beta} (start of pass 2).
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_psi_init(Layout L, const T* __restrict__ Wg,
+                                                       T* psi, const double* e, int nb) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  const int g0 = (slice * L.Bs + lane * VW) / DS;
+  const size_t bstride = (size_t)L.D * L.B;
+  const int ngs = L.n_groups();
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    T x[VW];
+    VecIO<T, VW>::ld(x, Wg + soff + (size_t)s * L.Bs);
+    for (int bi = 0; bi < nb; ++bi) {
+      const double* eb = e + (size_t)bi * ngs * NVG;
+      T p[VW];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) {
+          T t = (T)0;
+#pragma unroll
+          for (int i = 0; i < DS; ++i) t = fma(x[g * DS + i], (T)eb[(size_t)(g0 + g) * NVG + i * DS + j], t);
+          p[g * DS + j] = t;
+        }
+      VecIO<T, VW>::st(psi + bi * bstride + soff + (size_t)s * L.Bs, p);
+    }
+  }
+}
+
+// Gram partials of one psi block.
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __restrict__ P,
+                                                         double* partials) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  T acc[NG][DS][DS];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < DS; ++i)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    T p[VW];
+    VecIO<T, VW>::ld(p, P + soff + (size_t)s * L.Bs);
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) acc[g][i][j] = fma(p[g * DS + i], p[g * DS + j], acc[g][i][j]);
+  }
+  double vals[NG * NVG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < DS; ++i)
+#pragma unroll
+      for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
+  block_reduce_store<NG, NVG>(vals, tpr, partials, L.groups_per_slice());
+}
+
+// ---------------------------------------------------------------- per-group small steps
+
+constexpr int kSmallThreads = 128;
+
+// Sums the NV partials of group blockIdx.x over the gridx blocks (fixed order).
+template <int NV>
+__device__ void reduce_group(const Layout& L, const double* partials, double* out) {
+  __shared__ double sh[kSmallThreads];
+  const int l = blockIdx.x;
+  const int gs = L.groups_per_slice();
+  const int slice = l / gs, gis = l % gs;
+  for (int v = 0; v < NV; ++v) {
+    double s = 0.0;
+    for (int bx = threadIdx.x; bx < L.gridx; bx += kSmallThreads)
+      s += partials[((size_t)(slice * L.gridx + bx) * gs + gis) * NV + v];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kSmallThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[v] = sh[0];
+    __syncthreads();
+  }
+}
+
+template <int DS>
+__global__ void k_coef_init(int n_groups, double* mz, double* cp) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_groups) return;
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      mz[(size_t)l * DS * DS + i * DS + j] = i == j ? 1.0 : 0.0;
+      cp[(size_t)l * DS * DS + i * DS + j] = 0.0;
+    }
+}
+
+template <int DS>
+__global__ void k_small_a(Layout L, const double* partials, const double* mz, double* a_out,
+                          double* cw_out, uint32_t* flags) {
+  constexpr int NV = DS * DS;
+  __shared__ double tot[NV];
+  reduce_group<NV>(L, partials, tot);
+  if (threadIdx.x != 0) return;
+  const int l = blockIdx.x;
+  const double* M = mz + (size_t)l * NV;
+  double p1[DS][DS], A[DS][DS];
+  // P1 = M^T (W^T Z) = Q_j^T Z
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      double s = 0.0;
+      for (int c = 0; c < DS; ++c) s += M[c * DS + i] * tot[c * DS + j];
+      p1[i][j] = s;
+    }
+  bool finite = true;
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      A[i][j] = 0.5 * (p1[i][j] + p1[j][i]);
+      finite = finite && isfinite(A[i][j]);
+    }
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      a_out[(size_t)l * NV + i * DS + j] = A[i][j];
+      double s = 0.0;
+      for (int c = 0; c < DS; ++c) s += M[i * DS + c] * A[c][j];
+      cw_out[(size_t)l * NV + i * DS + j] = -s;
+    }
+  if (!finite) atomicOr(flags, kFlagNonFinite);
+}
+
+template <int DS>
+__global__ void k_small_b(Layout L, const double* partials, const double* mz_j, double* b_out,
+                          double* mz_next, double* cp_next, double thr_abs_sq, double thr_rel_sq,
+                          int n_real, uint32_t* flags) {
+  constexpr int NV = DS * DS;
+  __shared__ double tot[NV];
+  reduce_group<NV>(L, partials, tot);
+  if (threadIdx.x != 0) return;
+  const int l = blockIdx.x;
+  double G[DS][DS], R[DS][DS], Ri[DS][DS];
+  bool kept[DS];
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      G[i][j] = 0.5 * (tot[i * DS + j] + tot[j * DS + i]);
+      R[i][j] = 0.0;
+      Ri[i][j] = 0.0;
+    }
+  // Cholesky G = R^T R column by column, dropping numerically dependent columns
+  // (Gram-Schmidt in the G inner product; same rule as a column-wise QR).
+  bool dropped = false, finite = true;
+  for (int c = 0; c < DS; ++c) {
+    for (int k = 0; k < c; ++k) {
+      if (!kept[k]) continue;
+      double s = G[k][c];
+      for (int i = 0; i < k; ++i)
+        if (kept[i]) s -= R[i][k] * R[i][c];
+      R[k][c] = s / R[k][k];
+    }
+    double piv = G[c][c];
+    for (int k = 0; k < c; ++k)
+      if (kept[k]) piv -= R[k][c] * R[k][c];
+    finite = finite && isfinite(piv);
+    if (!(piv > thr_abs_sq) || !(piv > thr_rel_sq * G[c][c])) {
+      kept[c] = false;
+      R[c][c] = 0.0;
+      dropped = true;
+    } else {
+      kept[c] = true;
+      R[c][c] = sqrt(piv);
+    }
+  }
+  // Inverse of R restricted to the kept columns (back substitution), zero elsewhere.
+  for (int c = 0; c < DS; ++c) {
+    if (!kept[c]) continue;
+    Ri[c][c] = 1.0 / R[c][c];
+    for (int r = c - 1; r >= 0; --r) {
+      if (!kept[r]) continue;
+      double s = 0.0;
+      for (int m = r + 1; m <= c; ++m)
+        if (kept[m]) s += R[r][m] * Ri[m][c];
+      Ri[r][c] = -s / R[r][r];
+    }
+  }
+  const double* Mj = mz_j + (size_t)l * NV;
+  for (int i = 0; i < DS; ++i)
+    for (int j = 0; j < DS; ++j) {
+      b_out[(size_t)l * NV + i * DS + j] = R[i][j];
+      mz_next[(size_t)l * NV + i * DS + j] = Ri[i][j];
+      double s = 0.0;
+      for (int c = 0; c < DS; ++c) s += Mj[i * DS + c] * R[j][c];
+      cp_next[(size_t)l * NV + i * DS + j] = -s;
+    }
+  if (dropped && l < n_real) atomicOr(flags, (uint32_t)RDM_FLAG_DEFLATED);
+  if (!finite) atomicOr(flags, kFlagNonFinite);
+}
+
+template <int DS>
+__global__ void k_reduce_gram(Layout L, const double* partials, double* gram) {
+  constexpr int NV = DS * DS;
+  __shared__ double tot[NV];
+  reduce_group<NV>(L, partials, tot);
+  if (threadIdx.x != 0) return;
+  for (int v = 0; v < NV; ++v) gram[(size_t)blockIdx.x * NV + v] = tot[v];
+}
+
+inline dim3 grid_of(const Layout& L) { return dim3((unsigned)L.gridx, (unsigned)L.n_slices); }
+
+template <typename T>
+size_t terms_smem(int nf, int nd) {
+  return (size_t)(2 * nf + nd) * sizeof(T) + (size_t)(nf + nd) * sizeof(uint32_t) + 16;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- dispatch
+
+#define RDM_DISPATCH(L, ...)                                         \
+  do {                                                                \
+    if ((L).precision == RDM_FP32) {                                  \
+      using T = float;                                                \
+      constexpr int VW = 4;                                           \
+      if ((L).DS == 1) { constexpr int DS = 1; __VA_ARGS__; }                \
+      else if ((L).DS == 2) { constexpr int DS = 2; __VA_ARGS__; }           \
+      else { constexpr int DS = 4; __VA_ARGS__; }                            \
+    } else {                                                          \
+      using T = double;                                               \
+      if ((L).DS == 1) { constexpr int DS = 1; constexpr int VW = 2; __VA_ARGS__; } \
+      else if ((L).DS == 2) { constexpr int DS = 2; constexpr int VW = 2; __VA_ARGS__; } \
+      else { constexpr int DS = 4; constexpr int VW = 4; __VA_ARGS__; }      \
+    }                                                                 \
+  } while (0)
+
+#define RDM_DISPATCH_DS(DSV, ...)                      \
+  do {                                                  \
+    if ((DSV) == 1) { constexpr int DS = 1; __VA_ARGS__; }     \
+    else if ((DSV) == 2) { constexpr int DS = 2; __VA_ARGS__; } \
+    else { constexpr int DS = 4; __VA_ARGS__; }                \
+  } while (0)
+
+cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* partials,
+                               double* inv_norm, cudaStream_t st) {
+  int gx = (int)((d_b + 4095) / 4096);
+  if (gx > 64) gx = 64;
+  if (gx < 1) gx = 1;
+  k_gauss_sumsq<<<dim3(gx, n_v), kThreads, 0, st>>>(d_b, seed, partials);
+  k_gauss_finish<<<(n_v + 127) / 128, 128, 0, st>>>(n_v, gx, partials, inv_norm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
+                              const double* inv_norm, void* W, cudaStream_t st) {
+  RDM_DISPATCH(L, (k_init_block<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
+                      L, dist, seed, n_v_real, inv_norm, reinterpret_cast<T*>(W))));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st) {
+  RDM_DISPATCH(L, {
+    const size_t sm = terms_smem<T>(a.n_flip, a.n_diag);
+    if (mode == kModeApply)
+      k_spmm<T, DS, VW, kModeApply><<<grid_of(L), kThreads, sm, st>>>(L, a);
+    else if (mode == kModePass1)
+      k_spmm<T, DS, VW, kModePass1><<<grid_of(L), kThreads, sm, st>>>(L, a);
+    else
+      k_spmm<T, DS, VW, kModePass2><<<grid_of(L), kThreads, sm, st>>>(L, a);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orth(const Layout& L, const void* w, void* z, const double* cw,
+                        double* partials, cudaStream_t st) {
+  RDM_DISPATCH(L, (k_orth<T, DS, VW, true><<<grid_of(L), kThreads, 0, st>>>(
+                      L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, partials,
+                      nullptr, nullptr, 0)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const double* cw, void* psi,
+                            const double* e, int nb, cudaStream_t st) {
+  RDM_DISPATCH(L, (k_orth<T, DS, VW, false><<<grid_of(L), kThreads, 0, st>>>(
+                      L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
+                      reinterpret_cast<T*>(psi), e, nb)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_init(const Layout& L, const void* w, void* psi, const double* e, int nb,
+                            cudaStream_t st) {
+  RDM_DISPATCH(L, (k_psi_init<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
+                      L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(psi), e, nb)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_init(const Layout& L, StepCoefs c1, cudaStream_t st) {
+  const int ng = L.n_groups();
+  RDM_DISPATCH_DS(L.DS, (k_coef_init<DS><<<(ng + 127) / 128, 128, 0, st>>>(ng, c1.mz, c1.cp)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_a(const Layout& L, const double* partials, const double* mz,
+                           double* a_out, double* cw_out, uint32_t* flags, cudaStream_t st) {
+  RDM_DISPATCH_DS(L.DS, (k_small_a<DS><<<L.n_groups(), kSmallThreads, 0, st>>>(
+                           L, partials, mz, a_out, cw_out, flags)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_b(const Layout& L, const double* partials, const double* mz_j,
+                           double* b_out, double* mz_next, double* cp_next, double thr_abs_sq,
+                           double thr_rel_sq, int n_groups_real, uint32_t* flags,
+                           cudaStream_t st) {
+  RDM_DISPATCH_DS(L.DS, (k_small_b<DS><<<L.n_groups(), kSmallThreads, 0, st>>>(
+                           L, partials, mz_j, b_out, mz_next, cp_next, thr_abs_sq, thr_rel_sq,
+                           n_groups_real, flags)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials,
+                              cudaStream_t st) {
+  RDM_DISPATCH(L, (k_final_gram<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
+                      L, reinterpret_cast<const T*>(psi), partials)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,
+                               cudaStream_t st) {
+  RDM_DISPATCH_DS(L.DS, (k_reduce_gram<DS><<<L.n_groups(), kSmallThreads, 0, st>>>(
+                           L, partials, gram)));
+  return cudaGetLastError();
+}
+
+}  // namespace rdm

@@ -1,0 +1,86 @@
+// Host-side structures behind the opaque ABI handles.
+#pragma once
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "rdm_internal.h"
+
+namespace rdm {
+
+// A model compiled to term descriptors (host copy).
+struct HostModel {
+  int n = 0, ns = 0;
+  double lambda = 1.0;
+  double hnorm = 0.0;  // sum of |coefficients|, an upper bound on ||H||_2
+  std::vector<FlipTerm> flips;
+  std::vector<DiagTerm> diags;
+};
+
+struct ServeState;
+
+// Launch statistics with CUDA-event timing on the launching stream.
+enum KernelKind {
+  kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply, kKNumKinds
+};
+struct Profiler {
+  bool on = false;
+  uint64_t launches[kKNumKinds] = {};
+  double ms[kKNumKinds] = {};
+  double bytes[kKNumKinds] = {};
+  std::vector<cudaEvent_t> events;  // pool, reused
+  std::vector<std::pair<int, int>> pending;  // (kind, index of the start event)
+  int next = 0;
+  static const char* name(int k);
+  void reset();
+  // Counts a launch; with `timed`, records events around it (call before/after).
+  int begin(int kind, cudaStream_t s, bool timed);
+  void end(int kind, int ev, cudaStream_t s, double bytes);
+  // After the stream has been synchronised: folds pending event pairs into ms.
+  void collect();
+  ~Profiler();
+};
+
+}  // namespace rdm
+
+struct rdm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  char* ws = nullptr;  // caller-attached workspace
+  size_t ws_bytes = 0;
+  std::unique_ptr<rdm::ServeState> serve;
+  rdm::Profiler prof;
+  rdm_ctx();
+  ~rdm_ctx();  // defined where ServeState is complete
+};
+
+struct rdm_ham {
+  rdm_ctx* ctx = nullptr;
+  rdm::HostModel model;
+  void* d_terms = nullptr;  // owns flips + diags
+  rdm::FlipTerm* d_flips = nullptr;
+  rdm::DiagTerm* d_diags = nullptr;
+};
+
+namespace rdm {
+
+void set_error(const char* fmt, ...);
+rdm_status compile_model(const rdm_model* m, HostModel* out);
+rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad);
+rdm_status check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,
+                               const rdm_opts* opts, const rdm_result* out);
+// Runs the whole estimator on stream s. ws/ws_bytes: scratch to carve from (NULL:
+// allocate stream-ordered from the device pool and release at the end).
+rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
+                         const double* betas, int n_beta, int n_v, int k, uint64_t seed,
+                         const rdm_opts* o, rdm_result* out, Profiler* prof);
+// Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
+size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int nbc);
+
+}  // namespace rdm

@@ -1,0 +1,141 @@
+// Internal declarations shared by the host translation units and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rdm.h"
+
+#ifdef __CUDACC__
+#define RDM_HD __host__ __device__
+#else
+#define RDM_HD
+#endif
+
+namespace rdm {
+
+// One off-diagonal term family with flip mask m: H[s ^ m, s] = c_odd if
+// popcount(s & m) is odd, c_even otherwise (eq. Ht). A pair (a, b) gives
+// m = bit(a)|bit(b), c_odd = s_ab (jx + jy) (anti-aligned spins), c_even =
+// s_ab (jx - jy) (aligned); a transverse field gives m = bit(q), c_odd = c_even = gx.
+struct FlipTerm {
+  uint32_t mask;
+  uint32_t pad;
+  double c_odd;
+  double c_even;
+};
+
+// One diagonal term: contributes c * (1 - 2*parity(s & mask)), i.e. c * Z_a Z_b
+// for a pair mask or c * Z_q for a single-site mask.
+struct DiagTerm {
+  uint32_t mask;
+  uint32_t pad;
+  double c;
+};
+
+// Geometry of a Krylov block in device memory. The B = d_s * n_v_pad columns are
+// split into n_slices slices of Bs columns; slice k is a contiguous D x Bs
+// state-major, vector-minor array starting at k * D * Bs. A thread owns VW
+// consecutive columns (VW / DS whole bath-vector groups) of one row; TPR = Bs/VW
+// threads cover a row of a slice.
+struct Layout {
+  int n_bits;      // N
+  int n_bath_bits; // N_b
+  int64_t D;       // 2^N
+  int DS;          // d_s
+  int B;           // columns (padded)
+  int Bs;          // columns per slice
+  int n_slices;
+  int VW;          // columns per thread
+  int TPR;         // threads per row of a slice
+  int gridx;       // blocks per slice in the row dimension
+  int precision;   // RDM_FP64 | RDM_FP32
+  int elem;        // bytes per element
+  RDM_HD int groups_per_slice() const { return Bs / DS; }
+  RDM_HD int n_groups() const { return B / DS; }
+  RDM_HD size_t block_bytes() const { return (size_t)D * (size_t)B * (size_t)elem; }
+};
+
+constexpr int kThreads = 256;
+
+// Number of float64 reduction values per bath-vector group for each kernel kind.
+inline int nv_full(int ds) { return ds * ds; }
+
+// Per-step coefficient arrays (device, float64), each [step][group][DS*DS]:
+//   mz   = M_j            (true Q_j = W_j M_j)
+//   cp   = -M_{j-1} B_{j-1}^T
+//   cw   = -M_j A_j
+struct StepCoefs {
+  double* mz;
+  double* cp;
+  double* cw;
+};
+
+// ---- launchers (kernels.cu) ------------------------------------------------
+
+// Zero vector blocks etc. are plain cudaMemsetAsync on the host side.
+
+// Gaussian bath-vector norms: inv_norm[l] = 1/||g_l|| for l < n_v (float64),
+// partials scratch of n_v * gx doubles.
+cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* partials,
+                               double* inv_norm, cudaStream_t st);
+
+// W = [I_s (x) v_l] for l < n_v_real, zero columns beyond.
+cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
+                              const double* inv_norm, void* W, cudaStream_t st);
+
+struct SpmmArgs {
+  const FlipTerm* flips;
+  int n_flip;
+  const DiagTerm* diags;
+  int n_diag;
+  const void* w;       // W_j
+  const void* w_prev;  // W_{j-1} (nullable)
+  void* z;             // output
+  const double* mz;    // [group][DS*DS] (nullable: identity, no mixing)
+  const double* cp;    // [group][DS*DS]
+  double* partials;    // PASS1 reduction partials (nullable)
+  // pass 2: psi accumulation
+  void* psi;           // [nb][block] (nullable)
+  const double* e;     // [nb][group][DS*DS]
+  int nb;
+  int psi_first;       // 1: psi = w E (no read)
+};
+
+enum SpmmMode { kModeApply = 0, kModePass1 = 1, kModePass2 = 2 };
+cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st);
+
+// W_{j+1} = Z + W_j Cw in place over Z; partials of W_{j+1}^T W_{j+1} if non-null.
+cudaError_t launch_orth(const Layout& L, const void* w, void* z, const double* cw,
+                        double* partials, cudaStream_t st);
+
+// Per-group small steps.
+cudaError_t launch_coef_init(const Layout& L, StepCoefs c1, cudaStream_t st);
+// After the SpMM: A_j and Cw_j from the P1 partials.
+cudaError_t launch_small_a(const Layout& L, const double* partials, const double* mz,
+                           double* a_out, double* cw_out, uint32_t* flags, cudaStream_t st);
+// After the orthogonalisation: B_j, M_{j+1}, Cp_{j+1} from the Gram partials.
+cudaError_t launch_small_b(const Layout& L, const double* partials, const double* mz_j,
+                           double* b_out, double* mz_next, double* cp_next, double thr_abs_sq,
+                           double thr_rel_sq, int n_groups_real, uint32_t* flags,
+                           cudaStream_t st);
+
+// Pass 2: W_{j+1} = Z + W_j Cw in place over Z, then psi_beta += W_{j+1} E_beta for
+// the nb betas of the chunk (psi blocks are consecutive, D*B elements apart).
+cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const double* cw, void* psi,
+                            const double* e, int nb, cudaStream_t st);
+// Pass 2 start: psi_beta = W_1 E_{1,beta}.
+cudaError_t launch_psi_init(const Layout& L, const void* w, void* psi, const double* e, int nb,
+                            cudaStream_t st);
+// Partials of psi^T psi per group for one psi block.
+cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials, cudaStream_t st);
+// Sum gram partials -> gram[group][DS*DS].
+cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,
+                               cudaStream_t st);
+
+constexpr uint32_t kFlagNonFinite = 0x100u;
+
+}  // namespace rdm

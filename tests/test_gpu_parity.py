@@ -1,0 +1,300 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: the SpMM index logic is bit-exact (integer-valued data in float64 makes
+every sum exact); rho* entries within 1e-10 (float64 path) or 1e-4 (float32 path)
+max-abs of the oracle on the same seeded bath vectors.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_form, exact, lanczos, post, rng as orng, spin_ops
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context(0)
+    yield c
+    c.close()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---------------------------------------------------------------- a1 + a3: SpMM
+
+def _integer_model(n, n_sys, seed, lam=1.0):
+    r = np.random.default_rng(seed)
+    spec = W.random_model(n, n_sys, seed, lam=lam)
+    for t in (spec.jx, spec.jy, spec.jz):
+        t[:] = np.round(t * 2)
+    spec.hz[:] = np.round(spec.hz * 4)
+    spec.gx[:] = np.round(spec.gx * 4)
+    del r
+    return spec
+
+
+@pytest.mark.parametrize("n,n_sys,seed", [(2, 1, 1), (5, 0, 2), (7, 1, 3), (9, 2, 4), (11, 1, 5)])
+@pytest.mark.parametrize("ncols", [2, 8, 16])
+def test_apply_bit_exact_index_logic_fp64(ctx, lib, n, n_sys, seed, ncols):
+    torch = _torch()
+    spec = _integer_model(n, n_sys, seed, lam=2.0)
+    h = spin_ops.dense_hamiltonian(spec)
+    x = np.random.default_rng(seed).integers(-3, 4, size=(1 << n, ncols)).astype(np.float64)
+    ham = lib.Hamiltonian(ctx, spec)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    ham.apply(xd, yd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(yd.cpu().numpy(), h @ x)
+
+
+@pytest.mark.parametrize("n,n_sys,seed", [(6, 1, 11), (10, 2, 12), (12, 0, 13)])
+@pytest.mark.parametrize("ncols,dtype", [(4, "float32"), (32, "float32"), (2, "float64"), (16, "float64")])
+def test_apply_real_couplings(ctx, lib, n, n_sys, seed, ncols, dtype):
+    torch = _torch()
+    spec = W.random_model(n, n_sys, seed)
+    h = spin_ops.dense_hamiltonian(spec)
+    x = np.random.default_rng(seed).normal(size=(1 << n, ncols))
+    ham = lib.Hamiltonian(ctx, spec)
+    tdt = getattr(torch, dtype)
+    xd = torch.from_numpy(x).to(tdt).cuda()
+    yd = torch.empty_like(xd)
+    ham.apply(xd, yd)
+    torch.cuda.synchronize()
+    ref = h @ xd.double().cpu().numpy()
+    tol = 1e-13 if dtype == "float64" else 1e-5
+    scale = np.abs(h).sum(axis=1).max() * np.abs(x).max()
+    assert np.abs(yd.double().cpu().numpy() - ref).max() <= tol * scale
+
+
+def test_apply_rejects_bad_columns(ctx, lib):
+    torch = _torch()
+    ham = lib.Hamiltonian(ctx, W.random_model(4, 1, 1))
+    x = torch.zeros((16, 6), dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.RdmError) as e:
+        ham.apply(x, torch.zeros_like(x))
+    assert e.value.status == lib.EINVAL
+
+
+# ---------------------------------------------------------------- a2: starting block
+
+@pytest.mark.parametrize("dist", ["rademacher", "gauss", "basis"])
+@pytest.mark.parametrize("n,n_sys,n_v", [(8, 1, 4), (9, 2, 8), (10, 0, 8)])
+def test_starting_block_matches_generator(ctx, lib, dist, n, n_sys, n_v):
+    torch = _torch()
+    spec = W.random_model(n, n_sys, 3)
+    ham = lib.Hamiltonian(ctx, spec)
+    d_s = 1 << n_sys
+    ref = np.hstack([orng.starting_block(d_s, orng.bath_vector(spec.d_b, l, 1234, dist)) for l in range(n_v)])
+    for dtype in ("float64", "float32"):
+        x = torch.empty((1 << n, d_s * n_v), dtype=getattr(torch, dtype), device="cuda")
+        ham.starting_block(x, n_v, 1234, dist)
+        torch.cuda.synchronize()
+        got = x.cpu().numpy()
+        want = ref.astype(dtype)
+        if dist == "gauss":
+            np.testing.assert_allclose(got, want, rtol=4e-15 if dtype == "float64" else 1.2e-7, atol=0)
+        else:
+            np.testing.assert_array_equal(got, want)
+
+
+# ---------------------------------------------------------------- a4: recurrence
+
+def test_lanczos_coefficients_match_oracle_fp64(ctx, lib):
+    spec = W.random_model(9, 2, 21)
+    ham = lib.Hamiltonian(ctx, spec)
+    k = 6
+    out = ham.estimate([1.0], n_v=3, k=k, seed=5, precision="fp64", dist="rademacher", full=True)
+    est = lanczos.Estimator(spec)
+    for l in range(3):
+        a_l, b_l = lanczos.lanczos_coefficients(est.apply_h, est.starting_block(l, 5, "rademacher"), k, est.hnorm)
+        np.testing.assert_allclose(out["t_a"][l], np.array(a_l), atol=1e-12)
+        np.testing.assert_allclose(out["t_b"][l], np.array(b_l), atol=1e-12)
+        for b in out["t_b"][l]:
+            assert np.all(np.tril(b, -1) == 0) and np.all(np.diag(b) >= 0)
+
+
+# ---------------------------------------------------------------- full estimator
+
+def test_c1_fp64_matches_oracle(ctx, lib):
+    c = W.config_c1()
+    ham = lib.Hamiltonian(ctx, c["spec"])
+    out = ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64", dist=c["dist"], full=True)
+    ref = lanczos.Estimator(c["spec"]).run(c["betas"], c["n_v"], c["k"], c["seed"], c["dist"])
+    assert abs(out["e0"] - ref["e0"]) < 1e-10
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["rho_quad"], ref["rho_quad"], atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], atol=1e-9, rtol=0)
+    np.testing.assert_allclose(out["gram_l"], ref["gram_l"], atol=1e-10 * np.abs(ref["gram_l"]).max())
+
+
+def test_c1_fp32_matches_oracle(ctx, lib):
+    c = W.config_c1()
+    ham = lib.Hamiltonian(ctx, c["spec"])
+    out = ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32", dist=c["dist"])
+    ref = lanczos.Estimator(c["spec"]).run(c["betas"], c["n_v"], c["k"], c["seed"], c["dist"])
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], atol=1e-3, rtol=0)
+
+
+@pytest.mark.parametrize("n,n_sys", [(7, 1), (8, 2), (6, 0)])
+def test_exhaustive_basis_equals_exact_partial_trace(ctx, lib, n, n_sys):
+    spec = W.random_model(n, n_sys, 40 + n)
+    betas = [0.0, 0.3, 1.0, 4.0]
+    ham = lib.Hamiltonian(ctx, spec)
+    k = (1 << n) // spec.d_s + 2
+    out = ham.estimate(betas, spec.d_b, k, 0, precision="fp64", dist="basis")
+    rho, lnz = exact.exact_rho(spec, betas)
+    np.testing.assert_allclose(out["rho"], rho, atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["rho_quad"], rho, atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], lnz, atol=1e-9, rtol=0)
+
+
+def test_xy_chain_matches_app_c_closed_form(ctx, lib):
+    n = 8
+    spec = W.xy_open_chain(n, 2, 1.0, 0.3)
+    betas = np.geomspace(0.1, 10.0, 7)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate(betas, spec.d_b, 70, 0, precision="fp64", dist="basis")
+    for i, beta in enumerate(betas):
+        np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(out["rho"][i])),
+                                   closed_form.rho_eigenvalues(n, beta, 1.0, 0.3), atol=TOL64)
+        assert abs(out["lnZ"][i] - closed_form.log_partition_chain(n, beta, 1.0, 0.3)) < 1e-9
+
+
+def test_uncoupled_model_gives_bare_system_gibbs(ctx, lib):
+    spec = W.random_model(10, 2, 50, lam=0.0)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([0.5, 2.0], 3, 60, 9, precision="fp64", dist="gauss")
+    for i, beta in enumerate([0.5, 2.0]):
+        np.testing.assert_allclose(out["rho"][i], exact.bare_system_gibbs(spec, beta), atol=TOL64)
+    out32 = ham.estimate([0.5, 2.0], 3, 60, 9, precision="fp32", dist="gauss")
+    for i, beta in enumerate([0.5, 2.0]):
+        np.testing.assert_allclose(out32["rho"][i], exact.bare_system_gibbs(spec, beta), atol=TOL32)
+
+
+def test_beta_zero_is_maximally_mixed(ctx, lib):
+    spec = W.random_model(9, 2, 51)
+    ham = lib.Hamiltonian(ctx, spec)
+    for prec in ("fp64", "fp32"):
+        out = ham.estimate([0.0], 4, 10, 3, precision=prec, dist="rademacher")
+        np.testing.assert_allclose(out["rho"][0], np.eye(4) / 4, atol=1e-15 if prec == "fp64" else 1e-7)
+
+
+def test_low_temperature_limit(ctx, lib):
+    spec = W.random_model(8, 1, 13)
+    solver = exact.ExactSolver(spec)
+    beta = 40.0 / (solver.evals[1] - solver.evals[0])
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([beta], spec.d_b, 160, 0, precision="fp64", dist="basis")
+    np.testing.assert_allclose(out["rho"][0], solver.ground_state_reduced(), atol=1e-6)
+
+
+@pytest.mark.parametrize("n_v,k", [(1, 1), (1, 7), (5, 12), (13, 20)])
+def test_ragged_sizes_match_oracle(ctx, lib, n_v, k):
+    spec = W.random_model(9, 1, 60 + n_v)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = [0.4, 1.7]
+    out = ham.estimate(betas, n_v, k, 77, precision="fp64", dist="gauss", full=True)
+    ref = lanczos.Estimator(spec).run(betas, n_v, k, 77, "gauss")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL64)
+    np.testing.assert_allclose(out["rho_quad"], ref["rho_quad"], atol=TOL64)
+    out32 = ham.estimate(betas, n_v, k, 77, precision="fp32", dist="gauss")
+    np.testing.assert_allclose(out32["rho"], ref["rho"], atol=TOL32)
+
+
+def test_tiny_system_two_sites(ctx, lib):
+    spec = W.xxz_chain(2, 1, 1.0, 0.5, 0.2, 1.0, periodic=False)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([1.0], 2, 3, 0, precision="fp64", dist="basis")
+    rho, _ = exact.exact_rho(spec, [1.0])
+    np.testing.assert_allclose(out["rho"], rho, atol=TOL64)
+
+
+def test_deterministic_bitwise(ctx, lib):
+    spec = W.long_range_tfim(14, 2, 1.5, 0.8)
+    ham = lib.Hamiltonian(ctx, spec)
+    a = ham.estimate([1.0, 2.0], 8, 30, 11, precision="fp32", dist="gauss", full=True)
+    b = ham.estimate([1.0, 2.0], 8, 30, 11, precision="fp32", dist="gauss", full=True)
+    for key in ("rho", "gram_l", "t_a", "t_b"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_post_processing_of_gpu_rho(ctx, lib):
+    c = W.config_c1()
+    ham = lib.Hamiltonian(ctx, c["spec"])
+    out = ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64")
+    for i, beta in enumerate(c["betas"]):
+        np.testing.assert_allclose(lib.mean_force(out["rho"][i], beta), post.mean_force(out["rho"][i], beta), atol=1e-12)
+        assert abs(lib.entropy(out["rho"][i]) - post.entropy(out["rho"][i])) < 1e-13
+
+
+# ---------------------------------------------------------------- c2-shaped, FP32 vs FP64 oracle
+
+def test_lr_tfim_small_fp32_vs_oracle(ctx, lib):
+    spec = W.long_range_tfim(12, 2, 1.5, 1.1)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([1.0], 32, 60, 20220418, precision="fp32", dist="gauss", full=True)
+    ref = lanczos.Estimator(spec).run([1.0], 32, 60, 20220418, "gauss")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32)
+    assert abs(out["lnZ"][0] - ref["lnZ"][0]) < 1e-3
+
+
+def test_c2_full_size_sampled_vector(ctx, lib):
+    """Full-size LR-TFIM N=22 in the benchmark's launch configuration (n_v=32, k=60,
+    float32): the first Lanczos coefficients of a sampled bath vector against the
+    oracle run on that vector alone, plus properties of the whole result."""
+    c = W.config_c2(0)
+    ham = lib.Hamiltonian(ctx, c["spec"])
+    out = ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32", dist=c["dist"], full=True)
+    steps = 4
+    for l in (0, 31):
+        est = lanczos.Estimator(c["spec"])
+        a_l, b_l = lanczos.lanczos_coefficients(est.apply_h, est.starting_block(l, c["seed"], c["dist"]),
+                                                steps, est.hnorm)
+        scale = est.hnorm
+        assert np.abs(out["t_a"][l, :steps] - np.array(a_l)).max() < 2e-5 * scale
+        assert np.abs(out["t_b"][l, :steps] - np.array(b_l)).max() < 2e-5 * scale
+    rho = out["rho"][0]
+    np.testing.assert_allclose(rho, rho.T, atol=1e-15)
+    assert abs(np.trace(rho) - 1) < 1e-12 and np.linalg.eigvalsh(rho).min() > 0
+    # Gram and quadrature forms agree while the float32 basis stays orthogonal enough.
+    np.testing.assert_allclose(out["rho"], out["rho_quad"], atol=TOL32)
+    # float32 against the float64 GPU path on the same seeds (the whole 32-vector sum).
+    out64 = ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64", dist=c["dist"])
+    np.testing.assert_allclose(out["rho"], out64["rho"], atol=TOL32)
+    assert abs(out["lnZ"][0] - out64["lnZ"][0]) < 1e-3 * abs(out64["lnZ"][0])
+
+
+# ---------------------------------------------------------------- serving
+
+def test_serving_alone_equals_in_mix(ctx, lib):
+    reqs = W.serving_requests(12, seed=5, n_min=8, n_max=14)
+    for r in reqs:  # keep the host eigen-step of the test small
+        r["n_v"] = min(r["n_v"], 16)
+        r["k"] = min(r["k"], 40)
+        r["betas"] = r["betas"][:12]
+    alone = []
+    for r in reqs:
+        ham = lib.Hamiltonian(ctx, r["spec"])
+        alone.append(ham.estimate(r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32"))
+        ham.close()
+    ctx.serve_start(8 << 30, max_inflight=4)
+    try:
+        tickets = [ctx.submit(r["spec"], r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32") for r in reqs]
+        for t, a in zip(tickets, alone):
+            res = ctx.wait(t)
+            np.testing.assert_array_equal(res["rho"], a["rho"])
+            np.testing.assert_array_equal(res["lnZ"], a["lnZ"])
+            lat, q = ctx.request_times(t)
+            assert lat >= q >= 0
+    finally:
+        ctx.serve_stop()

@@ -1,0 +1,107 @@
+"""Host-side checks of the C-ABI library (no GPU needed): symbols, host math, errors."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rdm():
+    from paper_2204_08147_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build_library()
+    from paper_2204_08147_gb300 import rdm as mod
+    return mod
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "rdm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rdm_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_function(rdm):
+    names = _declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(rdm._lib, n), f"{n} declared in include/rdm.h but not exported"
+
+
+def test_symmetric_eig_matches_numpy(rdm):
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 3, 7, 40, 121):
+        a = rng.normal(size=(n, n))
+        a = a + a.T
+        w, v = rdm.symmetric_eig(a)
+        np.testing.assert_allclose(w, np.linalg.eigvalsh(a), atol=1e-12 * max(1, np.abs(a).max()) * n)
+        np.testing.assert_allclose(v.T @ v, np.eye(n), atol=1e-12 * n)
+        np.testing.assert_allclose(a @ v, v * w, atol=1e-11 * n)
+
+
+def test_symmetric_eig_block_tridiagonal_and_degenerate(rdm):
+    rng = np.random.default_rng(1)
+    p, k = 4, 30
+    t = np.zeros((p * k, p * k))
+    for j in range(k):
+        a = rng.normal(size=(p, p))
+        t[j * p:(j + 1) * p, j * p:(j + 1) * p] = a + a.T
+        if j + 1 < k:
+            b = np.triu(rng.normal(size=(p, p)))
+            t[(j + 1) * p:(j + 2) * p, j * p:(j + 1) * p] = b
+            t[j * p:(j + 1) * p, (j + 1) * p:(j + 2) * p] = b.T
+    w, v = rdm.symmetric_eig(t)
+    np.testing.assert_allclose(w, np.linalg.eigvalsh(t), atol=1e-11)
+    np.testing.assert_allclose(t @ v, v * w, atol=1e-10)
+    # exactly degenerate spectrum and a decoupled zero block
+    d = np.diag([2.0, 2.0, 2.0, -1.0, 0.0, 0.0])
+    q, _ = np.linalg.qr(rng.normal(size=(6, 6)))
+    m = q @ d @ q.T
+    w, v = rdm.symmetric_eig(m)
+    np.testing.assert_allclose(w, [-1, 0, 0, 2, 2, 2], atol=1e-13)
+    np.testing.assert_allclose(v.T @ v, np.eye(6), atol=1e-13)
+
+
+def test_mean_force_and_entropy_match_oracle(rdm):
+    from oracle import post
+    rng = np.random.default_rng(2)
+    for d in (1, 2, 4, 8):
+        x = rng.normal(size=(d, d))
+        rho = x @ x.T + 0.1 * np.eye(d)
+        rho /= np.trace(rho)
+        beta = 0.7
+        np.testing.assert_allclose(rdm.mean_force(rho, beta), post.mean_force(rho, beta), atol=1e-12)
+        assert abs(rdm.entropy(rho) - post.entropy(rho)) < 1e-13
+    assert abs(rdm.entropy(np.eye(4) / 4) - np.log(4)) < 1e-14
+    assert abs(rdm.entropy(np.diag([1.0, 0.0]))) == 0.0
+
+
+def test_mean_force_rejects_non_positive(rdm):
+    with pytest.raises(rdm.RdmError) as e:
+        rdm.mean_force(np.diag([1.0, 0.0]), 1.0)
+    assert e.value.status == rdm.ENOTPD
+    with pytest.raises(rdm.RdmError) as e:
+        rdm.mean_force(np.eye(2) / 2, 0.0)
+    assert e.value.status == rdm.EINVAL
+
+
+def test_create_without_gpu_fails_cleanly(rdm):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+    h = C.c_void_p()
+    st = rdm._lib.rdm_create(C.byref(h), 0, None)
+    assert st in (rdm.ECUDA, rdm.EINVAL)
+    assert rdm.last_error()
+
+
+def test_header_enums_match_binding(rdm):
+    txt = open(os.path.join(ROOT, "include", "rdm.h")).read()
+    for name, val in [("RDM_EINVAL", rdm.EINVAL), ("RDM_ENOMEM", rdm.ENOMEM), ("RDM_ECUDA", rdm.ECUDA),
+                      ("RDM_ENOTPD", rdm.ENOTPD), ("RDM_EBUSY", rdm.EBUSY)]:
+        assert re.search(rf"{name}\s*=\s*{val}\b", txt), name
+    assert re.search(r"RDM_FP64\s*=\s*0", txt) and re.search(r"RDM_FP32\s*=\s*1", txt)
+    assert "RDM_RADEMACHER = 0, RDM_GAUSS = 1, RDM_BASIS = 2" in txt
