@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -96,6 +97,65 @@ rdm_status compile_model(const rdm_model* m, HostModel* out) {
   return RDM_OK;
 }
 
+// Groups the flip terms by m_high = mask >> kTileBits for the tiled SpMM.
+void make_term_image(const HostModel& h, TermImage* img) {
+  std::map<uint32_t, std::vector<const FlipTerm*>> groups;
+  groups[0];  // pattern 0 always exists
+  for (const FlipTerm& f : h.flips) groups[f.mask >> kTileBits].push_back(&f);
+  std::vector<uint32_t> pat_high, pat_flags, term_low;
+  std::vector<int> pat_start;
+  std::vector<double> term_odd, term_even;
+  for (auto& kv : groups) {
+    pat_high.push_back(kv.first);
+    pat_start.push_back((int)term_low.size());
+    uint32_t flags = 1u;
+    for (const FlipTerm* f : kv.second) {
+      const uint32_t low = f->mask & (uint32_t)(kTileRows - 1);
+      if (low) flags &= ~1u;
+      if (f->c_odd != 0.0) flags |= 2u;
+      if (f->c_even != 0.0) flags |= 4u;
+      term_low.push_back(low);
+      term_odd.push_back(f->c_odd);
+      term_even.push_back(f->c_even);
+    }
+    pat_flags.push_back(flags);
+  }
+  pat_start.push_back((int)term_low.size());
+  const bool tiled = h.n >= kTileBits;
+  img->n_pat = tiled ? (int)pat_high.size() : 0;
+  img->n_terms = tiled ? (int)term_low.size() : 0;
+  auto& b = img->bytes;
+  b.clear();
+  auto put = [&](const void* src, size_t n) -> size_t {
+    const size_t off = (b.size() + 15) / 16 * 16;
+    b.resize(off + std::max<size_t>(n, 16), 0);
+    if (n) std::memcpy(b.data() + off, src, n);
+    return off;
+  };
+  img->off_flips = put(h.flips.data(), h.flips.size() * sizeof(FlipTerm));
+  img->off_diags = put(h.diags.data(), h.diags.size() * sizeof(DiagTerm));
+  img->off_pat_high = put(pat_high.data(), pat_high.size() * 4);
+  img->off_pat_start = put(pat_start.data(), pat_start.size() * 4);
+  img->off_pat_flags = put(pat_flags.data(), pat_flags.size() * 4);
+  img->off_term_low = put(term_low.data(), term_low.size() * 4);
+  img->off_term_odd = put(term_odd.data(), term_odd.size() * 8);
+  img->off_term_even = put(term_even.data(), term_even.size() * 8);
+}
+
+void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
+  ham->d_flips = reinterpret_cast<FlipTerm*>(dev + img.off_flips);
+  ham->d_diags = reinterpret_cast<DiagTerm*>(dev + img.off_diags);
+  TiledTerms& t = ham->tiled;
+  t.n_pat = img.n_pat;
+  t.n_terms = img.n_terms;
+  t.pat_high = reinterpret_cast<const uint32_t*>(dev + img.off_pat_high);
+  t.pat_start = reinterpret_cast<const int*>(dev + img.off_pat_start);
+  t.pat_flags = reinterpret_cast<const uint32_t*>(dev + img.off_pat_flags);
+  t.term_low = reinterpret_cast<const uint32_t*>(dev + img.off_term_low);
+  t.term_odd = reinterpret_cast<const double*>(dev + img.off_term_odd);
+  t.term_even = reinterpret_cast<const double*>(dev + img.off_term_even);
+}
+
 // ---------------------------------------------------------------- layout
 
 static int ilog2_exact(int64_t x) {
@@ -136,6 +196,7 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
   int64_t gx = (l.D + rpb - 1) / rpb;
   const int64_t cap = std::max<int64_t>(1, 1216 / l.n_slices);
   l.gridx = (int)std::min(gx, cap);
+  if (layout_tiled(l)) l.gridx = spmm_tiled_grid(l);  // the tiled SpMM's blocks per slice
   *L = l;
   *n_v_pad = l.B / l.DS;
   return RDM_OK;
@@ -322,17 +383,12 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   h->ctx = ctx;
   h->model = std::move(hm);
   CK(cudaSetDevice(ctx->device));
-  const size_t fb = std::max<size_t>(1, h->model.flips.size()) * sizeof(FlipTerm);
-  const size_t db = std::max<size_t>(1, h->model.diags.size()) * sizeof(DiagTerm);
-  CK(cudaMalloc(&h->d_terms, fb + db));
-  h->d_flips = reinterpret_cast<FlipTerm*>(h->d_terms);
-  h->d_diags = reinterpret_cast<DiagTerm*>(reinterpret_cast<char*>(h->d_terms) + fb);
-  if (!h->model.flips.empty())
-    CK(cudaMemcpyAsync(h->d_flips, h->model.flips.data(), h->model.flips.size() * sizeof(FlipTerm),
-                       cudaMemcpyHostToDevice, ctx->stream));
-  if (!h->model.diags.empty())
-    CK(cudaMemcpyAsync(h->d_diags, h->model.diags.data(), h->model.diags.size() * sizeof(DiagTerm),
-                       cudaMemcpyHostToDevice, ctx->stream));
+  TermImage img;
+  make_term_image(h->model, &img);
+  CK(cudaMalloc(&h->d_terms, img.bytes.size()));
+  bind_terms(img, reinterpret_cast<char*>(h->d_terms), h.get());
+  CK(cudaMemcpyAsync(h->d_terms, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   *out = h.release();
   return RDM_OK;
@@ -555,6 +611,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   sa.n_flip = (int)hm.flips.size();
   sa.diags = ham->d_diags;
   sa.n_diag = (int)hm.diags.size();
+  sa.tiled = ham->tiled;
+  sa.err = d_flags + 1;
 
   const double blk_b = (double)L.block_bytes();
   // Launch wrappers: count every launch; time the block-sized kernels with events.
@@ -613,6 +671,10 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   CK(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   d2h += (ta.size() + tb.size() + mz.size()) * sizeof(double) + sizeof flags;
+  if (flags[1]) {
+    set_error("a bulk-copy wait in the SpMM kernel gave up (device error)");
+    return RDM_ECUDA;
+  }
   if (flags[0] & kFlagNonFinite) {
     set_error("non-finite Lanczos coefficient (overflow or invalid model)");
     return RDM_ENUMERIC;

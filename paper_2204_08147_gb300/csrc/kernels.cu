@@ -331,6 +331,330 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- tiled SpMM
+//
+// Same result as k_spmm, organised around 256-state tiles of one slice (256 rows x
+// 128 bytes = 32 KB) held in shared memory. The own tile and, one after another,
+// every partner tile tile ^ m_high that an active term needs are fetched with TMA
+// bulk copies (cp.async.bulk, completion on an mbarrier), double-buffered so the
+// next partner streams in while the current one is consumed. Every flip term is
+// then a shared-memory read. Blocks walk the slices in order and the tiles of a
+// slice with a grid stride, so all SMs work on neighbouring tiles of one slice and
+// partner tiles are mostly served from L2.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after a fixed number of polls (the copy engine never
+// needs more than microseconds; giving up means something is broken).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int n_diag) {
+  size_t off = 3 * (size_t)kTileRows * 128 + 64;  // tiles + barriers + control
+  off += 2 * 8 * 16 * sizeof(T);                  // mixing coefficients of the 8 lanes
+  off += (size_t)n_pat * 12 + 4;                   // pat_high, pat_flags, pat_start (+1)
+  off = (off + 15) / 16 * 16;
+  off += (size_t)n_terms * (4 + 2 * sizeof(T));
+  off = (off + 15) / 16 * 16;
+  off += (size_t)n_diag * (4 + sizeof(T));
+  return off + 64;
+}
+
+// First pattern >= p that tile tix needs (uniform patterns may be inactive).
+__device__ __forceinline__ int tiled_next(int p, int npat, uint32_t tix, const uint32_t* pat_high,
+                                          const uint32_t* pat_flags) {
+  for (; p < npat; ++p) {
+    const uint32_t f = pat_flags[p];
+    if (!(f & 1u)) return p;
+    const bool odd = (__popc(tix & pat_high[p]) & 1) != 0;
+    if (odd ? (f & 2u) : (f & 4u)) return p;
+  }
+  return p;
+}
+
+template <typename T, int DS, int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  constexpr int BS = 128 / (int)sizeof(T);  // elements per 128-byte row
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  constexpr int RPT = kTileRows / (kThreads / 8);  // rows per thread (8)
+  constexpr uint32_t kTileBytes = kTileRows * 128;
+  constexpr int kTileElems = kTileRows * BS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const TiledTerms& tt = a.tiled;
+  const int npat = tt.n_pat, nterm = tt.n_terms, nd = a.n_diag;
+  T* const tiles = reinterpret_cast<T*>(smem);
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem + 3 * (size_t)kTileBytes);
+  int* const ctl = reinterpret_cast<int*>(smem + 3 * (size_t)kTileBytes + 32);
+  T* const s_mz = reinterpret_cast<T*>(smem + 3 * (size_t)kTileBytes + 64);  // [8 lanes][NG*NVG]
+  T* const s_cp = s_mz + 8 * 16;
+  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(s_cp + 8 * 16);
+  uint32_t* const pat_flags = pat_high + npat;
+  int* const pat_start = reinterpret_cast<int*>(pat_flags + npat);
+  size_t off = (size_t)(reinterpret_cast<unsigned char*>(pat_start + npat + 1) - smem);
+  off = (off + 15) / 16 * 16;
+  T* const term_odd = reinterpret_cast<T*>(smem + off);
+  T* const term_even = term_odd + nterm;
+  uint32_t* const term_low = reinterpret_cast<uint32_t*>(term_even + nterm);
+  off += (size_t)nterm * (4 + 2 * sizeof(T));
+  off = (off + 15) / 16 * 16;
+  T* const dc = reinterpret_cast<T*>(smem + off);
+  uint32_t* const dmask = reinterpret_cast<uint32_t*>(dc + nd);
+
+  for (int i = threadIdx.x; i < npat; i += blockDim.x) {
+    pat_high[i] = tt.pat_high[i];
+    pat_flags[i] = tt.pat_flags[i];
+  }
+  for (int i = threadIdx.x; i <= npat; i += blockDim.x) pat_start[i] = tt.pat_start[i];
+  for (int i = threadIdx.x; i < nterm; i += blockDim.x) {
+    term_low[i] = tt.term_low[i];
+    term_odd[i] = (T)tt.term_odd[i];
+    term_even[i] = (T)tt.term_even[i];
+  }
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    dmask[i] = a.diags[i].mask;
+    dc[i] = (T)a.diags[i].c;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < 4; ++i) ctl[i] = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 7;  // 16-byte column chunk of a row
+  const int rg = threadIdx.x >> 3;   // row group 0..31: rows rg + 32*m
+  const int64_t tps = L.D >> kTileBits;
+  uint32_t phases = 0u;  // bit b: parity of buffer b's next completion
+  bool aborted = false;
+
+  for (int slice = 0; slice < L.n_slices && !aborted; ++slice) {
+    const size_t soff = (size_t)slice * L.D * BS;
+    const T* __restrict__ W = reinterpret_cast<const T*>(a.w) + soff;
+    const T* __restrict__ Wp = a.w_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
+    T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
+    __syncthreads();
+    if (threadIdx.x < 8 * NG * NVG) {  // this slice's mixing coefficients
+      const int ln = threadIdx.x / (NG * NVG), e = threadIdx.x % (NG * NVG);
+      const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
+      s_mz[ln * 16 + e] = (T)a.mz[gidx];
+      s_cp[ln * 16 + e] = Wp ? (T)a.cp[gidx] : (T)0;
+    }
+    __syncthreads();
+    const T* mz = s_mz + lane * 16;
+    const T* cp = s_cp + lane * 16;
+    T acc[NG * NVG];
+#pragma unroll
+    for (int e = 0; e < NG * NVG; ++e) acc[e] = (T)0;
+
+    for (int64_t tix = blockIdx.x; tix < tps; tix += gridDim.x) {
+      const uint32_t ut = (uint32_t)tix;
+      const uint32_t row0 = ut << kTileBits;
+      const int pfirst = tiled_next(1, npat, ut, pat_high, pat_flags);
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar[0], kTileBytes);
+        bulk_load(tiles, W + (size_t)row0 * BS, kTileBytes, &bar[0]);
+        ctl[1] = 1;
+        if (pfirst < npat) {
+          mbar_expect_tx(&bar[1], kTileBytes);
+          bulk_load(tiles + kTileElems, W + (size_t)((ut ^ pat_high[pfirst]) << kTileBits) * BS,
+                    kTileBytes, &bar[1]);
+          ctl[2] = 1;
+        }
+      }
+      const bool ok0 = mbar_wait(&bar[0], phases & 1u);
+      phases ^= 1u;
+      if (__syncthreads_or(!ok0)) {
+        aborted = true;
+        break;
+      }
+      if (threadIdx.x == 0) ctl[1] = 0;
+      const T* own = tiles;
+      T y[RPT][VW];
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        const int r = rg + 32 * m;
+        const uint32_t su = row0 + (uint32_t)r;
+        T dg = (T)0;
+        for (int t = lane; t < nd; t += 8) {
+          const T c = dc[t];
+          dg += (__popc(su & dmask[t]) & 1) ? -c : c;
+        }
+        dg += __shfl_xor_sync(0xffffffffu, dg, 4, 8);
+        dg += __shfl_xor_sync(0xffffffffu, dg, 2, 8);
+        dg += __shfl_xor_sync(0xffffffffu, dg, 1, 8);
+        T x[VW];
+        VecIO<T, VW>::ld_rw(x, own + r * BS + lane * VW);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[m][v] = dg * x[v];
+      }
+      // in-tile terms (pattern 0)
+      const int t1 = pat_start[1];
+      for (int t = pat_start[0]; t < t1; ++t) {
+        const uint32_t ml = term_low[t];
+        const T co = term_odd[t], ce = term_even[t];
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          const int r = rg + 32 * m;
+          const T c = (__popc(((uint32_t)r) & ml) & 1) ? co : ce;
+          if (c != (T)0) {
+            T xp[VW];
+            VecIO<T, VW>::ld_rw(xp, own + (r ^ (int)ml) * BS + lane * VW);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+          }
+        }
+      }
+      // partner tiles, double-buffered in buffers 1 and 2
+      int cur = 1;
+      for (int p = pfirst; p < npat;) {
+        const int pnext = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
+        __syncthreads();  // buffer 3-cur is no longer read
+        if (threadIdx.x == 0 && pnext < npat) {
+          const int nb = 3 - cur;
+          fence_proxy_async();
+          mbar_expect_tx(&bar[nb], kTileBytes);
+          bulk_load(tiles + nb * kTileElems, W + (size_t)((ut ^ pat_high[pnext]) << kTileBits) * BS,
+                    kTileBytes, &bar[nb]);
+          ctl[1 + nb] = 1;
+        }
+        const bool ok = mbar_wait(&bar[cur], (phases >> cur) & 1u);
+        phases ^= 1u << cur;
+        if (__syncthreads_or(!ok)) {
+          aborted = true;
+          break;
+        }
+        if (threadIdx.x == 0) ctl[1 + cur] = 0;
+        const T* P = tiles + cur * kTileElems;
+        const uint32_t hi_bits = pat_high[p] << kTileBits;
+        const int te = pat_start[p + 1];
+        for (int t = pat_start[p]; t < te; ++t) {
+          const uint32_t ml = term_low[t];
+          const uint32_t mfull = ml | hi_bits;
+          const T co = term_odd[t], ce = term_even[t];
+#pragma unroll
+          for (int m = 0; m < RPT; ++m) {
+            const int r = rg + 32 * m;
+            const T c = (__popc((row0 + (uint32_t)r) & mfull) & 1) ? co : ce;
+            if (c != (T)0) {
+              T xp[VW];
+              VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
+#pragma unroll
+              for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+            }
+          }
+        }
+        p = pnext;
+        cur = 3 - cur;
+      }
+      if (aborted) break;
+      // epilogue: Z = (H W) M + W_prev Cp, reductions
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        const int r = rg + 32 * m;
+        const size_t row = (size_t)(row0 + (uint32_t)r);
+        T z[VW];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int j = 0; j < DS; ++j) {
+            T t = (T)0;
+#pragma unroll
+            for (int i = 0; i < DS; ++i) t = fma(y[m][g * DS + i], mz[g * NVG + i * DS + j], t);
+            z[g * DS + j] = t;
+          }
+        if (Wp) {
+          T xp[VW];
+          VecIO<T, VW>::ld(xp, Wp + row * BS + lane * VW);
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int j = 0; j < DS; ++j) {
+              T t = z[g * DS + j];
+#pragma unroll
+              for (int i = 0; i < DS; ++i) t = fma(xp[g * DS + i], cp[g * NVG + i * DS + j], t);
+              z[g * DS + j] = t;
+            }
+        }
+        VecIO<T, VW>::st(Z + row * BS + lane * VW, z);
+        if (MODE == kModePass1) {
+          T x[VW];
+          VecIO<T, VW>::ld_rw(x, own + r * BS + lane * VW);
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int i = 0; i < DS; ++i)
+#pragma unroll
+              for (int j = 0; j < DS; ++j)
+                acc[g * NVG + i * DS + j] = fma(x[g * DS + i], z[g * DS + j], acc[g * NVG + i * DS + j]);
+        }
+      }
+      __syncthreads();  // own tile and partner buffers free for the next tile
+    }
+    if (aborted) break;
+    if (MODE == kModePass1) {
+      // Fixed-order block reduction into partials[slice][block][group].
+      double* red = reinterpret_cast<double*>(smem);  // tile buffers are free here
+      constexpr int NV = NG * NVG;
+#pragma unroll
+      for (int e = 0; e < NV; ++e) red[threadIdx.x * NV + e] = (double)acc[e];
+      __syncthreads();
+      if (threadIdx.x < 8) {
+        const int gs = BS / DS;
+        const size_t base = ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
+        for (int v = 0; v < NV; ++v) {
+          double sum = 0.0;
+          for (int rr = 0; rr < kThreads / 8; ++rr) sum += red[(rr * 8 + threadIdx.x) * NV + v];
+          a.partials[base + v] = sum;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (aborted && threadIdx.x == 0) {
+    atomicOr(a.err, 1u);
+    // Let any copy still in flight land before the block's shared memory is released.
+    for (int b = 0; b < 3; ++b)
+      if (ctl[1 + b]) mbar_wait(&bar[b], (phases >> b) & 1u);
+  }
+}
+
 // ---------------------------------------------------------------- orthogonalisation
 
 template <typename T, int DS, int VW, bool PASS1>
@@ -682,7 +1006,33 @@ cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_
   return cudaGetLastError();
 }
 
+template <typename T, int DS, int MODE>
+static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a, cudaStream_t st) {
+  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.n_diag);
+  static size_t configured = 0;
+  if (sm > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_spmm_tiled<T, DS, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    configured = sm;
+  }
+  k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kThreads, sm, st>>>(L, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st) {
+  if (mode != kModeApply && layout_tiled(L) && a.tiled.n_pat > 0) {
+    cudaError_t e = cudaSuccess;
+    if (L.precision == RDM_FP32) {
+      if (L.DS == 1) e = mode == kModePass1 ? launch_tiled<float, 1, kModePass1>(L, a, st) : launch_tiled<float, 1, kModePass2>(L, a, st);
+      else if (L.DS == 2) e = mode == kModePass1 ? launch_tiled<float, 2, kModePass1>(L, a, st) : launch_tiled<float, 2, kModePass2>(L, a, st);
+      else e = mode == kModePass1 ? launch_tiled<float, 4, kModePass1>(L, a, st) : launch_tiled<float, 4, kModePass2>(L, a, st);
+    } else {
+      if (L.DS == 1) e = mode == kModePass1 ? launch_tiled<double, 1, kModePass1>(L, a, st) : launch_tiled<double, 1, kModePass2>(L, a, st);
+      else e = mode == kModePass1 ? launch_tiled<double, 2, kModePass1>(L, a, st) : launch_tiled<double, 2, kModePass2>(L, a, st);
+    }
+    return e;
+  }
   RDM_DISPATCH(L, {
     const size_t sm = terms_smem<T>(a.n_flip, a.n_diag);
     if (mode == kModeApply)

@@ -63,9 +63,10 @@ struct rdm_ctx {
 struct rdm_ham {
   rdm_ctx* ctx = nullptr;
   rdm::HostModel model;
-  void* d_terms = nullptr;  // owns flips + diags
+  void* d_terms = nullptr;  // owns flips, diags and the tiled tables
   rdm::FlipTerm* d_flips = nullptr;
   rdm::DiagTerm* d_diags = nullptr;
+  rdm::TiledTerms tiled{};
 };
 
 namespace rdm {
@@ -80,6 +81,18 @@ rdm_status check_estimate_args(const rdm_ham* ham, const double* betas, int n_be
 rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
                          const double* betas, int n_beta, int n_v, int k, uint64_t seed,
                          const rdm_opts* o, rdm_result* out, Profiler* prof);
+// Host image of every device-side term table of a model (flips, diagonal terms and
+// the tiled SpMM's pattern tables), uploaded with one copy.
+struct TermImage {
+  std::vector<unsigned char> bytes;
+  size_t off_flips = 0, off_diags = 0, off_pat_high = 0, off_pat_start = 0, off_pat_flags = 0,
+         off_term_low = 0, off_term_odd = 0, off_term_even = 0;
+  int n_pat = 0, n_terms = 0;
+};
+void make_term_image(const HostModel& h, TermImage* img);
+// Points ham's device term pointers into `dev`, a device copy of img.bytes.
+void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
+
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int nbc);
 

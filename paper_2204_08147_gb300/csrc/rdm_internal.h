@@ -87,6 +87,25 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* part
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
                               const double* inv_norm, void* W, cudaStream_t st);
 
+// Flip terms grouped for the tiled SpMM. A tile is 2^kTileBits consecutive states
+// of one slice; a flip mask m splits into m_high = m >> kTileBits (which tile the
+// partner row lies in, relative to this one: tile ^ m_high) and m_low (the row
+// permutation inside that tile). Pattern p collects the terms with one m_high;
+// pattern 0 has m_high = 0 (in-tile terms). Flags: bit0 = every term has m_low = 0
+// (its activity is uniform over a tile), bit1/bit2 = some c_odd/c_even is nonzero.
+constexpr int kTileBits = 8;
+constexpr int kTileRows = 1 << kTileBits;
+struct TiledTerms {
+  int n_pat;
+  int n_terms;
+  const uint32_t* pat_high;   // [n_pat]
+  const int* pat_start;       // [n_pat + 1]
+  const uint32_t* pat_flags;  // [n_pat]
+  const uint32_t* term_low;   // [n_terms]
+  const double* term_odd;     // [n_terms]
+  const double* term_even;    // [n_terms]
+};
+
 struct SpmmArgs {
   const FlipTerm* flips;
   int n_flip;
@@ -103,7 +122,20 @@ struct SpmmArgs {
   const double* e;     // [nb][group][DS*DS]
   int nb;
   int psi_first;       // 1: psi = w E (no read)
+  TiledTerms tiled;    // n_pat = 0: not available
+  uint32_t* err;       // bit 0 set if a bulk-copy wait gave up
 };
+
+// True if the tiled SpMM applies to this layout (128-byte rows, 16-byte vectors,
+// at least one full tile per slice).
+inline bool layout_tiled(const Layout& L) {
+  return L.Bs * L.elem == 128 && L.VW * L.elem == 16 && L.n_bits >= kTileBits;
+}
+// Blocks per slice of the tiled SpMM.
+inline int spmm_tiled_grid(const Layout& L) {
+  const int64_t tps = L.D >> kTileBits;
+  return (int)(tps < 304 ? tps : 304);
+}
 
 enum SpmmMode { kModeApply = 0, kModePass1 = 1, kModePass2 = 2 };
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st);

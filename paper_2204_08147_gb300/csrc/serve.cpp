@@ -61,26 +61,20 @@ static rdm_status run_request(ServeState& S, Request& r, cudaStream_t st) {
   rdm_ham ham;
   ham.ctx = nullptr;
   ham.model = r.hm;
-  const size_t fb = std::max<size_t>(1, r.hm.flips.size()) * sizeof(FlipTerm);
-  const size_t db = std::max<size_t>(1, r.hm.diags.size()) * sizeof(DiagTerm);
+  TermImage img;
+  make_term_image(r.hm, &img);
   char* mem = nullptr;
-  const size_t off = (fb + db + 255) / 256 * 256;
+  const size_t off = (img.bytes.size() + 255) / 256 * 256;
   if (cudaMallocAsync(reinterpret_cast<void**>(&mem), off + r.footprint, st) != cudaSuccess) {
     cudaGetLastError();
     set_error("request %llu: device allocation of %zu bytes failed", (unsigned long long)r.id,
               off + r.footprint);
     return RDM_ENOMEM;
   }
-  ham.d_flips = reinterpret_cast<FlipTerm*>(mem);
-  ham.d_diags = reinterpret_cast<DiagTerm*>(mem + fb);
+  bind_terms(img, mem, &ham);
   rdm_status s = RDM_OK;
-  if (!r.hm.flips.empty() &&
-      cudaMemcpyAsync(ham.d_flips, r.hm.flips.data(), r.hm.flips.size() * sizeof(FlipTerm),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
-    s = RDM_ECUDA;
-  if (s == RDM_OK && !r.hm.diags.empty() &&
-      cudaMemcpyAsync(ham.d_diags, r.hm.diags.data(), r.hm.diags.size() * sizeof(DiagTerm),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(mem, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
     s = RDM_ECUDA;
   if (s == RDM_OK)
     s = estimate_impl(&ham, st, mem + off, r.footprint, r.betas.data(), (int)r.betas.size(), r.n_v,
