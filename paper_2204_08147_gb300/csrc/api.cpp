@@ -244,6 +244,7 @@ struct Arena {
 struct Plan {
   Layout L;
   int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
+  bool gauss;                         // Gaussian bath vectors are generated once into a buffer
 };
 
 static size_t plan_bytes(const Plan& p) {
@@ -261,6 +262,8 @@ static size_t plan_bytes(const Plan& p) {
   a.take<double>((size_t)p.nbc * ng * nv);
   a.take<double>((size_t)p.n_v_pad * 65);
   a.take<uint32_t>(4);
+  a.take<char>((size_t)L.D * L.elem);  // diagonal of H
+  if (p.gauss) a.take<char>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits) * L.elem);
   return a.off + 256;
 }
 
@@ -277,6 +280,7 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   p.k = k;
   p.n_beta = n_beta;
   p.nbc = 1;
+  p.gauss = o->vec_dist == RDM_GAUSS;
   if (plan_bytes(p) > avail) {
     set_error("estimate needs %zu bytes of device memory, %zu available", plan_bytes(p), avail);
     return RDM_ENOMEM;
@@ -291,8 +295,9 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   return RDM_OK;
 }
 
-size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int nbc) {
-  rdm_opts o{precision, RDM_RADEMACHER, RDM_GRAM, 0};
+size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
+                          int nbc) {
+  rdm_opts o{precision, dist, RDM_GRAM, 0};
   Plan p;
   if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
   p.nbc = std::max(1, std::min(nbc, n_beta));
@@ -481,7 +486,7 @@ extern "C" rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, u
     CK(cudaMallocAsync(&norms, sizeof(double) * (size_t)n_v * 65, s));
     CK(launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, norms + n_v, norms, s));
   }
-  CK(launch_init_block(L, dist, seed, n_v, norms, x, s));
+  CK(launch_init_block(L, dist, seed, n_v, norms, nullptr, x, s));
   if (norms) CK(cudaFreeAsync(norms, s));
   return RDM_OK;
 }
@@ -595,6 +600,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   double* d_gram = ar.take<double>((size_t)p.nbc * ng * nv);
   double* d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
   uint32_t* d_flags = ar.take<uint32_t>(4);
+  char* d_diag = ar.take<char>((size_t)L.D * L.elem);
+  char* d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
   const size_t cstride = (size_t)ng * nv;
   auto MZ = [&](int j) { return coef + (size_t)j * cstride; };                   // j = 1..k+1
   auto CP = [&](int j) { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; };
@@ -612,6 +619,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   sa.diags = ham->d_diags;
   sa.n_diag = (int)hm.diags.size();
   sa.tiled = ham->tiled;
+  sa.diag = d_diag;
   sa.err = d_flags + 1;
 
   const double blk_b = (double)L.block_bytes();
@@ -628,12 +636,17 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   };
   uint64_t h2d = 0, d2h = 0;
 
+  // Once per estimate: the diagonal of H and (Gaussian case) the bath vectors.
+  CK(counted([&] { return launch_diag(L, ham->d_diags, (int)hm.diags.size(), d_diag, s); }));
+  if (p.gauss) {
+    CK(counted([&] { return launch_gauss_norms(d_b, n_v, seed, d_norm + p.n_v_pad, d_norm, s); }));
+    if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
+    CK(counted([&] { return launch_gauss_fill(L, n_v, seed, d_norm, d_vbuf, s); }));
+  }
   auto init_block = [&](char* w) -> rdm_status {
-    if (o->vec_dist == RDM_GAUSS) {
-      CK(counted([&] { return launch_gauss_norms(d_b, n_v, seed, d_norm + p.n_v_pad, d_norm, s); }));
-      if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
-    }
-    CK(timed(kKInit, blk_b, [&] { return launch_init_block(L, o->vec_dist, seed, n_v, d_norm, w, s); }));
+    CK(timed(kKInit, blk_b, [&] {
+      return launch_init_block(L, o->vec_dist, seed, n_v, nullptr, d_vbuf, w, s);
+    }));
     return RDM_OK;
   };
 

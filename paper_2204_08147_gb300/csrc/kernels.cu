@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rdm_internal.h"
 
 namespace rdm {
@@ -152,7 +154,8 @@ __global__ void k_gauss_finish(int n_v, int gx, const double* part, double* inv_
 
 template <typename T, int DS, int VW>
 __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uint64_t seed,
-                                                         int nvr, const double* inv_norm, T* W) {
+                                                         int nvr, const double* inv_norm,
+                                                         const T* vbuf, T* W) {
   constexpr int NG = VW / DS;
   const int tpr = L.TPR, rpb = kThreads / tpr;
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
           const uint64_t z = splitmix64(seed, (((uint64_t)l << 40) | b) + 1);
           val = (z >> 63) ? -rad : rad;
         } else if (dist == RDM_GAUSS) {
-          val = gauss_raw(seed, (uint64_t)l, b) * inv_norm[l];
+          val = inv_norm ? gauss_raw(seed, (uint64_t)l, b) * inv_norm[l]
+                         : (double)vbuf[((size_t)l << L.n_bath_bits) + b];
         } else {
           val = (b == (uint64_t)l) ? 1.0 : 0.0;
         }
@@ -183,6 +187,38 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
       for (int a = 0; a < DS; ++a) v[g * DS + a] = (a == i) ? (T)val : (T)0;
     }
     VecIO<T, VW>::st(base + (size_t)s * L.Bs, v);
+  }
+}
+
+__global__ void k_gauss_fill(int64_t d_b, uint64_t seed, const double* inv_norm, int precision,
+                             void* vbuf) {
+  const int l = blockIdx.y;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < d_b;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const double v = gauss_raw(seed, (uint64_t)l, (uint64_t)b) * inv_norm[l];
+    if (precision == RDM_FP32)
+      reinterpret_cast<float*>(vbuf)[(size_t)l * d_b + b] = (float)v;
+    else
+      reinterpret_cast<double*>(vbuf)[(size_t)l * d_b + b] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_diag(int64_t D, const DiagTerm* diags, int nd, T* out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* c = reinterpret_cast<double*>(smem_raw);
+  uint32_t* m = reinterpret_cast<uint32_t*>(c + nd);
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    c[i] = diags[i].c;
+    m[i] = diags[i].mask;
+  }
+  __syncthreads();
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < D;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t su = (uint32_t)s;
+    double d = 0.0;
+    for (int t = 0; t < nd; ++t) d += (__popc(su & m[t]) & 1) ? -c[t] : c[t];
+    out[s] = (T)d;
   }
 }
 
@@ -382,15 +418,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Producer/consumer layout of the tiled SpMM: warp 8 issues TMA bulk copies into a
+// ring of kStages shared-memory slots; warps 0..7 consume them. A slot holds one
+// 32 KB tile (256 rows x 128 bytes) plus, for the own tile, its 256 diagonal
+// entries. Per tile the stage sequence is: own tile, each needed partner tile,
+// then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
+// empty barriers (count 8, one arrival per consumer warp) order the ring.
+constexpr int kStages = 5;
+constexpr int kConsumerWarps = 8;
+constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
+constexpr uint32_t kTileBytes = kTileRows * 128;
+constexpr uint32_t kSlotBytes = kTileBytes + 2048;
+
 template <typename T>
-__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int n_diag) {
-  size_t off = 3 * (size_t)kTileRows * 128 + 64;  // tiles + barriers + control
-  off += 2 * 8 * 16 * sizeof(T);                  // mixing coefficients of the 8 lanes
+__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms) {
+  size_t off = (size_t)kStages * kSlotBytes;
+  off += 2 * kStages * 8 + 64;                     // full/empty barriers, control
+  off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the 8 lanes
+  off += (size_t)kConsumerWarps * 8 * 16 * 8;      // reduction scratch
   off += (size_t)n_pat * 12 + 4;                   // pat_high, pat_flags, pat_start (+1)
   off = (off + 15) / 16 * 16;
   off += (size_t)n_terms * (4 + 2 * sizeof(T));
-  off = (off + 15) / 16 * 16;
-  off += (size_t)n_diag * (4 + sizeof(T));
   return off + 64;
 }
 
@@ -406,24 +454,48 @@ __device__ __forceinline__ int tiled_next(int p, int npat, uint32_t tix, const u
   return p;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Named barrier over the consumer warps with an OR of `pred` (bar.red.or).
+__device__ __forceinline__ bool consumers_sync_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "n"(kConsumerWarps * 32)
+      : "memory");
+  return r != 0;
+}
+// Bounded wait that also gives up when another thread has raised the abort flag.
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
 template <typename T, int DS, int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a) {
+__global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int BS = 128 / (int)sizeof(T);  // elements per 128-byte row
   constexpr int NG = VW / DS;
   constexpr int NVG = DS * DS;
-  constexpr int RPT = kTileRows / (kThreads / 8);  // rows per thread (8)
-  constexpr uint32_t kTileBytes = kTileRows * 128;
-  constexpr int kTileElems = kTileRows * BS;
+  constexpr int NV = NG * NVG;
+  constexpr int RPT = kTileRows / 32;  // rows per consumer thread (8)
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;
-  const int npat = tt.n_pat, nterm = tt.n_terms, nd = a.n_diag;
-  T* const tiles = reinterpret_cast<T*>(smem);
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(smem + 3 * (size_t)kTileBytes);
-  int* const ctl = reinterpret_cast<int*>(smem + 3 * (size_t)kTileBytes + 32);
-  T* const s_mz = reinterpret_cast<T*>(smem + 3 * (size_t)kTileBytes + 64);  // [8 lanes][NG*NVG]
+  const int npat = tt.n_pat, nterm = tt.n_terms;
+  unsigned char* const ring = smem;
+  uint64_t* const full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kSlotBytes);
+  uint64_t* const empty = full + kStages;
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
+  T* const s_mz = reinterpret_cast<T*>(smem + (size_t)kStages * kSlotBytes + 2 * kStages * 8 + 64);
   T* const s_cp = s_mz + 8 * 16;
-  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(s_cp + 8 * 16);
+  double* const red = reinterpret_cast<double*>(s_cp + 8 * 16);
+  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(red + kConsumerWarps * 8 * 16);
   uint32_t* const pat_flags = pat_high + npat;
   int* const pat_start = reinterpret_cast<int*>(pat_flags + npat);
   size_t off = (size_t)(reinterpret_cast<unsigned char*>(pat_start + npat + 1) - smem);
@@ -431,10 +503,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a
   T* const term_odd = reinterpret_cast<T*>(smem + off);
   T* const term_even = term_odd + nterm;
   uint32_t* const term_low = reinterpret_cast<uint32_t*>(term_even + nterm);
-  off += (size_t)nterm * (4 + 2 * sizeof(T));
-  off = (off + 15) / 16 * 16;
-  T* const dc = reinterpret_cast<T*>(smem + off);
-  uint32_t* const dmask = reinterpret_cast<uint32_t*>(dc + nd);
 
   for (int i = threadIdx.x; i < npat; i += blockDim.x) {
     pat_high[i] = tt.pat_high[i];
@@ -446,85 +514,128 @@ __global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a
     term_odd[i] = (T)tt.term_odd[i];
     term_even[i] = (T)tt.term_even[i];
   }
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    dmask[i] = a.diags[i].mask;
-    dc[i] = (T)a.diags[i].c;
-  }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
-    for (int i = 0; i < 4; ++i) ctl[i] = 0;
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumerWarps);
+    }
+    *abort_flag = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  const int lane = threadIdx.x & 7;  // 16-byte column chunk of a row
-  const int rg = threadIdx.x >> 3;   // row group 0..31: rows rg + 32*m
+  const int warp = threadIdx.x >> 5;
   const int64_t tps = L.D >> kTileBits;
-  uint32_t phases = 0u;  // bit b: parity of buffer b's next completion
-  bool aborted = false;
+  const bool has_prev = a.w_prev != nullptr;
 
-  for (int slice = 0; slice < L.n_slices && !aborted; ++slice) {
-    const size_t soff = (size_t)slice * L.D * BS;
-    const T* __restrict__ W = reinterpret_cast<const T*>(a.w) + soff;
-    const T* __restrict__ Wp = a.w_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
-    T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
-    __syncthreads();
-    if (threadIdx.x < 8 * NG * NVG) {  // this slice's mixing coefficients
-      const int ln = threadIdx.x / (NG * NVG), e = threadIdx.x % (NG * NVG);
-      const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
-      s_mz[ln * 16 + e] = (T)a.mz[gidx];
-      s_cp[ln * 16 + e] = Wp ? (T)a.cp[gidx] : (T)0;
-    }
-    __syncthreads();
-    const T* mz = s_mz + lane * 16;
-    const T* cp = s_cp + lane * 16;
-    T acc[NG * NVG];
-#pragma unroll
-    for (int e = 0; e < NG * NVG; ++e) acc[e] = (T)0;
-
-    for (int64_t tix = blockIdx.x; tix < tps; tix += gridDim.x) {
-      const uint32_t ut = (uint32_t)tix;
-      const uint32_t row0 = ut << kTileBits;
-      const int pfirst = tiled_next(1, npat, ut, pat_high, pat_flags);
-      if (threadIdx.x == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&bar[0], kTileBytes);
-        bulk_load(tiles, W + (size_t)row0 * BS, kTileBytes, &bar[0]);
-        ctl[1] = 1;
-        if (pfirst < npat) {
-          mbar_expect_tx(&bar[1], kTileBytes);
-          bulk_load(tiles + kTileElems, W + (size_t)((ut ^ pat_high[pfirst]) << kTileBits) * BS,
-                    kTileBytes, &bar[1]);
-          ctl[2] = 1;
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------ producer (one lane)
+    if ((threadIdx.x & 31) != 0) return;
+    uint32_t seq = 0;
+    bool stop = false;
+    for (int slice = 0; slice < L.n_slices && !stop; ++slice) {
+      const size_t soff = (size_t)slice * L.D * BS;
+      const T* W = reinterpret_cast<const T*>(a.w) + soff;
+      const T* Wp = has_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
+      for (int64_t tix = blockIdx.x; tix < tps && !stop; tix += gridDim.x) {
+        const uint32_t ut = (uint32_t)tix;
+        // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
+        int p = 0;
+        int kind = -1;
+        while (true) {
+          const int slot = (int)(seq % kStages);
+          if (seq >= (uint32_t)kStages &&
+              !ring_wait(&empty[slot], ((seq / kStages) - 1u) & 1u, abort_flag)) {
+            stop = true;
+            break;
+          }
+          unsigned char* dst = ring + (size_t)slot * kSlotBytes;
+          fence_proxy_async();
+          if (kind == -1) {
+            mbar_expect_tx(&full[slot], kTileBytes + kTileRows * (uint32_t)sizeof(T));
+            bulk_load(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot]);
+            bulk_load(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits), kTileRows * (uint32_t)sizeof(T),
+                      &full[slot]);
+          } else if (kind == -2) {
+            mbar_expect_tx(&full[slot], kTileBytes);
+            bulk_load(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot]);
+          } else {
+            mbar_expect_tx(&full[slot], kTileBytes);
+            bulk_load(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes, &full[slot]);
+          }
+          ++seq;
+          // next stage of this tile
+          if (kind == -2) break;
+          p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
+          if (p < npat) {
+            kind = p;
+          } else if (has_prev) {
+            kind = -2;
+          } else {
+            break;
+          }
         }
       }
-      const bool ok0 = mbar_wait(&bar[0], phases & 1u);
-      phases ^= 1u;
-      if (__syncthreads_or(!ok0)) {
+    }
+    if (stop) atomicOr(a.err, 1u);
+    return;
+  }
+
+  // -------------------------------------------------- consumers (8 warps)
+  const int lane = threadIdx.x & 7;  // 16-byte column chunk of a row
+  const int rg = threadIdx.x >> 3;   // row group 0..31: rows rg + 32*m
+  const bool leader = (threadIdx.x & 31) == 0;
+  uint32_t seq = 0;
+  bool aborted = false;
+  auto acquire = [&](const unsigned char*& slot_ptr) -> bool {
+    const int slot = (int)(seq % kStages);
+    if (!ring_wait(&full[slot], (seq / kStages) & 1u, abort_flag)) return false;
+    slot_ptr = ring + (size_t)slot * kSlotBytes;
+    return true;
+  };
+  auto release = [&]() {
+    __syncwarp();
+    if (leader) mbar_arrive(&empty[seq % kStages]);
+    ++seq;
+  };
+
+  for (int slice = 0; slice < L.n_slices; ++slice) {
+    const size_t soff = (size_t)slice * L.D * BS;
+    T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
+    consumers_sync_or(false);
+    if (threadIdx.x < 8 * NV) {  // this slice's mixing coefficients
+      const int ln = threadIdx.x / NV, e = threadIdx.x % NV;
+      const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
+      s_mz[ln * 16 + e] = (T)a.mz[gidx];
+      s_cp[ln * 16 + e] = has_prev ? (T)a.cp[gidx] : (T)0;
+    }
+    consumers_sync_or(false);
+    const T* mz = s_mz + lane * 16;
+    const T* cp = s_cp + lane * 16;
+    T acc[NV];
+#pragma unroll
+    for (int e = 0; e < NV; ++e) acc[e] = (T)0;
+
+    for (int64_t tix = blockIdx.x; tix < tps && !aborted; tix += gridDim.x) {
+      const uint32_t ut = (uint32_t)tix;
+      const uint32_t row0 = ut << kTileBits;
+      const unsigned char* sp;
+      // own tile: diagonal and in-tile terms
+      if (!acquire(sp)) {
         aborted = true;
         break;
       }
-      if (threadIdx.x == 0) ctl[1] = 0;
-      const T* own = tiles;
-      T y[RPT][VW];
+      const T* own = reinterpret_cast<const T*>(sp);
+      const T* dgt = reinterpret_cast<const T*>(sp + kTileBytes);
+      T xo[RPT][VW], y[RPT][VW];
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
         const int r = rg + 32 * m;
-        const uint32_t su = row0 + (uint32_t)r;
-        T dg = (T)0;
-        for (int t = lane; t < nd; t += 8) {
-          const T c = dc[t];
-          dg += (__popc(su & dmask[t]) & 1) ? -c : c;
-        }
-        dg += __shfl_xor_sync(0xffffffffu, dg, 4, 8);
-        dg += __shfl_xor_sync(0xffffffffu, dg, 2, 8);
-        dg += __shfl_xor_sync(0xffffffffu, dg, 1, 8);
-        T x[VW];
-        VecIO<T, VW>::ld_rw(x, own + r * BS + lane * VW);
+        VecIO<T, VW>::ld_rw(xo[m], own + r * BS + lane * VW);
+        const T dg = dgt[r];
 #pragma unroll
-        for (int v = 0; v < VW; ++v) y[m][v] = dg * x[v];
+        for (int v = 0; v < VW; ++v) y[m][v] = dg * xo[m][v];
       }
-      // in-tile terms (pattern 0)
       const int t1 = pat_start[1];
       for (int t = pat_start[0]; t < t1; ++t) {
         const uint32_t ml = term_low[t];
@@ -541,55 +652,51 @@ __global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a
           }
         }
       }
-      // partner tiles, double-buffered in buffers 1 and 2
-      int cur = 1;
-      for (int p = pfirst; p < npat;) {
-        const int pnext = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
-        __syncthreads();  // buffer 3-cur is no longer read
-        if (threadIdx.x == 0 && pnext < npat) {
-          const int nb = 3 - cur;
-          fence_proxy_async();
-          mbar_expect_tx(&bar[nb], kTileBytes);
-          bulk_load(tiles + nb * kTileElems, W + (size_t)((ut ^ pat_high[pnext]) << kTileBits) * BS,
-                    kTileBytes, &bar[nb]);
-          ctl[1 + nb] = 1;
-        }
-        const bool ok = mbar_wait(&bar[cur], (phases >> cur) & 1u);
-        phases ^= 1u << cur;
-        if (__syncthreads_or(!ok)) {
+      release();
+      // partner tiles
+      for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;
+           p = tiled_next(p + 1, npat, ut, pat_high, pat_flags)) {
+        if (!acquire(sp)) {
           aborted = true;
           break;
         }
-        if (threadIdx.x == 0) ctl[1 + cur] = 0;
-        const T* P = tiles + cur * kTileElems;
+        const T* P = reinterpret_cast<const T*>(sp);
         const uint32_t hi_bits = pat_high[p] << kTileBits;
         const int te = pat_start[p + 1];
         for (int t = pat_start[p]; t < te; ++t) {
           const uint32_t ml = term_low[t];
           const uint32_t mfull = ml | hi_bits;
           const T co = term_odd[t], ce = term_even[t];
+          if (co == ce) {
 #pragma unroll
-          for (int m = 0; m < RPT; ++m) {
-            const int r = rg + 32 * m;
-            const T c = (__popc((row0 + (uint32_t)r) & mfull) & 1) ? co : ce;
-            if (c != (T)0) {
+            for (int m = 0; m < RPT; ++m) {
+              const int r = rg + 32 * m;
               T xp[VW];
               VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
 #pragma unroll
-              for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+              for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+              const int r = rg + 32 * m;
+              const T c = (__popc((row0 + (uint32_t)r) & mfull) & 1) ? co : ce;
+              if (c != (T)0) {
+                T xp[VW];
+                VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
+#pragma unroll
+                for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+              }
             }
           }
         }
-        p = pnext;
-        cur = 3 - cur;
+        release();
       }
       if (aborted) break;
-      // epilogue: Z = (H W) M + W_prev Cp, reductions
+      // Z = (H W) M + W_prev Cp
+      T z[RPT][VW];
 #pragma unroll
-      for (int m = 0; m < RPT; ++m) {
-        const int r = rg + 32 * m;
-        const size_t row = (size_t)(row0 + (uint32_t)r);
-        T z[VW];
+      for (int m = 0; m < RPT; ++m)
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -597,62 +704,79 @@ __global__ void __launch_bounds__(kThreads, 2) k_spmm_tiled(Layout L, SpmmArgs a
             T t = (T)0;
 #pragma unroll
             for (int i = 0; i < DS; ++i) t = fma(y[m][g * DS + i], mz[g * NVG + i * DS + j], t);
-            z[g * DS + j] = t;
+            z[m][g * DS + j] = t;
           }
-        if (Wp) {
+      if (has_prev) {
+        if (!acquire(sp)) {
+          aborted = true;
+          break;
+        }
+        const T* Pp = reinterpret_cast<const T*>(sp);
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          const int r = rg + 32 * m;
           T xp[VW];
-          VecIO<T, VW>::ld(xp, Wp + row * BS + lane * VW);
+          VecIO<T, VW>::ld_rw(xp, Pp + r * BS + lane * VW);
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
             for (int j = 0; j < DS; ++j) {
-              T t = z[g * DS + j];
+              T t = z[m][g * DS + j];
 #pragma unroll
               for (int i = 0; i < DS; ++i) t = fma(xp[g * DS + i], cp[g * NVG + i * DS + j], t);
-              z[g * DS + j] = t;
+              z[m][g * DS + j] = t;
             }
         }
-        VecIO<T, VW>::st(Z + row * BS + lane * VW, z);
+        release();
+      }
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        const int r = rg + 32 * m;
+        VecIO<T, VW>::st(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z[m]);
         if (MODE == kModePass1) {
-          T x[VW];
-          VecIO<T, VW>::ld_rw(x, own + r * BS + lane * VW);
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
             for (int i = 0; i < DS; ++i)
 #pragma unroll
               for (int j = 0; j < DS; ++j)
-                acc[g * NVG + i * DS + j] = fma(x[g * DS + i], z[g * DS + j], acc[g * NVG + i * DS + j]);
+                acc[g * NVG + i * DS + j] = fma(xo[m][g * DS + i], z[m][g * DS + j], acc[g * NVG + i * DS + j]);
         }
       }
-      __syncthreads();  // own tile and partner buffers free for the next tile
     }
-    if (aborted) break;
+    // Per-slice flush of the W_j^T Z partial sums: fixed-order reduction over the
+    // 32 row groups (shuffles within a warp, then shared memory across warps).
+    const bool any_abort = consumers_sync_or(aborted);
+    if (any_abort) {
+      aborted = true;
+      break;
+    }
     if (MODE == kModePass1) {
-      // Fixed-order block reduction into partials[slice][block][group].
-      double* red = reinterpret_cast<double*>(smem);  // tile buffers are free here
-      constexpr int NV = NG * NVG;
+      double v[NV];
 #pragma unroll
-      for (int e = 0; e < NV; ++e) red[threadIdx.x * NV + e] = (double)acc[e];
-      __syncthreads();
+      for (int e = 0; e < NV; ++e) {
+        double x = (double)acc[e];
+        x += __shfl_xor_sync(0xffffffffu, x, 8);
+        x += __shfl_xor_sync(0xffffffffu, x, 16);
+        v[e] = x;
+      }
+      if ((threadIdx.x & 31) < 8) {
+#pragma unroll
+        for (int e = 0; e < NV; ++e) red[(warp * 8 + lane) * 16 + e] = v[e];
+      }
+      consumers_sync_or(false);
       if (threadIdx.x < 8) {
         const int gs = BS / DS;
         const size_t base = ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
-        for (int v = 0; v < NV; ++v) {
+        for (int e = 0; e < NV; ++e) {
           double sum = 0.0;
-          for (int rr = 0; rr < kThreads / 8; ++rr) sum += red[(rr * 8 + threadIdx.x) * NV + v];
-          a.partials[base + v] = sum;
+          for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * 8 + threadIdx.x) * 16 + e];
+          a.partials[base + e] = sum;
         }
       }
-      __syncthreads();
     }
   }
-  if (aborted && threadIdx.x == 0) {
-    atomicOr(a.err, 1u);
-    // Let any copy still in flight land before the block's shared memory is released.
-    for (int b = 0; b < 3; ++b)
-      if (ctl[1 + b]) mbar_wait(&bar[b], (phases >> b) & 1u);
-  }
+  if (aborted && threadIdx.x == 0) atomicOr(a.err, 1u);
 }
 
 // ---------------------------------------------------------------- orthogonalisation
@@ -686,7 +810,18 @@ __global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict
     for (int i = 0; i < DS; ++i)
 #pragma unroll
       for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
-  const int ngs = L.n_groups();
+  // pass 2: this slice's E coefficients for all nb betas, as T, in shared memory
+  extern __shared__ __align__(16) unsigned char smem_e[];
+  T* sE = reinterpret_cast<T*>(smem_e);
+  const int gs = L.groups_per_slice();
+  if (!PASS1) {
+    const int ngs = L.n_groups();
+    for (int i = threadIdx.x; i < nb * gs * NVG; i += blockDim.x) {
+      const int bi = i / (gs * NVG), rem = i % (gs * NVG);
+      sE[i] = (T)e[(size_t)bi * ngs * NVG + (size_t)slice * gs * NVG + rem];
+    }
+    __syncthreads();
+  }
   for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
     T x[VW], z[VW];
     VecIO<T, VW>::ld(x, W + (size_t)s * L.Bs);
@@ -713,15 +848,14 @@ __global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict
         T* P = psi + bi * bstride + soff + (size_t)s * L.Bs;
         T p[VW];
         VecIO<T, VW>::ld_rw(p, P);
-        const double* eb = e + (size_t)bi * ngs * NVG;
+        const T* eb = sE + ((size_t)bi * gs + (size_t)lane * NG) * NVG;
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
           for (int j = 0; j < DS; ++j) {
             T t = p[g * DS + j];
 #pragma unroll
-            for (int i = 0; i < DS; ++i)
-              t = fma(z[g * DS + i], (T)eb[(size_t)(g0 + g) * NVG + i * DS + j], t);
+            for (int i = 0; i < DS; ++i) t = fma(z[g * DS + i], eb[g * NVG + i * DS + j], t);
             p[g * DS + j] = t;
           }
         VecIO<T, VW>::st(P, p);
@@ -1000,15 +1134,35 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* part
 }
 
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
-                              const double* inv_norm, void* W, cudaStream_t st) {
+                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st) {
   RDM_DISPATCH(L, (k_init_block<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
-                      L, dist, seed, n_v_real, inv_norm, reinterpret_cast<T*>(W))));
+                      L, dist, seed, n_v_real, inv_norm, reinterpret_cast<const T*>(vbuf),
+                      reinterpret_cast<T*>(W))));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, const double* inv_norm,
+                              void* vbuf, cudaStream_t st) {
+  const int64_t d_b = int64_t(1) << L.n_bath_bits;
+  int gx = (int)std::min<int64_t>((d_b + 255) / 256, 1024);
+  k_gauss_fill<<<dim3(gx, n_v), 256, 0, st>>>(d_b, seed, inv_norm, L.precision, vbuf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void* diag,
+                        cudaStream_t st) {
+  const int gx = (int)std::min<int64_t>((L.D + 255) / 256, 4096);
+  const size_t sm = (size_t)std::max(n_diag, 1) * 12 + 16;
+  if (L.precision == RDM_FP32)
+    k_diag<float><<<gx, 256, sm, st>>>(L.D, diags, n_diag, reinterpret_cast<float*>(diag));
+  else
+    k_diag<double><<<gx, 256, sm, st>>>(L.D, diags, n_diag, reinterpret_cast<double*>(diag));
   return cudaGetLastError();
 }
 
 template <typename T, int DS, int MODE>
 static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a, cudaStream_t st) {
-  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.n_diag);
+  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms);
   static size_t configured = 0;
   if (sm > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_spmm_tiled<T, DS, MODE>,
@@ -1016,12 +1170,12 @@ static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a, cudaStream_t
     if (e != cudaSuccess) return e;
     configured = sm;
   }
-  k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kThreads, sm, st>>>(L, a);
+  k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st) {
-  if (mode != kModeApply && layout_tiled(L) && a.tiled.n_pat > 0) {
+  if (mode != kModeApply && layout_tiled(L) && a.tiled.n_pat > 0 && a.diag) {
     cudaError_t e = cudaSuccess;
     if (L.precision == RDM_FP32) {
       if (L.DS == 1) e = mode == kModePass1 ? launch_tiled<float, 1, kModePass1>(L, a, st) : launch_tiled<float, 1, kModePass2>(L, a, st);
@@ -1055,9 +1209,17 @@ cudaError_t launch_orth(const Layout& L, const void* w, void* z, const double* c
 
 cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const double* cw, void* psi,
                             const double* e, int nb, cudaStream_t st) {
-  RDM_DISPATCH(L, (k_orth<T, DS, VW, false><<<grid_of(L), kThreads, 0, st>>>(
-                      L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
-                      reinterpret_cast<T*>(psi), e, nb)));
+  RDM_DISPATCH(L, {
+    const size_t sm = (size_t)nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
+    if (sm > 48 * 1024) {
+      cudaError_t ce = cudaFuncSetAttribute(k_orth<T, DS, VW, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (ce != cudaSuccess) return ce;
+    }
+    k_orth<T, DS, VW, false><<<grid_of(L), kThreads, sm, st>>>(
+        L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
+        reinterpret_cast<T*>(psi), e, nb);
+  });
   return cudaGetLastError();
 }
 

@@ -94,6 +94,7 @@ void make_term_image(const HostModel& h, TermImage* img);
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
-size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int nbc);
+size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
+                          int nbc);
 
 }  // namespace rdm

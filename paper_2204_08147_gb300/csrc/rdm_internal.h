@@ -83,9 +83,13 @@ struct StepCoefs {
 cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* partials,
                                double* inv_norm, cudaStream_t st);
 
-// W = [I_s (x) v_l] for l < n_v_real, zero columns beyond.
+// W = [I_s (x) v_l] for l < n_v_real, zero columns beyond. Gaussian values come
+// from inv_norm (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T).
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
-                              const double* inv_norm, void* W, cudaStream_t st);
+                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st);
+// vbuf[l][b] = normalised Gaussian bath vector l (T = the layout's precision).
+cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, const double* inv_norm,
+                              void* vbuf, cudaStream_t st);
 
 // Flip terms grouped for the tiled SpMM. A tile is 2^kTileBits consecutive states
 // of one slice; a flip mask m splits into m_high = m >> kTileBits (which tile the
@@ -123,6 +127,7 @@ struct SpmmArgs {
   int nb;
   int psi_first;       // 1: psi = w E (no read)
   TiledTerms tiled;    // n_pat = 0: not available
+  const void* diag;    // [D] diagonal of H in the block's precision (tiled SpMM)
   uint32_t* err;       // bit 0 set if a bulk-copy wait gave up
 };
 
@@ -131,11 +136,15 @@ struct SpmmArgs {
 inline bool layout_tiled(const Layout& L) {
   return L.Bs * L.elem == 128 && L.VW * L.elem == 16 && L.n_bits >= kTileBits;
 }
-// Blocks per slice of the tiled SpMM.
+// Blocks per slice of the tiled SpMM (one persistent block per SM).
 inline int spmm_tiled_grid(const Layout& L) {
   const int64_t tps = L.D >> kTileBits;
-  return (int)(tps < 304 ? tps : 304);
+  return (int)(tps < 152 ? tps : 152);
 }
+
+// diag[s] = sum_t c_t (1 - 2 parity(s & m_t)), summed in float64, stored as T.
+cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void* diag,
+                        cudaStream_t st);
 
 enum SpmmMode { kModeApply = 0, kModePass1 = 1, kModePass2 = 2 };
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st);
