@@ -419,13 +419,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Producer/consumer layout of the tiled SpMM: warp 8 issues TMA bulk copies into a
-// ring of kStages shared-memory slots; warps 0..7 consume them. A slot holds one
+// ring of kStages shared-memory slots; the consumer warps read them. A slot holds one
 // 32 KB tile (256 rows x 128 bytes) plus, for the own tile, its 256 diagonal
 // entries. Per tile the stage sequence is: own tile, each needed partner tile,
 // then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
-// empty barriers (count 8, one arrival per consumer warp) order the ring.
+// empty barriers (one arrival per consumer warp) order the ring.
 constexpr int kStages = 5;
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 16;
 constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
 constexpr uint32_t kTileBytes = kTileRows * 128;
 constexpr uint32_t kSlotBytes = kTileBytes + 2048;
@@ -478,13 +478,14 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volati
 }
 
 template <typename T, int DS, int MODE>
-__global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
+__global__ void __launch_bounds__(kTiledThreads) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int BS = 128 / (int)sizeof(T);  // elements per 128-byte row
   constexpr int NG = VW / DS;
   constexpr int NVG = DS * DS;
   constexpr int NV = NG * NVG;
-  constexpr int RPT = kTileRows / 32;  // rows per consumer thread (8)
+  constexpr int RG = kConsumerWarps * 4;  // row groups of 8 lanes
+  constexpr int RPT = kTileRows / RG;     // rows per consumer thread
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;
   const int npat = tt.n_pat, nterm = tt.n_terms;
@@ -581,9 +582,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     return;
   }
 
-  // -------------------------------------------------- consumers (8 warps)
+  // -------------------------------------------------- consumers
   const int lane = threadIdx.x & 7;  // 16-byte column chunk of a row
-  const int rg = threadIdx.x >> 3;   // row group 0..31: rows rg + 32*m
+  const int rg = threadIdx.x >> 3;   // row group: rows rg + RG*m
   const bool leader = (threadIdx.x & 31) == 0;
   uint32_t seq = 0;
   bool aborted = false;
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       T xo[RPT][VW], y[RPT][VW];
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
-        const int r = rg + 32 * m;
+        const int r = rg + RG * m;
         VecIO<T, VW>::ld_rw(xo[m], own + r * BS + lane * VW);
         const T dg = dgt[r];
 #pragma unroll
@@ -640,15 +641,26 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       for (int t = pat_start[0]; t < t1; ++t) {
         const uint32_t ml = term_low[t];
         const T co = term_odd[t], ce = term_even[t];
+        if (co == ce) {
 #pragma unroll
-        for (int m = 0; m < RPT; ++m) {
-          const int r = rg + 32 * m;
-          const T c = (__popc(((uint32_t)r) & ml) & 1) ? co : ce;
-          if (c != (T)0) {
+          for (int m = 0; m < RPT; ++m) {
+            const int r = rg + RG * m;
             T xp[VW];
             VecIO<T, VW>::ld_rw(xp, own + (r ^ (int)ml) * BS + lane * VW);
 #pragma unroll
-            for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+            for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < RPT; ++m) {
+            const int r = rg + RG * m;
+            const T c = (__popc(((uint32_t)r) & ml) & 1) ? co : ce;
+            if (c != (T)0) {
+              T xp[VW];
+              VecIO<T, VW>::ld_rw(xp, own + (r ^ (int)ml) * BS + lane * VW);
+#pragma unroll
+              for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+            }
           }
         }
       }
@@ -670,7 +682,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           if (co == ce) {
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
-              const int r = rg + 32 * m;
+              const int r = rg + RG * m;
               T xp[VW];
               VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
 #pragma unroll
@@ -679,7 +691,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           } else {
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
-              const int r = rg + 32 * m;
+              const int r = rg + RG * m;
               const T c = (__popc((row0 + (uint32_t)r) & mfull) & 1) ? co : ce;
               if (c != (T)0) {
                 T xp[VW];
@@ -693,10 +705,19 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         release();
       }
       if (aborted) break;
-      // Z = (H W) M + W_prev Cp
-      T z[RPT][VW];
+      // Z = (H W) M + W_prev Cp, row by row, with the W_j^T Z partial sums
+      const T* Pp = nullptr;
+      if (has_prev) {
+        if (!acquire(sp)) {
+          aborted = true;
+          break;
+        }
+        Pp = reinterpret_cast<const T*>(sp);
+      }
 #pragma unroll
-      for (int m = 0; m < RPT; ++m)
+      for (int m = 0; m < RPT; ++m) {
+        const int r = rg + RG * m;
+        T z[VW];
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -704,35 +725,22 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             T t = (T)0;
 #pragma unroll
             for (int i = 0; i < DS; ++i) t = fma(y[m][g * DS + i], mz[g * NVG + i * DS + j], t);
-            z[m][g * DS + j] = t;
+            z[g * DS + j] = t;
           }
-      if (has_prev) {
-        if (!acquire(sp)) {
-          aborted = true;
-          break;
-        }
-        const T* Pp = reinterpret_cast<const T*>(sp);
-#pragma unroll
-        for (int m = 0; m < RPT; ++m) {
-          const int r = rg + 32 * m;
+        if (has_prev) {
           T xp[VW];
           VecIO<T, VW>::ld_rw(xp, Pp + r * BS + lane * VW);
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
             for (int j = 0; j < DS; ++j) {
-              T t = z[m][g * DS + j];
+              T t = z[g * DS + j];
 #pragma unroll
               for (int i = 0; i < DS; ++i) t = fma(xp[g * DS + i], cp[g * NVG + i * DS + j], t);
-              z[m][g * DS + j] = t;
+              z[g * DS + j] = t;
             }
         }
-        release();
-      }
-#pragma unroll
-      for (int m = 0; m < RPT; ++m) {
-        const int r = rg + 32 * m;
-        VecIO<T, VW>::st(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z[m]);
+        VecIO<T, VW>::st(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z);
         if (MODE == kModePass1) {
 #pragma unroll
           for (int g = 0; g < NG; ++g)
@@ -740,9 +748,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             for (int i = 0; i < DS; ++i)
 #pragma unroll
               for (int j = 0; j < DS; ++j)
-                acc[g * NVG + i * DS + j] = fma(xo[m][g * DS + i], z[m][g * DS + j], acc[g * NVG + i * DS + j]);
+                acc[g * NVG + i * DS + j] = fma(xo[m][g * DS + i], z[g * DS + j], acc[g * NVG + i * DS + j]);
         }
       }
+      if (has_prev) release();
     }
     // Per-slice flush of the W_j^T Z partial sums: fixed-order reduction over the
     // 32 row groups (shuffles within a warp, then shared memory across warps).
