@@ -425,7 +425,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
 // empty barriers (one arrival per consumer warp) order the ring.
 constexpr int kStages = 5;
-constexpr int kConsumerWarps = 16;
+constexpr int kConsumerWarps = 8;
 constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
 constexpr uint32_t kTileBytes = kTileRows * 128;
 constexpr uint32_t kSlotBytes = kTileBytes + 2048;
@@ -477,8 +477,23 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volati
   return false;
 }
 
+// In-tile flip whose partner rows belong to the same thread: the thread's rows
+// rg + 32 m (m = 0..7) form a subcube over tile bits 5..7, so a mask with no bit
+// below 5 maps row m to row m ^ K of the same thread (K = mask >> 5).
+template <int K, typename T, int VW, int RPT>
+__device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW], int rg, uint32_t ml,
+                                         T co, T ce) {
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    const uint32_t r = (uint32_t)(rg + 32 * m);
+    const T c = (co == ce) ? co : ((__popc(r & ml) & 1) ? co : ce);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xo[m ^ K][v], y[m][v]);
+  }
+}
+
 template <typename T, int DS, int MODE>
-__global__ void __launch_bounds__(kTiledThreads) k_spmm_tiled(Layout L, SpmmArgs a) {
+__global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int BS = 128 / (int)sizeof(T);  // elements per 128-byte row
   constexpr int NG = VW / DS;
@@ -611,8 +626,12 @@ __global__ void __launch_bounds__(kTiledThreads) k_spmm_tiled(Layout L, SpmmArgs
       s_cp[ln * 16 + e] = has_prev ? (T)a.cp[gidx] : (T)0;
     }
     consumers_sync_or(false);
-    const T* mz = s_mz + lane * 16;
-    const T* cp = s_cp + lane * 16;
+    T mz[NV], cp[NV];  // this lane's mixing coefficients, kept in registers
+#pragma unroll
+    for (int e = 0; e < NV; ++e) {
+      mz[e] = s_mz[lane * 16 + e];
+      cp[e] = s_cp[lane * 16 + e];
+    }
     T acc[NV];
 #pragma unroll
     for (int e = 0; e < NV; ++e) acc[e] = (T)0;
@@ -641,7 +660,17 @@ __global__ void __launch_bounds__(kTiledThreads) k_spmm_tiled(Layout L, SpmmArgs
       for (int t = pat_start[0]; t < t1; ++t) {
         const uint32_t ml = term_low[t];
         const T co = term_odd[t], ce = term_even[t];
-        if (co == ce) {
+        if (RPT == 8 && (ml & 31u) == 0u) {
+          switch (ml >> 5) {
+            case 1: reg_flip<1>(y, xo, rg, ml, co, ce); break;
+            case 2: reg_flip<2>(y, xo, rg, ml, co, ce); break;
+            case 3: reg_flip<3>(y, xo, rg, ml, co, ce); break;
+            case 4: reg_flip<4>(y, xo, rg, ml, co, ce); break;
+            case 5: reg_flip<5>(y, xo, rg, ml, co, ce); break;
+            case 6: reg_flip<6>(y, xo, rg, ml, co, ce); break;
+            default: reg_flip<7>(y, xo, rg, ml, co, ce); break;
+          }
+        } else if (co == ce) {
 #pragma unroll
           for (int m = 0; m < RPT; ++m) {
             const int r = rg + RG * m;
