@@ -92,11 +92,20 @@ typedef struct {
   double lambda_sb;
 } rdm_model;
 
+/* How the Gram form obtains Q_1..Q_k (Algorithm 1 returns them all):
+ *   RDM_PASSES_AUTO:      store them if k+1 Krylov blocks fit the device memory the
+ *                         call may use, else recompute;
+ *   RDM_PASSES_STORE:     keep every block of pass 1 (k+1 blocks of D x B);
+ *   RDM_PASSES_RECOMPUTE: keep 3 blocks and run the recurrence a second time with
+ *                         the stored coefficients (bit-identical blocks).
+ * Both give bit-identical results. */
+enum { RDM_PASSES_AUTO = 0, RDM_PASSES_STORE = 1, RDM_PASSES_RECOMPUTE = 2 };
+
 typedef struct {
   int precision; /* RDM_FP64 | RDM_FP32 */
   int vec_dist;  /* RDM_RADEMACHER | RDM_GAUSS | RDM_BASIS */
   int form;      /* RDM_GRAM | RDM_QUADRATURE */
-  int reserved;  /* must be 0 */
+  int passes;    /* RDM_PASSES_* */
 } rdm_opts;
 
 /* Outputs of rdm_estimate; every pointer is a caller-owned host array. rho is

@@ -245,17 +245,16 @@ struct Plan {
   Layout L;
   int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
   bool gauss;                         // Gaussian bath vectors are generated once into a buffer
+  bool store;                         // keep all k+1 Krylov blocks (no second pass)
 };
 
 static size_t plan_bytes(const Plan& p) {
   Arena a;  // dry run: only offsets
   const Layout& L = p.L;
   const size_t ng = L.n_groups(), nv = (size_t)L.DS * L.DS;
-  a.take<char>(L.block_bytes());
-  a.take<char>(L.block_bytes());
-  a.take<char>(L.block_bytes());
-  a.take<char>(L.block_bytes() * p.nbc);
-  a.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv);
+  a.take<char>(L.block_bytes() * (p.store ? (size_t)p.k + 1 : 3));
+  if (!p.store) a.take<char>(L.block_bytes() * p.nbc);
+  a.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv * 4);
   a.take<double>((size_t)(p.k + 2) * ng * nv * 3);
   a.take<double>((size_t)p.k * ng * nv * 2);
   a.take<double>((size_t)p.k * p.nbc * ng * nv);
@@ -281,6 +280,21 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   p.n_beta = n_beta;
   p.nbc = 1;
   p.gauss = o->vec_dist == RDM_GAUSS;
+  p.store = false;
+  if (o->passes != RDM_PASSES_RECOMPUTE) {
+    Plan q = p;
+    q.store = true;
+    q.nbc = n_beta;
+    if (gram_stored_max_betas(q.L, k) >= 1 && plan_bytes(q) <= avail) {
+      *out = q;
+      return RDM_OK;
+    }
+    if (o->passes == RDM_PASSES_STORE) {
+      set_error("storing %d Krylov blocks needs %zu bytes of device memory, %zu available", k + 1,
+                plan_bytes(q), avail);
+      return RDM_ENOMEM;
+    }
+  }
   if (plan_bytes(p) > avail) {
     set_error("estimate needs %zu bytes of device memory, %zu available", plan_bytes(p), avail);
     return RDM_ENOMEM;
@@ -296,11 +310,12 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
 }
 
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int nbc) {
-  rdm_opts o{precision, dist, RDM_GRAM, 0};
+                          int passes, int nbc) {
+  rdm_opts o{precision, dist, RDM_GRAM, passes == RDM_PASSES_STORE ? RDM_PASSES_STORE
+                                                                     : RDM_PASSES_RECOMPUTE};
   Plan p;
   if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
-  p.nbc = std::max(1, std::min(nbc, n_beta));
+  if (!p.store) p.nbc = std::max(1, std::min(nbc, n_beta));
   return plan_bytes(p);
 }
 
@@ -500,9 +515,11 @@ extern "C" rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v
     return RDM_EINVAL;
   }
   Plan p;
-  rdm_status st = make_plan(ham->model, n_beta, n_v, k, opts, SIZE_MAX, &p);
+  rdm_opts o = *opts;
+  if (o.passes == RDM_PASSES_AUTO) o.passes = RDM_PASSES_RECOMPUTE;  // the smaller of the two
+  rdm_status st = make_plan(ham->model, n_beta, n_v, k, &o, SIZE_MAX, &p);
   if (st != RDM_OK) return st;
-  p.nbc = 1;
+  if (!p.store) p.nbc = 1;
   *bytes = plan_bytes(p);
   return RDM_OK;
 }
@@ -589,10 +606,16 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   Arena ar;
   ar.base = ws;
   ar.cap = ws_bytes;
-  char* blk[3];
-  for (int i = 0; i < 3; ++i) blk[i] = ar.take<char>(L.block_bytes());
-  char* psi = ar.take<char>(L.block_bytes() * p.nbc);
-  double* partials = ar.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv);
+  const bool store = p.store;
+  const int nblk = store ? k + 1 : 3;
+  std::vector<char*> blk(nblk);
+  {
+    char* base = ar.take<char>(L.block_bytes() * nblk);
+    for (int i = 0; i < nblk; ++i) blk[i] = base + (size_t)i * L.block_bytes();
+  }
+  char* psi = store ? nullptr : ar.take<char>(L.block_bytes() * p.nbc);
+  const size_t pstride = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv;
+  double* partials = ar.take<double>(pstride * 4);
   double* coef = ar.take<double>((size_t)(k + 2) * ng * nv * 3);
   double* d_ta = ar.take<double>((size_t)k * ng * nv);
   double* d_tb = ar.take<double>((size_t)k * ng * nv);
@@ -674,7 +697,10 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     const int old_prev = prv;
     prv = cur;
     cur = nxt;
-    nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+    if (store)
+      nxt = cur + 1;
+    else
+      nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
   }
   std::vector<double> ta((size_t)k * cstride), tb((size_t)k * cstride), mz((size_t)(k + 1) * cstride);
   uint32_t flags[4];
@@ -757,9 +783,23 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
       }
     });
     if (!want_gram) continue;
-    // ---- pass 2: recompute W_j (bit-identical) and accumulate psi.
     CK(cudaMemcpyAsync(d_e, hE.data(), hE.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     h2d += hE.size() * sizeof(double);
+    if (store) {
+      // ---- psi = sum_j W_j E_j over the stored blocks, Gram fused.
+      const int gmax = gram_stored_max_betas(L, k);
+      for (int q = 0; q < nb; q += gmax) {
+        const int nq = std::min(gmax, nb - q);
+        CK(timed(kKGram, blk_b * k, [&] {
+          return launch_gram_stored(L, blk[0], k, d_e, p.nbc, q, nq, partials, pstride, s);
+        }));
+        for (int i = 0; i < nq; ++i)
+          CK(counted([&] {
+            return launch_reduce_gram(L, partials + (size_t)i * pstride, d_gram + (size_t)(q + i) * cstride, s);
+          }));
+      }
+    } else {
+    // ---- pass 2: recompute W_j (bit-identical) and accumulate psi.
     st = init_block(blk[0]);
     if (st != RDM_OK) return st;
     CK(timed(kKPsiInit, blk_b * (1 + nb), [&] { return launch_psi_init(L, blk[0], psi, d_e, nb, s); }));
@@ -785,6 +825,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     for (int bi = 0; bi < nb; ++bi) {
       CK(timed(kKGram, blk_b, [&] { return launch_final_gram(L, psi + (size_t)bi * L.block_bytes(), partials, s); }));
       CK(counted([&] { return launch_reduce_gram(L, partials, d_gram + (size_t)bi * cstride, s); }));
+    }
     }
     CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cstride * sizeof(double),
                        cudaMemcpyDeviceToHost, s));
@@ -845,7 +886,9 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
 static bool valid_opts(const rdm_opts* o) {
   return o && (o->precision == RDM_FP32 || o->precision == RDM_FP64) &&
          (o->vec_dist == RDM_RADEMACHER || o->vec_dist == RDM_GAUSS || o->vec_dist == RDM_BASIS) &&
-         (o->form == RDM_GRAM || o->form == RDM_QUADRATURE) && o->reserved == 0;
+         (o->form == RDM_GRAM || o->form == RDM_QUADRATURE) &&
+         (o->passes == RDM_PASSES_AUTO || o->passes == RDM_PASSES_STORE ||
+          o->passes == RDM_PASSES_RECOMPUTE);
 }
 
 rdm_status rdm::check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,

@@ -982,6 +982,89 @@ __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __re
   block_reduce_store<NG, NVG>(vals, tpr, partials, L.groups_per_slice());
 }
 
+// Stored-basis Gram: psi_beta = sum_{j=1..k} W_j E_{j,beta} row by row (the same
+// fma sequence as the two-pass accumulation, so the result is bit-identical) and
+// the partial sums of psi_beta^T psi_beta, for up to kGramBetas betas per launch.
+// W_j = W1 + (j-1) * D * B elements; e: [j][beta (stride nbs)][group][DS*DS].
+constexpr int kGramBetas = 4;
+
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __restrict__ W1, int k,
+                                                          const double* e, int nbs, int b0, int nb,
+                                                          double* partials, size_t pstride) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  extern __shared__ __align__(16) unsigned char smem_g[];
+  T* sE = reinterpret_cast<T*>(smem_g);  // [j][bi][gs][NVG]
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const int gs = L.groups_per_slice(), ng = L.n_groups();
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  const size_t bstride = (size_t)L.D * L.B;
+  for (int i = threadIdx.x; i < k * nb * gs * NVG; i += blockDim.x) {
+    const int j = i / (nb * gs * NVG);
+    const int rem = i % (nb * gs * NVG);
+    const int bi = rem / (gs * NVG), r2 = rem % (gs * NVG);
+    sE[i] = (T)e[(((size_t)j * nbs + b0 + bi) * ng) * NVG + (size_t)slice * gs * NVG + r2];
+  }
+  __syncthreads();
+  T acc[kGramBetas][NG][DS][DS];
+#pragma unroll
+  for (int bi = 0; bi < kGramBetas; ++bi)
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) acc[bi][g][i][j] = (T)0;
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    T psi[kGramBetas][VW];
+#pragma unroll
+    for (int bi = 0; bi < kGramBetas; ++bi)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) psi[bi][v] = (T)0;
+    for (int j = 0; j < k; ++j) {
+      T x[VW];
+      VecIO<T, VW>::ld(x, W1 + (size_t)j * bstride + soff + (size_t)s * L.Bs);
+#pragma unroll
+      for (int bi = 0; bi < kGramBetas; ++bi) {
+        if (bi >= nb) break;
+        const T* eb = sE + (((size_t)j * nb + bi) * gs + (size_t)lane * NG) * NVG;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int jj = 0; jj < DS; ++jj) {
+            T t = psi[bi][g * DS + jj];
+#pragma unroll
+            for (int i = 0; i < DS; ++i) t = fma(x[g * DS + i], eb[g * NVG + i * DS + jj], t);
+            psi[bi][g * DS + jj] = t;
+          }
+      }
+    }
+#pragma unroll
+    for (int bi = 0; bi < kGramBetas; ++bi)
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int i = 0; i < DS; ++i)
+#pragma unroll
+          for (int j = 0; j < DS; ++j)
+            acc[bi][g][i][j] = fma(psi[bi][g * DS + i], psi[bi][g * DS + j], acc[bi][g][i][j]);
+  }
+  for (int bi = 0; bi < nb; ++bi) {
+    double vals[NG * NVG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < DS; ++i)
+#pragma unroll
+        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[bi][g][i][j];
+    block_reduce_store<NG, NVG>(vals, tpr, partials + (size_t)bi * pstride, gs);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- per-group small steps
 
 constexpr int kSmallThreads = 128;
@@ -1296,6 +1379,27 @@ cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials
   RDM_DISPATCH(L, (k_final_gram<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
                       L, reinterpret_cast<const T*>(psi), partials)));
   return cudaGetLastError();
+}
+
+cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const double* e, int nbs,
+                               int b0, int nb, double* partials, size_t pstride, cudaStream_t st) {
+  RDM_DISPATCH(L, {
+    const size_t sm = (size_t)k * nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
+    if (sm > 48 * 1024) {
+      cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (ce != cudaSuccess) return ce;
+    }
+    k_gram_stored<T, DS, VW><<<grid_of(L), kThreads, sm, st>>>(
+        L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
+  });
+  return cudaGetLastError();
+}
+
+int gram_stored_max_betas(const Layout& L, int k) {
+  const size_t per = (size_t)k * L.groups_per_slice() * L.DS * L.DS * L.elem;
+  int nb = (int)((160 * 1024) / (per ? per : 1));
+  return std::max(0, std::min(nb, kGramBetas));
 }
 
 cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,

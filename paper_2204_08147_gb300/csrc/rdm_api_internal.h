@@ -95,6 +95,6 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int nbc);
+                          int passes, int nbc);
 
 }  // namespace rdm

@@ -173,6 +173,12 @@ cudaError_t launch_psi_init(const Layout& L, const void* w, void* psi, const dou
                             cudaStream_t st);
 // Partials of psi^T psi per group for one psi block.
 cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials, cudaStream_t st);
+// Stored-basis Gram for betas b0..b0+nb-1 of the E array (beta stride nbs):
+// partials for beta b0+i at partials + i*pstride.
+cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const double* e, int nbs,
+                               int b0, int nb, double* partials, size_t pstride, cudaStream_t st);
+// Betas one stored-basis Gram launch can take (0: the coefficients do not fit).
+int gram_stored_max_betas(const Layout& L, int k);
 // Sum gram partials -> gram[group][DS*DS].
 cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,
                                cudaStream_t st);

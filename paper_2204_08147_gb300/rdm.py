@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EBUSY, ENOTPD, ENOTFOUND = 0, -1,
 FP64, FP32 = 0, 1
 RADEMACHER, GAUSS, BASIS = 0, 1, 2
 GRAM, QUADRATURE = 0, 1
+PASSES_AUTO, PASSES_STORE, PASSES_RECOMPUTE = 0, 1, 2
 FLAG_DEFLATED, FLAG_PADDED = 1, 2
 
 _PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
@@ -40,7 +41,7 @@ class Model(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("vec_dist", C.c_int), ("form", C.c_int),
-                ("reserved", C.c_int)]
+                ("passes", C.c_int)]
 
 
 class Result(C.Structure):
@@ -130,8 +131,12 @@ class _ModelArrays:
                             _ptr(self.hz), _ptr(self.gx), float(spec.lambda_sb))
 
 
-def _opts(precision, dist, form) -> Opts:
-    return Opts(_PREC[precision], _DIST[dist], _FORM[form], 0)
+_PASSES = {"auto": PASSES_AUTO, "store": PASSES_STORE, "recompute": PASSES_RECOMPUTE,
+           PASSES_AUTO: PASSES_AUTO, PASSES_STORE: PASSES_STORE, PASSES_RECOMPUTE: PASSES_RECOMPUTE}
+
+
+def _opts(precision, dist, form, passes="auto") -> Opts:
+    return Opts(_PREC[precision], _DIST[dist], _FORM[form], _PASSES[passes])
 
 
 class _ResultArrays:
@@ -299,18 +304,19 @@ class Hamiltonian:
         except Exception:
             pass
 
-    def workspace_size(self, n_beta, n_v, k, precision="fp32", dist="rademacher", form="gram") -> int:
-        o = _opts(precision, dist, form)
+    def workspace_size(self, n_beta, n_v, k, precision="fp32", dist="rademacher", form="gram",
+                       passes="recompute") -> int:
+        o = _opts(precision, dist, form, passes)
         n = C.c_size_t()
         _check(_lib.rdm_workspace_size(self.h, int(n_beta), int(n_v), int(k), C.byref(o), C.byref(n)),
                "rdm_workspace_size")
         return n.value
 
     def estimate(self, betas, n_v, k, seed, precision="fp32", dist="rademacher", form="gram",
-                 full=False) -> dict:
+                 full=False, passes="auto") -> dict:
         b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
         res = _ResultArrays(len(b), n_v, k, self.d_s, full)
-        o = _opts(precision, dist, form)
+        o = _opts(precision, dist, form, passes)
         _check(_lib.rdm_estimate(self.h, _ptr(b), len(b), int(n_v), int(k), int(seed) & (2 ** 64 - 1),
                                  C.byref(o), C.byref(res.struct)), "rdm_estimate")
         return res.as_dict(o.form)

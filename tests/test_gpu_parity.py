@@ -298,3 +298,39 @@ def test_serving_alone_equals_in_mix(ctx, lib):
             assert lat >= q >= 0
     finally:
         ctx.serve_stop()
+
+
+# ---------------------------------------------------------------- storage modes
+
+def test_store_and_recompute_are_bit_identical(ctx, lib):
+    spec = W.long_range_tfim(14, 2, 1.5, 0.7)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = [0.3, 1.0, 2.5, 6.0, 9.0]
+    for prec in ("fp32", "fp64"):
+        a = ham.estimate(betas, 8, 30, 4, precision=prec, dist="gauss", full=True, passes="store")
+        b = ham.estimate(betas, 8, 30, 4, precision=prec, dist="gauss", full=True, passes="recompute")
+        for key in ("rho", "lnZ", "gram_l", "quad_l", "t_a", "t_b"):
+            np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_beta_chunks_in_a_small_workspace(ctx, lib):
+    """A caller workspace that holds one psi block forces one pass-2 sweep per beta."""
+    spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = list(W.beta_grid(5, 0.1, 10.0))
+    ref = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True, passes="store")
+    nbytes = ham.workspace_size(len(betas), 16, 25, precision="fp32", dist="rademacher")
+    ctx.attach_workspace(nbytes)
+    try:
+        got = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True)
+    finally:
+        ctx.detach_workspace()
+    for key in ("rho", "lnZ", "gram_l"):
+        np.testing.assert_array_equal(got[key], ref[key])
+    with pytest.raises(lib.RdmError) as e:  # storing every block does not fit that workspace
+        ctx.attach_workspace(nbytes)
+        try:
+            ham.estimate(betas, 16, 25, 8, precision="fp32", passes="store")
+        finally:
+            ctx.detach_workspace()
+    assert e.value.status == lib.ENOMEM
