@@ -1332,11 +1332,9 @@ cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const doubl
                             const double* e, int nb, cudaStream_t st) {
   RDM_DISPATCH(L, {
     const size_t sm = (size_t)nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
-    if (sm > 48 * 1024) {
-      cudaError_t ce = cudaFuncSetAttribute(k_orth<T, DS, VW, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (ce != cudaSuccess) return ce;
-    }
+    cudaError_t ce = cudaFuncSetAttribute(k_orth<T, DS, VW, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce != cudaSuccess) return ce;
     k_orth<T, DS, VW, false><<<grid_of(L), kThreads, sm, st>>>(
         L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
         reinterpret_cast<T*>(psi), e, nb);
@@ -1384,12 +1382,11 @@ cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials
 cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const double* e, int nbs,
                                int b0, int nb, double* partials, size_t pstride, cudaStream_t st) {
   RDM_DISPATCH(L, {
+    // static reduction scratch (block_reduce_store) + dynamic coefficients: opt in
     const size_t sm = (size_t)k * nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
-    if (sm > 48 * 1024) {
-      cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (ce != cudaSuccess) return ce;
-    }
+    cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce != cudaSuccess) return ce;
     k_gram_stored<T, DS, VW><<<grid_of(L), kThreads, sm, st>>>(
         L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
   });
