@@ -134,8 +134,10 @@ rdm_status rdm_create(rdm_ctx** out, int device, void* stream);
 void rdm_destroy(rdm_ctx* ctx);
 
 /* Attaches caller-owned device memory (e.g. a framework tensor) that rdm_estimate
- * carves its scratch from instead of allocating; NULL/0 detaches. The memory must
- * stay valid and unused by others while calls on this context run. */
+ * carves its scratch from; NULL/0 detaches. The memory must stay valid and unused
+ * by others while calls on this context run. Without an attached workspace the
+ * context allocates its own (sized for the call, grown when a later call needs
+ * more, kept between calls, freed by rdm_destroy). */
 rdm_status rdm_set_workspace(rdm_ctx* ctx, void* device_ptr, size_t bytes);
 
 /* Bytes of device scratch rdm_estimate needs for these sizes (3 Krylov blocks,

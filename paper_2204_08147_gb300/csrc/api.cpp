@@ -309,6 +309,12 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   return RDM_OK;
 }
 
+size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail) {
+  Plan p;
+  if (make_plan(h, n_beta, n_v, k, o, avail, &p) != RDM_OK) return 0;
+  return plan_bytes(p);
+}
+
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
                           int passes, int nbc) {
   rdm_opts o{precision, dist, RDM_GRAM, passes == RDM_PASSES_STORE ? RDM_PASSES_STORE
@@ -357,10 +363,9 @@ extern "C" void rdm_destroy(rdm_ctx* ctx) {
   if (!ctx) return;
   rdm_serve_stop(ctx);
   cudaSetDevice(ctx->device);
-  if (ctx->owns_stream) {
-    cudaStreamSynchronize(ctx->stream);
-    cudaStreamDestroy(ctx->stream);
-  }
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_ws) cudaFree(ctx->own_ws);
+  if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
 
@@ -573,7 +578,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
                          const rdm_opts* o, rdm_result* out, Profiler* prof) {
   const HostModel& hm = ham->model;
   Plan p;
-  rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws ? ws_bytes : SIZE_MAX, &p);
+  rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p);
   if (st != RDM_OK) return st;
   const Layout& L = p.L;
   const int ds = L.DS, nv = ds * ds, ng = L.n_groups();
@@ -582,27 +587,10 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     set_error("RDM_BASIS needs n_v <= d_b = %lld", (long long)d_b);
     return RDM_EINVAL;
   }
-  // Pass-2 chunk: as many psi blocks as fit in the device memory we may use.
-  bool own = false;
   if (!ws) {
-    size_t free_b = 0, total_b = 0;
-    CK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t usable = (size_t)(0.85 * (double)free_b);
-    st = make_plan(hm, n_beta, n_v, k, o, usable, &p);
-    if (st != RDM_OK) return st;
-    ws_bytes = plan_bytes(p);
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&ws), ws_bytes, s));
-    own = true;
+    set_error("internal: estimator called without a workspace");
+    return RDM_EINVAL;
   }
-  struct Free {
-    char* p;
-    cudaStream_t s;
-    bool own;
-    ~Free() {
-      if (own && p) cudaFreeAsync(p, s);
-    }
-  } guard{ws, s, own};
-
   Arena ar;
   ar.base = ws;
   ar.cap = ws_bytes;
@@ -913,7 +901,27 @@ extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta
                                    uint64_t seed, const rdm_opts* opts, rdm_result* out) {
   rdm_status st = check_estimate_args(ham, betas, n_beta, opts, out);
   if (st != RDM_OK) return st;
-  CK(cudaSetDevice(ham->ctx->device));
-  return estimate_impl(ham, ham->ctx->stream, ham->ctx->ws, ham->ctx->ws_bytes, betas, n_beta,
-                       n_v, k, seed, opts, out, &ham->ctx->prof);
+  rdm_ctx* ctx = ham->ctx;
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->ws)
+    return estimate_impl(ham, ctx->stream, ctx->ws, ctx->ws_bytes, betas, n_beta, n_v, k, seed, opts,
+                         out, &ctx->prof);
+  // Context-owned workspace: sized by what the plan needs given the device memory
+  // this context may use (85% of what is free plus what it already holds), kept
+  // for later calls.
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const size_t usable = (size_t)(0.85 * (double)(free_b + ctx->own_bytes));
+  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable);
+  if (need == 0) return RDM_ENOMEM;  // make_plan set the message
+  if (ctx->own_bytes < need) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->own_ws) CK(cudaFree(ctx->own_ws));
+    ctx->own_ws = nullptr;
+    ctx->own_bytes = 0;
+    CK(cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), need));
+    ctx->own_bytes = need;
+  }
+  return estimate_impl(ham, ctx->stream, ctx->own_ws, ctx->own_bytes, betas, n_beta, n_v, k, seed,
+                       opts, out, &ctx->prof);
 }

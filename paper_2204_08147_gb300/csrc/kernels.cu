@@ -988,7 +988,49 @@ __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __re
 // W_j = W1 + (j-1) * D * B elements; e: [j][beta (stride nbs)][group][DS*DS].
 constexpr int kGramBetas = 4;
 
-template <typename T, int DS, int VW>
+template <typename T, int DS>
+struct RowVec;  // DS consecutive coefficients as one shared-memory load
+template <>
+struct RowVec<float, 4> {
+  __device__ static void ld(float* r, const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+};
+template <>
+struct RowVec<float, 2> {
+  __device__ static void ld(float* r, const float* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  }
+};
+template <>
+struct RowVec<float, 1> {
+  __device__ static void ld(float* r, const float* p) { r[0] = *p; }
+};
+template <>
+struct RowVec<double, 4> {
+  __device__ static void ld(double* r, const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+  }
+};
+template <>
+struct RowVec<double, 2> {
+  __device__ static void ld(double* r, const double* p) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  }
+};
+template <>
+struct RowVec<double, 1> {
+  __device__ static void ld(double* r, const double* p) { r[0] = *p; }
+};
+
+// Each thread takes two rows at a time so every coefficient row read from shared
+// memory serves both.
+template <typename T, int DS, int VW, int NBT>
 __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __restrict__ W1, int k,
                                                           const double* e, int nbs, int b0, int nb,
                                                           double* partials, size_t pstride) {
@@ -1009,59 +1051,99 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
     sE[i] = (T)e[(((size_t)j * nbs + b0 + bi) * ng) * NVG + (size_t)slice * gs * NVG + r2];
   }
   __syncthreads();
-  T acc[kGramBetas][NG][DS][DS];
+  T acc[NBT][NG][DS][DS];
 #pragma unroll
-  for (int bi = 0; bi < kGramBetas; ++bi)
+  for (int bi = 0; bi < NBT; ++bi)
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int i = 0; i < DS; ++i)
 #pragma unroll
         for (int j = 0; j < DS; ++j) acc[bi][g][i][j] = (T)0;
-  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
-    T psi[kGramBetas][VW];
+  // Rows s and s + stride form a pair; the accumulation order per row is the same
+  // as for single rows (rows are visited in the same sequence per thread).
+  const int64_t stride = (int64_t)gridDim.x * rpb;
+  for (int64_t s0 = (int64_t)blockIdx.x * rpb + rs; s0 < L.D; s0 += 2 * stride) {
+    const int64_t s1 = s0 + stride;
+    const bool two = s1 < L.D;
+    T psi[2][NBT][VW];
 #pragma unroll
-    for (int bi = 0; bi < kGramBetas; ++bi)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int v = 0; v < VW; ++v) psi[bi][v] = (T)0;
-    for (int j = 0; j < k; ++j) {
-      T x[VW];
-      VecIO<T, VW>::ld(x, W1 + (size_t)j * bstride + soff + (size_t)s * L.Bs);
+      for (int bi = 0; bi < NBT; ++bi)
 #pragma unroll
-      for (int bi = 0; bi < kGramBetas; ++bi) {
+        for (int v = 0; v < VW; ++v) psi[h][bi][v] = (T)0;
+    auto step = [&](int j, const T (&x)[2][VW]) {
+#pragma unroll
+      for (int bi = 0; bi < NBT; ++bi) {
         if (bi >= nb) break;
         const T* eb = sE + (((size_t)j * nb + bi) * gs + (size_t)lane * NG) * NVG;
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
-          for (int jj = 0; jj < DS; ++jj) {
-            T t = psi[bi][g * DS + jj];
+          for (int i = 0; i < DS; ++i) {
+            T er[DS];
+            RowVec<T, DS>::ld(er, eb + g * NVG + i * DS);
 #pragma unroll
-            for (int i = 0; i < DS; ++i) t = fma(x[g * DS + i], eb[g * NVG + i * DS + jj], t);
-            psi[bi][g * DS + jj] = t;
+            for (int jj = 0; jj < DS; ++jj) {
+              psi[0][bi][g * DS + jj] = fma(x[0][g * DS + i], er[jj], psi[0][bi][g * DS + jj]);
+              psi[1][bi][g * DS + jj] = fma(x[1][g * DS + i], er[jj], psi[1][bi][g * DS + jj]);
+            }
           }
       }
+    };
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {  // four blocks' loads in flight before their use
+      T x[4][2][VW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T* wj = W1 + (size_t)(j + u) * bstride + soff;
+        VecIO<T, VW>::ld(x[u][0], wj + (size_t)s0 * L.Bs);
+        if (two) VecIO<T, VW>::ld(x[u][1], wj + (size_t)s1 * L.Bs);
+        else
+#pragma unroll
+          for (int v = 0; v < VW; ++v) x[u][1][v] = (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) step(j + u, x[u]);
+    }
+    for (; j < k; ++j) {
+      T x[2][VW];
+      const T* wj = W1 + (size_t)j * bstride + soff;
+      VecIO<T, VW>::ld(x[0], wj + (size_t)s0 * L.Bs);
+      if (two) VecIO<T, VW>::ld(x[1], wj + (size_t)s1 * L.Bs);
+      else
+#pragma unroll
+        for (int v = 0; v < VW; ++v) x[1][v] = (T)0;
+      step(j, x);
     }
 #pragma unroll
-    for (int bi = 0; bi < kGramBetas; ++bi)
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+#pragma unroll
+      for (int bi = 0; bi < NBT; ++bi)
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int i = 0; i < DS; ++i)
+#pragma unroll
+            for (int j = 0; j < DS; ++j)
+              acc[bi][g][i][j] = fma(psi[h][bi][g * DS + i], psi[h][bi][g * DS + j], acc[bi][g][i][j]);
+    }
+  }
+#pragma unroll
+  for (int bi = 0; bi < NBT; ++bi) {  // static indices keep acc in registers
+    if (bi < nb) {
+      double vals[NG * NVG];
 #pragma unroll
       for (int g = 0; g < NG; ++g)
 #pragma unroll
         for (int i = 0; i < DS; ++i)
 #pragma unroll
-          for (int j = 0; j < DS; ++j)
-            acc[bi][g][i][j] = fma(psi[bi][g * DS + i], psi[bi][g * DS + j], acc[bi][g][i][j]);
-  }
-  for (int bi = 0; bi < nb; ++bi) {
-    double vals[NG * NVG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g)
-#pragma unroll
-      for (int i = 0; i < DS; ++i)
-#pragma unroll
-        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[bi][g][i][j];
-    block_reduce_store<NG, NVG>(vals, tpr, partials + (size_t)bi * pstride, gs);
-    __syncthreads();
+          for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[bi][g][i][j];
+      block_reduce_store<NG, NVG>(vals, tpr, partials + (size_t)bi * pstride, gs);
+      __syncthreads();
+    }
   }
 }
 
@@ -1384,11 +1466,24 @@ cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const dou
   RDM_DISPATCH(L, {
     // static reduction scratch (block_reduce_store) + dynamic coefficients: opt in
     const size_t sm = (size_t)k * nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
-    cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW>,
+    cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, 1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce == cudaSuccess)
+      ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce == cudaSuccess)
+      ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, kGramBetas>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (ce != cudaSuccess) return ce;
-    k_gram_stored<T, DS, VW><<<grid_of(L), kThreads, sm, st>>>(
-        L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
+    if (nb == 1)
+      k_gram_stored<T, DS, VW, 1><<<grid_of(L), kThreads, sm, st>>>(
+          L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
+    else if (nb == 2)
+      k_gram_stored<T, DS, VW, 2><<<grid_of(L), kThreads, sm, st>>>(
+          L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
+    else
+      k_gram_stored<T, DS, VW, kGramBetas><<<grid_of(L), kThreads, sm, st>>>(
+          L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
   });
   return cudaGetLastError();
 }

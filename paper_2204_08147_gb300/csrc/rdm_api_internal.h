@@ -54,6 +54,8 @@ struct rdm_ctx {
   bool owns_stream = false;
   char* ws = nullptr;  // caller-attached workspace
   size_t ws_bytes = 0;
+  char* own_ws = nullptr;  // context-owned workspace, grown on demand, kept between calls
+  size_t own_bytes = 0;
   std::unique_ptr<rdm::ServeState> serve;
   rdm::Profiler prof;
   rdm_ctx();
@@ -76,8 +78,7 @@ rdm_status compile_model(const rdm_model* m, HostModel* out);
 rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad);
 rdm_status check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,
                                const rdm_opts* opts, const rdm_result* out);
-// Runs the whole estimator on stream s. ws/ws_bytes: scratch to carve from (NULL:
-// allocate stream-ordered from the device pool and release at the end).
+// Runs the whole estimator on stream s, carving its scratch from ws/ws_bytes.
 rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
                          const double* betas, int n_beta, int n_v, int k, uint64_t seed,
                          const rdm_opts* o, rdm_result* out, Profiler* prof);
@@ -94,6 +95,8 @@ void make_term_image(const HostModel& h, TermImage* img);
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
+// Bytes the estimator would use given `avail` bytes (0 if the sizes are invalid).
+size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail);
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
                           int passes, int nbc);
 
