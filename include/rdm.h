@@ -208,6 +208,25 @@ rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const void* x, voi
 rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, uint64_t seed,
                               int vec_dist, void* x);
 
+/* The starting block of rdm_starting_block, computed without allocating device
+ * memory. The paper has no counterpart: this is a service for callers that may not
+ * allocate device memory themselves, e.g. code running inside a framework whose
+ * caching allocator owns the device memory budget (a side cudaMalloc can fail or
+ * fragment it), or latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device. Same arguments, layout and result as
+ * rdm_starting_block; x is still caller-owned device memory.
+ * Scratch: the Gaussian vectors' norms use a fixed device array of this library
+ * (1024 * 65 float64 = 532,480 bytes), which every GPU that loads the library
+ * holds until the process exits. n_v may be at most 1024: larger n_v returns
+ * RDM_EINVAL. The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before any
+ * stream capture. All calls share the one array: calls whose device work overlaps
+ * (different streams, or different contexts on the same device) race on it and
+ * must be ordered by the caller. Each call writes every scratch entry it reads,
+ * so no clearing is needed between calls. */
+rdm_status rdm_starting_block_noalloc(rdm_ham* ham, int precision, int n_v, uint64_t seed,
+                                      int vec_dist, void* x);
+
 /* ---------------------------------------------------------------- post-processing
  * Host float64, no device work. rho is d_s x d_s row-major, symmetric. */
 

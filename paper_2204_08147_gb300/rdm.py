@@ -78,6 +78,7 @@ _sig("rdm_estimate", C.c_int, _vp, _dp, C.c_int, C.c_int, C.c_int, C.c_uint64, C
      C.POINTER(Result))
 _sig("rdm_apply_hamiltonian", C.c_int, _vp, C.c_int, _vp, _vp, C.c_int)
 _sig("rdm_starting_block", C.c_int, _vp, C.c_int, C.c_int, C.c_uint64, C.c_int, _vp)
+_sig("rdm_starting_block_noalloc", C.c_int, _vp, C.c_int, C.c_int, C.c_uint64, C.c_int, _vp)
 _sig("rdm_mean_force", C.c_int, _dp, C.c_int, C.c_double, _dp)
 _sig("rdm_entropy", C.c_int, _dp, C.c_int, _dp)
 _sig("rdm_symmetric_eig", C.c_int, C.c_int, _dp, _dp, _dp)
@@ -337,6 +338,15 @@ class Hamiltonian:
         assert x.is_contiguous() and x.shape[1] == self.d_s * n_v
         _check(_lib.rdm_starting_block(self.h, prec, int(n_v), int(seed) & (2 ** 64 - 1),
                                        _DIST[dist], _vp(x.data_ptr())), "rdm_starting_block")
+
+    def starting_block_noalloc(self, x, n_v, seed, dist="rademacher"):
+        """As starting_block, with the library's fixed scratch instead of an allocation."""
+        import torch
+        prec = FP32 if x.dtype == torch.float32 else FP64
+        assert x.is_contiguous() and x.shape[1] == self.d_s * n_v
+        _check(_lib.rdm_starting_block_noalloc(self.h, prec, int(n_v), int(seed) & (2 ** 64 - 1),
+                                               _DIST[dist], _vp(x.data_ptr())),
+               "rdm_starting_block_noalloc")
 
 
 # ---------------------------------------------------------------- host post-processing
