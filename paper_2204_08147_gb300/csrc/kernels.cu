@@ -21,6 +21,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 
 #include "rdm_internal.h"
 
@@ -1301,6 +1303,27 @@ size_t terms_smem(int nf, int nd) {
 
 }  // namespace
 
+// Raises a kernel's dynamic shared-memory limit to the device maximum (minus its
+// static shared memory), once per kernel. Setting it to the largest value once,
+// instead of to each launch's size, keeps concurrent host threads from lowering it
+// under one another's launches.
+static cudaError_t opt_in_smem(const void* func) {
+  static std::mutex mu;
+  static std::set<const void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(func)) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert(func);
+  return e;
+}
+
 // ---------------------------------------------------------------- dispatch
 
 #define RDM_DISPATCH(L, ...)                                         \
@@ -1366,13 +1389,8 @@ cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void
 template <typename T, int DS, int MODE>
 static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a, cudaStream_t st) {
   const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms);
-  static size_t configured = 0;
-  if (sm > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_spmm_tiled<T, DS, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    configured = sm;
-  }
+  cudaError_t e = opt_in_smem(reinterpret_cast<const void*>(k_spmm_tiled<T, DS, MODE>));
+  if (e != cudaSuccess) return e;
   k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
 }
@@ -1414,8 +1432,7 @@ cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const doubl
                             const double* e, int nb, cudaStream_t st) {
   RDM_DISPATCH(L, {
     const size_t sm = (size_t)nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
-    cudaError_t ce = cudaFuncSetAttribute(k_orth<T, DS, VW, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t ce = opt_in_smem(reinterpret_cast<const void*>(k_orth<T, DS, VW, false>));
     if (ce != cudaSuccess) return ce;
     k_orth<T, DS, VW, false><<<grid_of(L), kThreads, sm, st>>>(
         L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
@@ -1466,14 +1483,10 @@ cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const dou
   RDM_DISPATCH(L, {
     // static reduction scratch (block_reduce_store) + dynamic coefficients: opt in
     const size_t sm = (size_t)k * nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
-    cudaError_t ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, 1>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t ce = opt_in_smem(reinterpret_cast<const void*>(k_gram_stored<T, DS, VW, 1>));
+    if (ce == cudaSuccess) ce = opt_in_smem(reinterpret_cast<const void*>(k_gram_stored<T, DS, VW, 2>));
     if (ce == cudaSuccess)
-      ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, 2>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (ce == cudaSuccess)
-      ce = cudaFuncSetAttribute(k_gram_stored<T, DS, VW, kGramBetas>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ce = opt_in_smem(reinterpret_cast<const void*>(k_gram_stored<T, DS, VW, kGramBetas>));
     if (ce != cudaSuccess) return ce;
     if (nb == 1)
       k_gram_stored<T, DS, VW, 1><<<grid_of(L), kThreads, sm, st>>>(
