@@ -37,7 +37,7 @@ def build_library(verbose: bool = False, extra_nvcc: list[str] | None = None) ->
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     cu_flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-Xptxas", "-warn-spills"] + ARCH + (extra_nvcc or [])
-    cxx_flags = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
+    cxx_flags = ["-O3", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
                  "-I", os.path.join(cuda, "include")]
     jobs = []
     for name in sorted(os.listdir(CSRC)):

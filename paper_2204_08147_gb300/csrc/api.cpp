@@ -30,6 +30,8 @@ void set_error(const char* fmt, ...) {
 }
 
 bool sym_eig(int n, const double* a, double* w, double* vt);
+bool tdense_fT(int n, int p, const double* t, int n_beta, const double* betas, double* t_min,
+               double* c_out);
 
 #define CK(call)                                                                     \
   do {                                                                               \
@@ -531,12 +533,6 @@ extern "C" rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v
 
 namespace rdm {
 
-// Host part of the small dense step for one bath vector: eigenpairs of T_l.
-struct TEig {
-  std::vector<double> w, vt;  // vt: rows are eigenvectors
-  bool ok = true;
-};
-
 static void build_t(int ds, int k, int ng, int l, const std::vector<double>& ta,
                     const std::vector<double>& tb, std::vector<double>& t) {
   const int n = k * ds, nv = ds * ds;
@@ -707,37 +703,31 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     return RDM_ENUMERIC;
   }
 
-  // ---- small dense step (host float64): eigenpairs of each T_l, E0, f(T_l) E1.
+  // ---- small dense step (host float64): f(T_l) E1 for every beta (eq. fT) with the
+  // per-vector shift t_min(l); E0 = min_l t_min(l) (Sec. 3.2), then rescaling.
   const int n = k * ds;
-  std::vector<TEig> eig(n_v);
+  std::vector<double> cstore((size_t)n_v * n_beta * n * ds);
+  std::vector<double> tmin(n_v, 0.0);
+  std::vector<char> okv(n_v, 1);
   parallel_for(n_v, [&](int l) {
     std::vector<double> t;
     build_t(ds, k, ng, l, ta, tb, t);
-    eig[l].w.resize(n);
-    eig[l].vt.resize((size_t)n * n);
-    eig[l].ok = sym_eig(n, t.data(), eig[l].w.data(), eig[l].vt.data());
+    okv[l] = tdense_fT(n, ds, t.data(), n_beta, betas, &tmin[l], &cstore[(size_t)l * n_beta * n * ds]);
   });
   double e0 = INFINITY;
   for (int l = 0; l < n_v; ++l) {
-    if (!eig[l].ok) {
+    if (!okv[l]) {
       set_error("eigensolver did not converge on T_%d", l);
       return RDM_ENUMERIC;
     }
-    e0 = std::min(e0, eig[l].w[0]);
+    e0 = std::min(e0, tmin[l]);
   }
-  // c[beta][l] = V f(Theta) V[0:ds,:]^T  (k*ds x ds), quad = c^T c
-  auto coef_c = [&](int l, double beta, std::vector<double>& c) {
-    const TEig& E = eig[l];
-    c.assign((size_t)n * ds, 0.0);
-    for (int m = 0; m < n; ++m) {
-      const double f = std::exp(-0.5 * beta * (E.w[m] - e0));
-      const double* vm = &E.vt[(size_t)m * n];
-      for (int i = 0; i < ds; ++i) {
-        const double fv = f * vm[i];
-        if (fv == 0.0) continue;
-        for (int r = 0; r < n; ++r) c[(size_t)r * ds + i] += vm[r] * fv;
-      }
-    }
+  // c[beta][l] = exp(-beta (t_min(l) - E0)/2) * (the t_min(l)-shifted c)
+  auto coef_c = [&](int l, int bi, std::vector<double>& c) {
+    const double* src = &cstore[((size_t)l * n_beta + bi) * n * ds];
+    const double f = std::exp(-0.5 * betas[bi] * (tmin[l] - e0));
+    c.resize((size_t)n * ds);
+    for (size_t i = 0; i < c.size(); ++i) c[i] = f * src[i];
   };
   std::vector<double> quad((size_t)n_beta * n_v * nv, 0.0), gram((size_t)n_beta * n_v * nv, 0.0);
   const bool want_gram = true;
@@ -749,7 +739,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     parallel_for(n_v, [&](int l) {
       std::vector<double> c;
       for (int bi = 0; bi < nb; ++bi) {
-        coef_c(l, betas[b0 + bi], c);
+        coef_c(l, b0 + bi, c);
         double* q = &quad[((size_t)(b0 + bi) * n_v + l) * nv];
         for (int a = 0; a < ds; ++a)
           for (int b = 0; b < ds; ++b) {

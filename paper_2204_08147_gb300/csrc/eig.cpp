@@ -145,6 +145,155 @@ bool sym_eig(int n, const double* a_in, double* w, double* vt) {
   return true;
 }
 
+
+// f(T) E1 for every beta of a grid without forming eigenvectors.
+//
+// T = Q S Q^T (Householder, Q = H_0 H_1 ... kept as reflectors), S = U Theta U^T
+// (implicit QR, U = G_1 G_2 ... kept as rotations). Then
+//   c_beta = Q U exp(-beta (Theta - t_min)/2) U^T Q^T E1,
+// applied to the p columns of E1 only: O(n^3) for the reduction plus O(n^2 p) per
+// beta instead of the O(n^3) accumulation of full eigenvectors. The shift is this
+// matrix's own smallest eigenvalue t_min (no overflow); the caller rescales by
+// exp(-beta (t_min - E0)/2) once the common E0 is known.
+bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas, double* t_min,
+               double* c_out) {
+  std::vector<double> a(t_in, t_in + (size_t)n * n);
+  auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+  std::vector<double> hv((size_t)n * n, 0.0), hb(n, 0.0);  // reflector k: v in row k, beta
+  std::vector<double> p_(n), wv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double tail = 0.0;
+    for (int i = k + 2; i < n; ++i) tail += A(i, k) * A(i, k);
+    if (tail == 0.0) continue;
+    const double x0 = A(k + 1, k);
+    const double nrm = std::sqrt(tail + x0 * x0);
+    const double alpha = x0 > 0 ? -nrm : nrm;
+    double* v = &hv[(size_t)k * n];
+    v[k + 1] = x0 - alpha;
+    double vv = v[k + 1] * v[k + 1];
+    for (int i = k + 2; i < n; ++i) {
+      v[i] = A(i, k);
+      vv += v[i] * v[i];
+    }
+    const double beta = 2.0 / vv;
+    hb[k] = beta;
+    double vp = 0.0;
+    for (int i = k + 1; i < n; ++i) {
+      double sacc = 0.0;
+      const double* ai = &a[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) sacc += ai[j] * v[j];
+      p_[i] = beta * sacc;
+      vp += v[i] * p_[i];
+    }
+    const double kk = 0.5 * beta * vp;
+    for (int i = k + 1; i < n; ++i) wv[i] = p_[i] - kk * v[i];
+    for (int i = k + 1; i < n; ++i) {
+      double* ai = &a[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) ai[j] -= v[i] * wv[j] + wv[i] * v[j];
+    }
+    A(k + 1, k) = A(k, k + 1) = alpha;
+    for (int i = k + 2; i < n; ++i) A(i, k) = A(k, i) = 0.0;
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = A(i + 1, i);
+  // y = Q^T E1 (n x p, row-major): apply H_0, H_1, ... in order.
+  std::vector<double> y((size_t)n * p, 0.0);
+  for (int i = 0; i < p && i < n; ++i) y[(size_t)i * p + i] = 1.0;
+  auto apply_reflector = [&](int k, std::vector<double>& z) {
+    if (hb[k] == 0.0) return;
+    const double* v = &hv[(size_t)k * n];
+    for (int c = 0; c < p; ++c) {
+      double dot = 0.0;
+      for (int i = k + 1; i < n; ++i) dot += v[i] * z[(size_t)i * p + c];
+      dot *= hb[k];
+      for (int i = k + 1; i < n; ++i) z[(size_t)i * p + c] -= dot * v[i];
+    }
+  };
+  for (int k = 0; k + 2 < n; ++k) apply_reflector(k, y);
+  // Implicit QR with Wilkinson shift; each rotation is also applied to y (U^T y).
+  struct Rot {
+    int k;
+    double c, s;
+  };
+  std::vector<Rot> rots;
+  rots.reserve((size_t)4 * n * n / 2 + 16);
+  auto rot_t = [&](std::vector<double>& z, int k, double c, double sn) {  // G^T z
+    double* za = &z[(size_t)k * p];
+    double* zb = &z[(size_t)(k + 1) * p];
+    for (int q = 0; q < p; ++q) {
+      const double u = za[q], w = zb[q];
+      za[q] = c * u - sn * w;
+      zb[q] = sn * u + c * w;
+    }
+  };
+  const double eps = DBL_EPSILON;
+  int hi = n - 1;
+  long iters = 0;
+  const long max_iters = 60L * n;
+  while (hi > 0) {
+    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi])) ||
+        std::fabs(e[hi - 1]) < DBL_MIN) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo])) &&
+           std::fabs(e[lo - 1]) >= DBL_MIN)
+      --lo;
+    if (++iters > max_iters) return false;
+    const double delta = 0.5 * (d[hi - 1] - d[hi]);
+    const double eh = e[hi - 1];
+    const double denom = delta + (delta >= 0 ? 1.0 : -1.0) * std::hypot(delta, eh);
+    const double mu = d[hi] - eh * eh / denom;
+    double x = d[lo] - mu;
+    double z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r;
+      const double sn = r == 0.0 ? 0.0 : -z / r;
+      if (k > lo) e[k - 1] = r;
+      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+      d[k] = c * c * dk - 2.0 * c * sn * ek + sn * sn * dk1;
+      d[k + 1] = sn * sn * dk + 2.0 * c * sn * ek + c * c * dk1;
+      e[k] = c * sn * (dk - dk1) + (c * c - sn * sn) * ek;
+      if (k + 1 < hi) {
+        x = e[k];
+        z = -sn * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+      }
+      rots.push_back(Rot{k, c, sn});
+      rot_t(y, k, c, sn);
+    }
+  }
+  double tmin = d[0];
+  for (int i = 1; i < n; ++i) tmin = std::min(tmin, d[i]);
+  *t_min = tmin;
+  // Per beta: z = exp(-beta (theta - t_min)/2) * y, then U z (rotations in reverse,
+  // untransposed), then Q z (reflectors in reverse).
+  std::vector<double> zb((size_t)n * p);
+  for (int b = 0; b < n_beta; ++b) {
+    for (int m = 0; m < n; ++m) {
+      const double f = std::exp(-0.5 * betas[b] * (d[m] - tmin));
+      for (int q = 0; q < p; ++q) zb[(size_t)m * p + q] = f * y[(size_t)m * p + q];
+    }
+    for (size_t r = rots.size(); r-- > 0;) {
+      const Rot& g = rots[r];
+      double* za = &zb[(size_t)g.k * p];
+      double* zc = &zb[(size_t)(g.k + 1) * p];
+      for (int q = 0; q < p; ++q) {
+        const double u = za[q], w = zc[q];
+        za[q] = g.c * u + g.s * w;
+        zc[q] = -g.s * u + g.c * w;
+      }
+    }
+    for (int k = n - 3; k >= 0; --k) apply_reflector(k, zb);
+    std::copy(zb.begin(), zb.end(), c_out + (size_t)b * n * p);
+  }
+  return true;
+}
+
 }  // namespace rdm
 
 using rdm::set_error;
