@@ -106,6 +106,9 @@ typedef struct {
   int vec_dist;  /* RDM_RADEMACHER | RDM_GAUSS | RDM_BASIS */
   int form;      /* RDM_GRAM | RDM_QUADRATURE */
   int passes;    /* RDM_PASSES_* */
+  int64_t first_vector; /* bath vectors l = first_vector .. first_vector+n_v-1 of the
+                           seeded sequence (0 for a whole run; a shard of a run split
+                           over GPUs starts further in, eq. trace_est is a sum over l) */
 } rdm_opts;
 
 /* Outputs of rdm_estimate; every pointer is a caller-owned host array. rho is

@@ -319,8 +319,8 @@ size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_
 
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
                           int passes, int nbc) {
-  rdm_opts o{precision, dist, RDM_GRAM, passes == RDM_PASSES_STORE ? RDM_PASSES_STORE
-                                                                     : RDM_PASSES_RECOMPUTE};
+  rdm_opts o{precision, dist, RDM_GRAM,
+             passes == RDM_PASSES_STORE ? RDM_PASSES_STORE : RDM_PASSES_RECOMPUTE, 0};
   Plan p;
   if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
   if (!p.store) p.nbc = std::max(1, std::min(nbc, n_beta));
@@ -506,9 +506,9 @@ extern "C" rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, u
   double* norms = nullptr;
   if (dist == RDM_GAUSS) {
     CK(cudaMallocAsync(&norms, sizeof(double) * (size_t)n_v * 65, s));
-    CK(launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, norms + n_v, norms, s));
+    CK(launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, 0, norms + n_v, norms, s));
   }
-  CK(launch_init_block(L, dist, seed, n_v, norms, nullptr, x, s));
+  CK(launch_init_block(L, dist, seed, 0, n_v, norms, nullptr, x, s));
   if (norms) CK(cudaFreeAsync(norms, s));
   return RDM_OK;
 }
@@ -579,8 +579,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   const Layout& L = p.L;
   const int ds = L.DS, nv = ds * ds, ng = L.n_groups();
   const int64_t d_b = int64_t(1) << L.n_bath_bits;
-  if (o->vec_dist == RDM_BASIS && (int64_t)n_v > d_b) {
-    set_error("RDM_BASIS needs n_v <= d_b = %lld", (long long)d_b);
+  if (o->vec_dist == RDM_BASIS && o->first_vector + (int64_t)n_v > d_b) {
+    set_error("RDM_BASIS needs first_vector + n_v <= d_b = %lld", (long long)d_b);
     return RDM_EINVAL;
   }
   if (!ws) {
@@ -646,13 +646,15 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   // Once per estimate: the diagonal of H and (Gaussian case) the bath vectors.
   CK(counted([&] { return launch_diag(L, ham->d_diags, (int)hm.diags.size(), d_diag, s); }));
   if (p.gauss) {
-    CK(counted([&] { return launch_gauss_norms(d_b, n_v, seed, d_norm + p.n_v_pad, d_norm, s); }));
+    CK(counted([&] {
+      return launch_gauss_norms(d_b, n_v, seed, o->first_vector, d_norm + p.n_v_pad, d_norm, s);
+    }));
     if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
-    CK(counted([&] { return launch_gauss_fill(L, n_v, seed, d_norm, d_vbuf, s); }));
+    CK(counted([&] { return launch_gauss_fill(L, n_v, seed, o->first_vector, d_norm, d_vbuf, s); }));
   }
   auto init_block = [&](char* w) -> rdm_status {
     CK(timed(kKInit, blk_b, [&] {
-      return launch_init_block(L, o->vec_dist, seed, n_v, nullptr, d_vbuf, w, s);
+      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s);
     }));
     return RDM_OK;
   };
@@ -866,7 +868,8 @@ static bool valid_opts(const rdm_opts* o) {
          (o->vec_dist == RDM_RADEMACHER || o->vec_dist == RDM_GAUSS || o->vec_dist == RDM_BASIS) &&
          (o->form == RDM_GRAM || o->form == RDM_QUADRATURE) &&
          (o->passes == RDM_PASSES_AUTO || o->passes == RDM_PASSES_STORE ||
-          o->passes == RDM_PASSES_RECOMPUTE);
+          o->passes == RDM_PASSES_RECOMPUTE) &&
+         o->first_vector >= 0 && o->first_vector < (int64_t(1) << 23);
 }
 
 rdm_status rdm::check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,

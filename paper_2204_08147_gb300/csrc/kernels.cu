@@ -126,7 +126,7 @@ __device__ void block_reduce_store(const double* vals, int tpr, double* partials
 
 // ---------------------------------------------------------------- init
 
-__global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, double* part) {
+__global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, int64_t l0, double* part) {
   __shared__ double sh[kThreads];
   const int l = blockIdx.y;
   const int64_t chunk = (d_b + gridDim.x - 1) / gridDim.x;
@@ -134,7 +134,7 @@ __global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, double* part) {
   const int64_t hi = lo + chunk < d_b ? lo + chunk : d_b;
   double acc = 0.0;
   for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-    const double g = gauss_raw(seed, (uint64_t)l, (uint64_t)b);
+    const double g = gauss_raw(seed, (uint64_t)(l0 + l), (uint64_t)b);
     acc += g * g;
   }
   sh[threadIdx.x] = acc;
@@ -156,7 +156,7 @@ __global__ void k_gauss_finish(int n_v, int gx, const double* part, double* inv_
 
 template <typename T, int DS, int VW>
 __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uint64_t seed,
-                                                         int nvr, const double* inv_norm,
+                                                         int64_t l0, int nvr, const double* inv_norm,
                                                          const T* vbuf, T* W) {
   constexpr int NG = VW / DS;
   const int tpr = L.TPR, rpb = kThreads / tpr;
@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
       const int l = g0 + g;
       double val = 0.0;
       if (l < nvr) {
+        const uint64_t lg = (uint64_t)(l0 + l);  // index in the seeded sequence
         if (dist == RDM_RADEMACHER) {
-          const uint64_t z = splitmix64(seed, (((uint64_t)l << 40) | b) + 1);
+          const uint64_t z = splitmix64(seed, ((lg << 40) | b) + 1);
           val = (z >> 63) ? -rad : rad;
         } else if (dist == RDM_GAUSS) {
-          val = inv_norm ? gauss_raw(seed, (uint64_t)l, b) * inv_norm[l]
+          val = inv_norm ? gauss_raw(seed, lg, b) * inv_norm[l]
                          : (double)vbuf[((size_t)l << L.n_bath_bits) + b];
         } else {
-          val = (b == (uint64_t)l) ? 1.0 : 0.0;
+          val = (b == lg) ? 1.0 : 0.0;
         }
       }
 #pragma unroll
@@ -192,12 +193,12 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
   }
 }
 
-__global__ void k_gauss_fill(int64_t d_b, uint64_t seed, const double* inv_norm, int precision,
-                             void* vbuf) {
+__global__ void k_gauss_fill(int64_t d_b, uint64_t seed, int64_t l0, const double* inv_norm,
+                             int precision, void* vbuf) {
   const int l = blockIdx.y;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < d_b;
        b += (int64_t)gridDim.x * blockDim.x) {
-    const double v = gauss_raw(seed, (uint64_t)l, (uint64_t)b) * inv_norm[l];
+    const double v = gauss_raw(seed, (uint64_t)(l0 + l), (uint64_t)b) * inv_norm[l];
     if (precision == RDM_FP32)
       reinterpret_cast<float*>(vbuf)[(size_t)l * d_b + b] = (float)v;
     else
@@ -1349,29 +1350,29 @@ static cudaError_t opt_in_smem(const void* func) {
     else { constexpr int DS = 4; __VA_ARGS__; }                \
   } while (0)
 
-cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* partials,
+cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, double* partials,
                                double* inv_norm, cudaStream_t st) {
   int gx = (int)((d_b + 4095) / 4096);
   if (gx > 64) gx = 64;
   if (gx < 1) gx = 1;
-  k_gauss_sumsq<<<dim3(gx, n_v), kThreads, 0, st>>>(d_b, seed, partials);
+  k_gauss_sumsq<<<dim3(gx, n_v), kThreads, 0, st>>>(d_b, seed, l0, partials);
   k_gauss_finish<<<(n_v + 127) / 128, 128, 0, st>>>(n_v, gx, partials, inv_norm);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
+cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
                               const double* inv_norm, const void* vbuf, void* W, cudaStream_t st) {
   RDM_DISPATCH(L, (k_init_block<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
-                      L, dist, seed, n_v_real, inv_norm, reinterpret_cast<const T*>(vbuf),
+                      L, dist, seed, l0, n_v_real, inv_norm, reinterpret_cast<const T*>(vbuf),
                       reinterpret_cast<T*>(W))));
   return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, const double* inv_norm,
-                              void* vbuf, cudaStream_t st) {
+cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
+                              const double* inv_norm, void* vbuf, cudaStream_t st) {
   const int64_t d_b = int64_t(1) << L.n_bath_bits;
   int gx = (int)std::min<int64_t>((d_b + 255) / 256, 1024);
-  k_gauss_fill<<<dim3(gx, n_v), 256, 0, st>>>(d_b, seed, inv_norm, L.precision, vbuf);
+  k_gauss_fill<<<dim3(gx, n_v), 256, 0, st>>>(d_b, seed, l0, inv_norm, L.precision, vbuf);
   return cudaGetLastError();
 }
 

@@ -117,13 +117,13 @@ extern "C" rdm_status rdm_starting_block_noalloc(rdm_ham* ham, int precision, in
     // entry the kernels read is written earlier in the same call, so nothing needs
     // clearing.
     norms = scratch;
-    cudaError_t e = launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, scratch + n_v, norms, s);
+    cudaError_t e = launch_gauss_norms(int64_t(1) << L.n_bath_bits, n_v, seed, 0, scratch + n_v, norms, s);
     if (e != cudaSuccess) {
       set_error("rdm_starting_block_noalloc: norm kernels failed: %s", cudaGetErrorString(e));
       return RDM_ECUDA;
     }
   }
-  const cudaError_t e = launch_init_block(L, dist, seed, n_v, norms, nullptr, x, s);
+  const cudaError_t e = launch_init_block(L, dist, seed, 0, n_v, norms, nullptr, x, s);
   if (e != cudaSuccess) {
     set_error("rdm_starting_block_noalloc: kernel launch failed: %s", cudaGetErrorString(e));
     return RDM_ECUDA;

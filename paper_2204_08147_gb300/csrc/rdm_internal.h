@@ -80,16 +80,17 @@ struct StepCoefs {
 
 // Gaussian bath-vector norms: inv_norm[l] = 1/||g_l|| for l < n_v (float64),
 // partials scratch of n_v * gx doubles.
-cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, double* partials,
+cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, double* partials,
                                double* inv_norm, cudaStream_t st);
 
-// W = [I_s (x) v_l] for l < n_v_real, zero columns beyond. Gaussian values come
-// from inv_norm (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T).
-cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int n_v_real,
+// W = [I_s (x) v_l] for l < n_v_real, zero columns beyond; vector l of the block is
+// vector l0 + l of the seeded sequence. Gaussian values come from inv_norm
+// (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T).
+cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
                               const double* inv_norm, const void* vbuf, void* W, cudaStream_t st);
-// vbuf[l][b] = normalised Gaussian bath vector l (T = the layout's precision).
-cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, const double* inv_norm,
-                              void* vbuf, cudaStream_t st);
+// vbuf[l][b] = normalised Gaussian bath vector l0 + l (T = the layout's precision).
+cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
+                              const double* inv_norm, void* vbuf, cudaStream_t st);
 
 // Flip terms grouped for the tiled SpMM. A tile is 2^kTileBits consecutive states
 // of one slice; a flip mask m splits into m_high = m >> kTileBits (which tile the

@@ -41,7 +41,7 @@ class Model(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("vec_dist", C.c_int), ("form", C.c_int),
-                ("passes", C.c_int)]
+                ("passes", C.c_int), ("first_vector", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -136,8 +136,8 @@ _PASSES = {"auto": PASSES_AUTO, "store": PASSES_STORE, "recompute": PASSES_RECOM
            PASSES_AUTO: PASSES_AUTO, PASSES_STORE: PASSES_STORE, PASSES_RECOMPUTE: PASSES_RECOMPUTE}
 
 
-def _opts(precision, dist, form, passes="auto") -> Opts:
-    return Opts(_PREC[precision], _DIST[dist], _FORM[form], _PASSES[passes])
+def _opts(precision, dist, form, passes="auto", first_vector=0) -> Opts:
+    return Opts(_PREC[precision], _DIST[dist], _FORM[form], _PASSES[passes], int(first_vector))
 
 
 class _ResultArrays:
@@ -314,10 +314,10 @@ class Hamiltonian:
         return n.value
 
     def estimate(self, betas, n_v, k, seed, precision="fp32", dist="rademacher", form="gram",
-                 full=False, passes="auto") -> dict:
+                 full=False, passes="auto", first_vector=0) -> dict:
         b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
         res = _ResultArrays(len(b), n_v, k, self.d_s, full)
-        o = _opts(precision, dist, form, passes)
+        o = _opts(precision, dist, form, passes, first_vector)
         _check(_lib.rdm_estimate(self.h, _ptr(b), len(b), int(n_v), int(k), int(seed) & (2 ** 64 - 1),
                                  C.byref(o), C.byref(res.struct)), "rdm_estimate")
         return res.as_dict(o.form)

@@ -334,3 +334,24 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
         finally:
             ctx.detach_workspace()
     assert e.value.status == lib.ENOMEM
+
+
+# ---------------------------------------------------------------- bath-vector shards
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_shards_combine_to_the_whole_run(ctx, lib, prec, tol):
+    """Three shards of the bath vectors (first_vector offsets), run one after another
+    on this GPU and folded on the host, equal the single run."""
+    from paper_2204_08147_gb300.sharded import combine, local_part
+    spec = W.long_range_tfim(12, 2, 1.5, 0.9)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = [0.5, 2.0, 7.0]
+    whole = ham.estimate(betas, 10, 24, 31, precision=prec, dist="gauss")
+    parts = [local_part(ham, betas, 10, 24, 31, r, 3, precision=prec, dist="gauss") for r in range(3)]
+    res = combine(parts, betas, spec.d_b, 10)
+    assert abs(res["e0"] - whole["e0"]) < 1e-12
+    np.testing.assert_allclose(res["rho"], whole["rho"], atol=tol)
+    np.testing.assert_allclose(res["lnZ"], whole["lnZ"], atol=tol)
+    # and against the oracle
+    ref = lanczos.Estimator(spec).run(betas, 10, 24, 31, "gauss")
+    np.testing.assert_allclose(res["rho"], ref["rho"], atol=TOL64 if prec == "fp64" else TOL32)
