@@ -107,7 +107,14 @@ void make_term_image(const HostModel& h, TermImage* img) {
   std::vector<uint32_t> pat_high, pat_flags, term_low;
   std::vector<int> pat_start;
   std::vector<double> term_odd, term_even;
-  for (auto& kv : groups) {
+  // Pattern 0 (in-tile terms) first, then partner tiles from the farthest (largest
+  // m_high, the likeliest L2 misses) to the nearest, so the slow copies enter the
+  // SpMM's copy ring early.
+  std::vector<std::pair<const uint32_t, std::vector<const FlipTerm*>>*> order;
+  for (auto& kv : groups) order.push_back(&kv);
+  std::sort(order.begin() + 1, order.end(), [](auto* x, auto* y) { return x->first > y->first; });
+  for (auto* kvp : order) {
+    auto& kv = *kvp;
     pat_high.push_back(kv.first);
     pat_start.push_back((int)term_low.size());
     uint32_t flags = 1u;

