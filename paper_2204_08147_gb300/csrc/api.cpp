@@ -187,10 +187,15 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
   l.precision = precision;
   l.elem = precision == RDM_FP32 ? 4 : 8;
   l.VW = precision == RDM_FP32 ? 4 : (l.DS == 4 ? 4 : 2);
-  const int slice_cols = 128 / l.elem;  // 128-byte rows per slice
   int cols = l.DS * n_v;
   int bcols;
-  if (cols >= slice_cols) {
+  if (l.VW * l.elem == 16 && h.n >= kTileBits) {
+    // tiled layout: narrow slices of kTiledLanes vectors per row
+    const int sc = l.VW * kTiledLanes;
+    bcols = (cols + sc - 1) / sc * sc;
+    l.Bs = sc;
+  } else if (cols >= 128 / l.elem) {
+    const int slice_cols = 128 / l.elem;  // 128-byte rows per slice
     bcols = (cols + slice_cols - 1) / slice_cols * slice_cols;
     l.Bs = slice_cols;
   } else {

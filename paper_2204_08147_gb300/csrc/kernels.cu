@@ -452,18 +452,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 // Producer/consumer layout of the tiled SpMM: warp 8 issues TMA bulk copies into a
 // ring of kStages shared-memory slots; the consumer warps read them. A slot holds one
-// 32 KB tile (256 rows x 128 bytes) plus, for the own tile, its 256 diagonal
-// entries. Per tile the stage sequence is: own tile, each needed partner tile,
+// 32 KB tile (kTileRows rows of a slice) plus, for the own tile, its kTileRows
+// diagonal entries. Per tile the stage sequence is: own tile, each needed partner tile,
 // then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
 // empty barriers (one arrival per consumer warp) order the ring.
-constexpr int kStages = 6;
 constexpr int kConsumerWarps = 8;
 constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
-constexpr uint32_t kTileBytes = kTileRows * 128;
-constexpr uint32_t kSlotBytes = kTileBytes + 2048;
+constexpr uint32_t kTileBytes = (uint32_t)kTileRows * kTiledLanes * 16;  // 32 KB
+template <typename T>
+__host__ __device__ constexpr uint32_t slot_bytes() {
+  return kTileBytes + (uint32_t)kTileRows * (uint32_t)sizeof(T);
+}
+// As many slots as fit beside ~24 KB of tables and scratch in 227 KB (at most 6).
+template <typename T>
+__host__ __device__ constexpr int ring_stages() {
+  return (232448 - 24576) / (int)slot_bytes<T>() < 6 ? (232448 - 24576) / (int)slot_bytes<T>() : 6;
+}
 
 template <typename T>
 __host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms) {
+  constexpr int kStages = ring_stages<T>();
+  constexpr uint32_t kSlotBytes = slot_bytes<T>();
   size_t off = (size_t)kStages * kSlotBytes;
   off += 2 * kStages * 8 + 64;                     // full/empty barriers, control
   off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the 8 lanes
@@ -510,14 +519,14 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volati
 }
 
 // In-tile flip whose partner rows belong to the same thread: the thread's rows
-// rg + 32 m (m = 0..7) form a subcube over tile bits 5..7, so a mask with no bit
-// below 5 maps row m to row m ^ K of the same thread (K = mask >> 5).
-template <int K, typename T, int VW, int RPT>
+// rg + RG m (m = 0..7) form a subcube over the top three tile bits, so a mask with
+// no bit below log2(RG) maps row m to row m ^ K of the same thread.
+template <int K, int RG, typename T, int VW, int RPT>
 __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW], int rg, uint32_t ml,
                                          T co, T ce) {
 #pragma unroll
   for (int m = 0; m < RPT; ++m) {
-    const uint32_t r = (uint32_t)(rg + 32 * m);
+    const uint32_t r = (uint32_t)(rg + RG * m);
     const T c = (co == ce) ? co : ((__popc(r & ml) & 1) ? co : ce);
 #pragma unroll
     for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xo[m ^ K][v], y[m][v]);
@@ -527,12 +536,18 @@ __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW]
 template <typename T, int DS, int MODE>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
-  constexpr int BS = 128 / (int)sizeof(T);  // elements per 128-byte row
+  constexpr int LPR = kTiledLanes;          // 16-byte vectors per row
+  constexpr int BS = VW * LPR;              // elements per row of a slice
   constexpr int NG = VW / DS;
   constexpr int NVG = DS * DS;
   constexpr int NV = NG * NVG;
-  constexpr int RG = kConsumerWarps * 4;  // row groups of 8 lanes
-  constexpr int RPT = kTileRows / RG;     // rows per consumer thread
+  constexpr int RG = kConsumerWarps * 32 / LPR;  // row groups
+  constexpr int RGL = (RG >= 256) ? 8 : (RG >= 128) ? 7 : (RG >= 64) ? 6 : 5;  // log2(RG)
+  constexpr int RPT = kTileRows / RG;            // rows per consumer thread (8)
+  constexpr int kStages = ring_stages<T>();
+  constexpr uint32_t kSlotBytes = slot_bytes<T>();
+  static_assert(RPT == 8, "eight rows per consumer thread");
+  static_assert((1 << RGL) == RG, "row groups are a power of two");
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;
   const int npat = tt.n_pat, nterm = tt.n_terms;
@@ -635,8 +650,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   }
 
   // -------------------------------------------------- consumers
-  const int lane = threadIdx.x & 7;  // 16-byte column chunk of a row
-  const int rg = threadIdx.x >> 3;   // row group: rows rg + RG*m
+  const int lane = threadIdx.x % LPR;  // 16-byte column chunk of a row
+  const int rg = threadIdx.x / LPR;    // row group: rows rg + RG*m
   const bool leader = (threadIdx.x & 31) == 0;
   uint32_t seq = 0;
   bool aborted = false;
@@ -656,7 +671,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     const size_t soff = (size_t)slice * L.D * BS;
     T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
     consumers_sync_or(false);
-    if (threadIdx.x < 8 * NV) {  // this slice's mixing coefficients
+    if (threadIdx.x < LPR * NV) {  // this slice's mixing coefficients
       const int ln = threadIdx.x / NV, e = threadIdx.x % NV;
       const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
       s_mz[ln * 16 + e] = (T)a.mz[gidx];
@@ -697,15 +712,15 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       for (int t = pat_start[0]; t < t1; ++t) {
         const uint32_t ml = term_low[t];
         const T co = term_odd[t], ce = term_even[t];
-        if (RPT == 8 && (ml & 31u) == 0u) {
-          switch (ml >> 5) {
-            case 1: reg_flip<1>(y, xo, rg, ml, co, ce); break;
-            case 2: reg_flip<2>(y, xo, rg, ml, co, ce); break;
-            case 3: reg_flip<3>(y, xo, rg, ml, co, ce); break;
-            case 4: reg_flip<4>(y, xo, rg, ml, co, ce); break;
-            case 5: reg_flip<5>(y, xo, rg, ml, co, ce); break;
-            case 6: reg_flip<6>(y, xo, rg, ml, co, ce); break;
-            default: reg_flip<7>(y, xo, rg, ml, co, ce); break;
+        if ((ml & (uint32_t)(RG - 1)) == 0u) {
+          switch (ml >> RGL) {
+            case 1: reg_flip<1, RG>(y, xo, rg, ml, co, ce); break;
+            case 2: reg_flip<2, RG>(y, xo, rg, ml, co, ce); break;
+            case 3: reg_flip<3, RG>(y, xo, rg, ml, co, ce); break;
+            case 4: reg_flip<4, RG>(y, xo, rg, ml, co, ce); break;
+            case 5: reg_flip<5, RG>(y, xo, rg, ml, co, ce); break;
+            case 6: reg_flip<6, RG>(y, xo, rg, ml, co, ce); break;
+            default: reg_flip<7, RG>(y, xo, rg, ml, co, ce); break;
           }
         } else if (co == ce) {
 #pragma unroll
@@ -831,21 +846,21 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
 #pragma unroll
       for (int e = 0; e < NV; ++e) {
         double x = (double)acc[e];
-        x += __shfl_xor_sync(0xffffffffu, x, 8);
-        x += __shfl_xor_sync(0xffffffffu, x, 16);
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
         v[e] = x;
       }
-      if ((threadIdx.x & 31) < 8) {
+      if ((threadIdx.x & 31) < LPR) {
 #pragma unroll
-        for (int e = 0; e < NV; ++e) red[(warp * 8 + lane) * 16 + e] = v[e];
+        for (int e = 0; e < NV; ++e) red[(warp * LPR + lane) * 16 + e] = v[e];
       }
       consumers_sync_or(false);
-      if (threadIdx.x < 8) {
+      if (threadIdx.x < LPR) {
         const int gs = BS / DS;
         const size_t base = ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
         for (int e = 0; e < NV; ++e) {
           double sum = 0.0;
-          for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * 8 + threadIdx.x) * 16 + e];
+          for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * LPR + threadIdx.x) * 16 + e];
           a.partials[base + e] = sum;
         }
       }

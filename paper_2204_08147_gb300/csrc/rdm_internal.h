@@ -92,13 +92,18 @@ cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t 
 cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
                               const double* inv_norm, void* vbuf, cudaStream_t st);
 
-// Flip terms grouped for the tiled SpMM. A tile is 2^kTileBits consecutive states
-// of one slice; a flip mask m splits into m_high = m >> kTileBits (which tile the
-// partner row lies in, relative to this one: tile ^ m_high) and m_low (the row
-// permutation inside that tile). Pattern p collects the terms with one m_high;
-// pattern 0 has m_high = 0 (in-tile terms). Flags: bit0 = every term has m_low = 0
-// (its activity is uniform over a tile), bit1/bit2 = some c_odd/c_even is nonzero.
-constexpr int kTileBits = 8;
+// Flip terms grouped for the tiled SpMM. In the tiled layout a row of a slice is
+// kTiledLanes 16-byte vectors (32 bytes: 8 float32 / 4 float64 columns) and a tile
+// is 2^kTileBits consecutive states of one slice, 32 KB. Narrow rows put many
+// states into each byte of L2, so the partner tiles of a tile stay cached. A flip
+// mask m splits into m_high = m >> kTileBits (which tile the partner row lies in,
+// relative to this one: tile ^ m_high) and m_low (the row permutation inside that
+// tile). Pattern p collects the terms with one m_high; pattern 0 has m_high = 0
+// (in-tile terms). Flags: bit0 = every term has m_low = 0 (its activity is uniform
+// over a tile), bit1/bit2 = some c_odd/c_even is nonzero.
+constexpr int kTiledLanesLog = 1;
+constexpr int kTiledLanes = 1 << kTiledLanesLog;
+constexpr int kTileBits = 11 - kTiledLanesLog;
 constexpr int kTileRows = 1 << kTileBits;
 struct TiledTerms {
   int n_pat;
@@ -132,10 +137,10 @@ struct SpmmArgs {
   uint32_t* err;       // bit 0 set if a bulk-copy wait gave up
 };
 
-// True if the tiled SpMM applies to this layout (128-byte rows, 16-byte vectors,
-// at least one full tile per slice).
+// True if the tiled SpMM applies to this layout (16-byte vectors, kTiledLanes of
+// them per row, at least one full tile per slice).
 inline bool layout_tiled(const Layout& L) {
-  return L.Bs * L.elem == 128 && L.VW * L.elem == 16 && L.n_bits >= kTileBits;
+  return L.VW * L.elem == 16 && L.Bs == L.VW * kTiledLanes && L.n_bits >= kTileBits;
 }
 // Blocks per slice of the tiled SpMM (one persistent block per SM).
 inline int spmm_tiled_grid(const Layout& L) {
