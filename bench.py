@@ -335,18 +335,30 @@ def run_ours(a):
     return 0
 
 
+def spmm_source_hash() -> str:
+    """sha256 (16 hex) of the tiled SpMM's source: its region of kernels.cu plus the
+    layout constants header. A committed DRAM-traffic figure is only reported while
+    this matches the hash it was measured with."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2204_08147_gb300", "csrc")
+    src = open(os.path.join(csrc, "kernels.cu")).read()
+    a = src.index("// ---------------------------------------------------------------- tiled SpMM")
+    b = src.index("// ---------------------------------------------------------------- orthogonalisation")
+    h = hashlib.sha256(src[a:b].encode())
+    h.update(open(os.path.join(csrc, "rdm_internal.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_from_profiles():
     """DRAM bytes per k_spmm launch from the committed ncu summary, if it was taken
     on the current kernel source (else null)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_spmm_lr_tfim_N22.md")
-    src = os.path.join(ROOT, "paper_2204_08147_gb300", "csrc", "kernels.cu")
+    path = os.path.join(ROOT, "profiles", "k_spmm_tiled_lr_tfim_N22_dram.md")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = spmm_source_hash()
         for line in open(path):
             if line.startswith("traffic_bytes_per_launch:"):
-                val, _, tag = line.split(":", 1)[1].strip().partition(" kernels.cu sha256 ")
-                return float(val) if tag.strip() == h else None
+                fields = line.split()
+                return float(fields[1]) if fields[-1] == h else None
     except Exception:
         return None
     return None
