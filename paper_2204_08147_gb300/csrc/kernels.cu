@@ -463,20 +463,15 @@ template <typename T>
 __host__ __device__ constexpr uint32_t slot_bytes() {
   return kTileBytes + (uint32_t)kTileRows * (uint32_t)sizeof(T);
 }
-// As many slots as fit beside ~24 KB of tables and scratch in 227 KB (at most 6).
-template <typename T>
-__host__ __device__ constexpr int ring_stages() {
-  return (232448 - 24576) / (int)slot_bytes<T>() < 6 ? (232448 - 24576) / (int)slot_bytes<T>() : 6;
-}
+constexpr int kMaxStages = 8;
 
 template <typename T>
-__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms) {
-  constexpr int kStages = ring_stages<T>();
+__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int stages) {
   constexpr uint32_t kSlotBytes = slot_bytes<T>();
-  size_t off = (size_t)kStages * kSlotBytes;
-  off += 2 * kStages * 8 + 64;                     // full/empty barriers, control
+  size_t off = (size_t)stages * kSlotBytes;
+  off += 2 * kMaxStages * 8 + 64;                  // full/empty barriers, control
   off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the 8 lanes
-  off += (size_t)kConsumerWarps * 8 * 16 * 8;      // reduction scratch
+  off += (size_t)kConsumerWarps * kTiledLanes * 16 * 8;  // reduction scratch
   off += (size_t)n_pat * 12 + 4;                   // pat_high, pat_flags, pat_start (+1)
   off = (off + 15) / 16 * 16;
   off += (size_t)n_terms * (4 + 2 * sizeof(T));
@@ -544,7 +539,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   constexpr int RG = kConsumerWarps * 32 / LPR;  // row groups
   constexpr int RGL = (RG >= 256) ? 8 : (RG >= 128) ? 7 : (RG >= 64) ? 6 : 5;  // log2(RG)
   constexpr int RPT = kTileRows / RG;            // rows per consumer thread (8)
-  constexpr int kStages = ring_stages<T>();
+  const int kStages = a.stages;
   constexpr uint32_t kSlotBytes = slot_bytes<T>();
   static_assert(RPT == 8, "eight rows per consumer thread");
   static_assert((1 << RGL) == RG, "row groups are a power of two");
@@ -553,12 +548,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   const int npat = tt.n_pat, nterm = tt.n_terms;
   unsigned char* const ring = smem;
   uint64_t* const full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kSlotBytes);
-  uint64_t* const empty = full + kStages;
-  volatile int* const abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
-  T* const s_mz = reinterpret_cast<T*>(smem + (size_t)kStages * kSlotBytes + 2 * kStages * 8 + 64);
+  uint64_t* const empty = full + kMaxStages;
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(empty + kMaxStages);
+  T* const s_mz = reinterpret_cast<T*>(smem + (size_t)kStages * kSlotBytes + 2 * kMaxStages * 8 + 64);
   T* const s_cp = s_mz + 8 * 16;
   double* const red = reinterpret_cast<double*>(s_cp + 8 * 16);
-  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(red + kConsumerWarps * 8 * 16);
+  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(red + kConsumerWarps * kTiledLanes * 16);
   uint32_t* const pat_flags = pat_high + npat;
   int* const pat_start = reinterpret_cast<int*>(pat_flags + npat);
   size_t off = (size_t)(reinterpret_cast<unsigned char*>(pat_start + npat + 1) - smem);
@@ -1437,10 +1432,22 @@ cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void
 }
 
 template <typename T, int DS, int MODE>
-static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a, cudaStream_t st) {
-  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms);
+static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a0, cudaStream_t st) {
   cudaError_t e = opt_in_smem(reinterpret_cast<const void*>(k_spmm_tiled<T, DS, MODE>));
   if (e != cudaSuccess) return e;
+  static int optin = 0;
+  if (!optin) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+  }
+  // Deepest ring (up to 6 slots) that fits beside this Hamiltonian's term tables.
+  SpmmArgs a = a0;
+  a.stages = 6;
+  while (a.stages > 2 && tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages) > (size_t)optin)
+    --a.stages;
+  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages);
   k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
 }

@@ -135,6 +135,7 @@ struct SpmmArgs {
   TiledTerms tiled;    // n_pat = 0: not available
   const void* diag;    // [D] diagonal of H in the block's precision (tiled SpMM)
   uint32_t* err;       // bit 0 set if a bulk-copy wait gave up
+  int stages;          // tiled SpMM: copy-ring depth (set by the launcher)
 };
 
 // True if the tiled SpMM applies to this layout (16-byte vectors, kTiledLanes of
