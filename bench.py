@@ -47,6 +47,8 @@ def _args():
     p.add_argument("--n-sites", type=int, default=22,
                    help="spins of the workload (22 = the benchmark; smaller only for profiling)")
     p.add_argument("--k", type=int, default=60, help="Lanczos steps (60 = the benchmark)")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving sub-benchmark")
+    p.add_argument("--serving-requests", type=int, default=32)
     return p.parse_args()
 
 
@@ -284,6 +286,25 @@ def run_ours(a):
         plain = {"value": 1.0 / (time.perf_counter() - t0), "unit": "solves/s",
                  "form": "float64, one bath vector per call (32 calls = one solve), no batching"}
 
+    # Precision: float32 path against the float64 path on the same seeds (one g value).
+    precision = None
+    if rank == 0 and (a.n_sites, a.k) == (22, 60):
+        c = cfgs[0]
+        r32 = hams[0].estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32", dist=c["dist"])
+        r64 = hams[0].estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64", dist=c["dist"])
+        b = float(c["betas"][0])
+        precision = {
+            "rho_max_abs": float(np.abs(r32["rho"] - r64["rho"]).max()),
+            "hstar_max_abs": float(np.abs(rdm.mean_force(r32["rho"][0], b) - rdm.mean_force(r64["rho"][0], b)).max()),
+            "entropy_abs": abs(rdm.entropy(r32["rho"][0]) - rdm.entropy(r64["rho"][0])),
+            "lnZ_abs": float(abs(r32["lnZ"][0] - r64["lnZ"][0])),
+            "against": "float64 path of this library, same bath vectors (g index 0)",
+        }
+
+    serving = None
+    if rank == 0 and not a.no_serving:
+        serving = serving_bench(rdm, ctx, a.serving_requests)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -322,6 +343,8 @@ def run_ours(a):
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["launches"]},
         "roofline": roof,
         "plain_fp64": plain,
+        "precision_fp32_vs_fp64": precision,
+        "serving": serving,
     }
     if cpu_sample is not None:
         line["cpu_baseline"] = {"value": oracle_solves_per_s(cpu_sample), "unit": "solves/s", "cores": 1,
@@ -333,6 +356,43 @@ def run_ours(a):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def serving_bench(rdm, ctx, n_req: int) -> dict:
+    """Mixed request stream (XXZ or LR-TFIM, N in 12..18, mixed beta grids, n_v, k)
+    through the library's request loop: first all requests at once (saturated
+    throughput), then Poisson arrivals at 0.8x that rate (latency percentiles)."""
+    reqs = W.serving_requests(n_req, seed=20220419, n_min=12, n_max=18)
+    budget = 64 << 30
+
+    def run(gaps):
+        ctx.serve_start(budget, max_inflight=4)
+        try:
+            t0 = time.perf_counter()
+            tickets, t_next = [], t0
+            for r, g in zip(reqs, gaps):
+                t_next += g
+                while time.perf_counter() < t_next:
+                    time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+                tickets.append(ctx.submit(r["spec"], r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32"))
+            for t in tickets:
+                ctx.wait(t)
+            wall = time.perf_counter() - t0
+            lat = [ctx.request_times(t)[0] for t in tickets]
+        finally:
+            ctx.serve_stop()
+        return wall, lat
+
+    wall, _ = run([0.0] * n_req)
+    rate = n_req / wall
+    rng = np.random.default_rng(7)
+    wall2, lat = run(list(rng.exponential(1.0 / (0.8 * rate), size=n_req)))
+    return {"requests": n_req, "saturated_solves_per_s": rate,
+            "poisson_rate_per_s": 0.8 * rate, "poisson_solves_per_s": n_req / wall2,
+            "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)),
+                           "p99": 1000 * float(np.percentile(lat, 99))},
+            "stream": "XXZ/LR-TFIM mix, N 12..18, N_s 1-2, 8-64 betas, n_v 8-64, k 30-100, float32",
+            "max_inflight": 4, "budget_gib": budget >> 30}
 
 
 def spmm_source_hash() -> str:
