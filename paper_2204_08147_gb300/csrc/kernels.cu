@@ -457,7 +457,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
 // empty barriers (one arrival per consumer warp) order the ring.
 constexpr int kConsumerWarps = 8;
-constexpr int kTiledThreads = (kConsumerWarps + 1) * 32;
+constexpr int kProducerWarps = 2;  // each issues the copies of every other ring slot
+constexpr int kTiledThreads = (kConsumerWarps + kProducerWarps) * 32;
 constexpr uint32_t kTileBytes = (uint32_t)kTileRows * kTiledLanes * 16;  // 32 KB
 template <typename T>
 __host__ __device__ constexpr uint32_t slot_bytes() {
@@ -528,6 +529,50 @@ __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW]
   }
 }
 
+// y[m] += c * P[row m ^ ml] for one term whose coefficient depends on the parity of
+// (row0 + row) & mparity (c_odd / c_even), rows of this thread.
+template <typename T, int VW, int RPT, int RG>
+__device__ __forceinline__ void apply_term(T (&y)[RPT][VW], const int (&roff)[RPT], int rg, const T* P,
+                                           uint32_t mparity, int mlb, uint32_t ml, T co, T ce,
+                                           uint32_t row0) {
+  (void)ml;
+  if (co == ce) {
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      T xp[VW];
+      VecIO<T, VW>::ld_rw(xp, P + (roff[m] ^ mlb));
+#pragma unroll
+      for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      const uint32_t r = (uint32_t)(rg + RG * m);
+      const T c = (__popc((row0 + r) & mparity) & 1) ? co : ce;
+      if (c != (T)0) {
+        T xp[VW];
+        VecIO<T, VW>::ld_rw(xp, P + (roff[m] ^ mlb));
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+      }
+    }
+  }
+}
+
+// Two uniform-coefficient terms at once (loads of both issued before their FMAs).
+template <typename T, int VW, int RPT>
+__device__ __forceinline__ void apply2_uniform(T (&y)[RPT][VW], const int (&roff)[RPT], const T* PA, int mlbA,
+                                               T cA, const T* PB, int mlbB, T cB) {
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    T a[VW], b[VW];
+    VecIO<T, VW>::ld_rw(a, PA + (roff[m] ^ mlbA));
+    VecIO<T, VW>::ld_rw(b, PB + (roff[m] ^ mlbB));
+#pragma unroll
+    for (int v = 0; v < VW; ++v) y[m][v] = fma(cB, b[v], fma(cA, a[v], y[m][v]));
+  }
+}
+
 template <typename T, int DS, int MODE>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
@@ -586,9 +631,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   const int64_t tps = L.D >> kTileBits;
   const bool has_prev = a.w_prev != nullptr;
 
-  if (warp == kConsumerWarps) {
-    // ------------------------------------------------ producer (one lane)
+  if (warp >= kConsumerWarps) {
+    // ------------------------------------------------ producers (lane 0 of each)
+    // Both walk the whole stage sequence; producer q issues the stages with
+    // seq % kProducerWarps == q (the ring depth is a multiple of kProducerWarps, so
+    // each owns fixed slots).
     if ((threadIdx.x & 31) != 0) return;
+    const uint32_t q = (uint32_t)(warp - kConsumerWarps);
     // W_j tiles are reused as partners of neighbouring tiles: keep them in L2;
     // W_{j-1} tiles are read once: let them leave first.
     const uint64_t keep = policy_evict_last();
@@ -602,34 +651,35 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       for (int64_t tix = blockIdx.x; tix < tps && !stop; tix += gridDim.x) {
         const uint32_t ut = (uint32_t)tix;
         // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
-        int p = 0;
         int kind = -1;
         while (true) {
-          const int slot = (int)(seq % kStages);
-          if (seq >= (uint32_t)kStages &&
-              !ring_wait(&empty[slot], ((seq / kStages) - 1u) & 1u, abort_flag)) {
-            stop = true;
-            break;
-          }
-          unsigned char* dst = ring + (size_t)slot * kSlotBytes;
-          fence_proxy_async();
-          if (kind == -1) {
-            mbar_expect_tx(&full[slot], kTileBytes + kTileRows * (uint32_t)sizeof(T));
-            bulk_load_hint(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], keep);
-            bulk_load_hint(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits),
-                           kTileRows * (uint32_t)sizeof(T), &full[slot], stream);
-          } else if (kind == -2) {
-            mbar_expect_tx(&full[slot], kTileBytes);
-            bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
-          } else {
-            mbar_expect_tx(&full[slot], kTileBytes);
-            bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
-                           &full[slot], keep);
+          if (seq % kProducerWarps == q) {
+            const int slot = (int)(seq % (uint32_t)kStages);
+            if (seq >= (uint32_t)kStages &&
+                !ring_wait(&empty[slot], ((seq / (uint32_t)kStages) - 1u) & 1u, abort_flag)) {
+              stop = true;
+              break;
+            }
+            unsigned char* dst = ring + (size_t)slot * kSlotBytes;
+            fence_proxy_async();
+            if (kind == -1) {
+              mbar_expect_tx(&full[slot], kTileBytes + kTileRows * (uint32_t)sizeof(T));
+              bulk_load_hint(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], keep);
+              bulk_load_hint(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits),
+                             kTileRows * (uint32_t)sizeof(T), &full[slot], stream);
+            } else if (kind == -2) {
+              mbar_expect_tx(&full[slot], kTileBytes);
+              bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
+            } else {
+              mbar_expect_tx(&full[slot], kTileBytes);
+              bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
+                             &full[slot], keep);
+            }
           }
           ++seq;
           // next stage of this tile
           if (kind == -2) break;
-          p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
+          const int p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
           if (p < npat) {
             kind = p;
           } else if (has_prev) {
@@ -647,12 +697,19 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   // -------------------------------------------------- consumers
   const int lane = threadIdx.x % LPR;  // 16-byte column chunk of a row
   const int rg = threadIdx.x / LPR;    // row group: rows rg + RG*m
+  // Element offsets of this thread's rows in a tile; the partner of row r under an
+  // in-tile mask ml is at offset roff ^ (ml * BS) (BS is a power of two > lane*VW).
+  int roff[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) roff[m] = (rg + RG * m) * BS + lane * VW;
   const bool leader = (threadIdx.x & 31) == 0;
   uint32_t seq = 0;
   bool aborted = false;
-  auto acquire = [&](const unsigned char*& slot_ptr) -> bool {
-    const int slot = (int)(seq % kStages);
-    if (!ring_wait(&full[slot], (seq / kStages) & 1u, abort_flag)) return false;
+  // Waits for the ring slot `ahead` stages past the next unreleased one.
+  auto acquire = [&](const unsigned char*& slot_ptr, uint32_t ahead) -> bool {
+    const uint32_t q = seq + ahead;
+    const int slot = (int)(q % (uint32_t)kStages);
+    if (!ring_wait(&full[slot], (q / (uint32_t)kStages) & 1u, abort_flag)) return false;
     slot_ptr = ring + (size_t)slot * kSlotBytes;
     return true;
   };
@@ -688,7 +745,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       const uint32_t row0 = ut << kTileBits;
       const unsigned char* sp;
       // own tile: diagonal and in-tile terms
-      if (!acquire(sp)) {
+      if (!acquire(sp, 0)) {
         aborted = true;
         break;
       }
@@ -697,14 +754,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       T xo[RPT][VW], y[RPT][VW];
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
-        const int r = rg + RG * m;
-        VecIO<T, VW>::ld_rw(xo[m], own + r * BS + lane * VW);
-        const T dg = dgt[r];
+        VecIO<T, VW>::ld_rw(xo[m], own + roff[m]);
+        const T dg = dgt[rg + RG * m];
 #pragma unroll
         for (int v = 0; v < VW; ++v) y[m][v] = dg * xo[m][v];
       }
       const int t1 = pat_start[1];
-      for (int t = pat_start[0]; t < t1; ++t) {
+      for (int t = pat_start[0]; t < t1;) {
         const uint32_t ml = term_low[t];
         const T co = term_odd[t], ce = term_even[t];
         if ((ml & (uint32_t)(RG - 1)) == 0u) {
@@ -717,74 +773,70 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             case 6: reg_flip<6, RG>(y, xo, rg, ml, co, ce); break;
             default: reg_flip<7, RG>(y, xo, rg, ml, co, ce); break;
           }
-        } else if (co == ce) {
-#pragma unroll
-          for (int m = 0; m < RPT; ++m) {
-            const int r = rg + RG * m;
-            T xp[VW];
-            VecIO<T, VW>::ld_rw(xp, own + (r ^ (int)ml) * BS + lane * VW);
-#pragma unroll
-            for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < RPT; ++m) {
-            const int r = rg + RG * m;
-            const T c = (__popc(((uint32_t)r) & ml) & 1) ? co : ce;
-            if (c != (T)0) {
-              T xp[VW];
-              VecIO<T, VW>::ld_rw(xp, own + (r ^ (int)ml) * BS + lane * VW);
-#pragma unroll
-              for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
-            }
+          ++t;
+          continue;
+        }
+        if (co == ce && t + 1 < t1) {
+          const uint32_t ml2 = term_low[t + 1];
+          const T c2 = term_odd[t + 1];
+          if ((ml2 & (uint32_t)(RG - 1)) != 0u && c2 == term_even[t + 1]) {
+            apply2_uniform<T, VW, RPT>(y, roff, own, (int)ml * BS, co, own, (int)ml2 * BS, c2);
+            t += 2;
+            continue;
           }
         }
+        apply_term<T, VW, RPT, RG>(y, roff, rg, own, ml, (int)ml * BS, ml, co, ce, 0u);
+        ++t;
       }
       release();
-      // partner tiles
-      for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;
-           p = tiled_next(p + 1, npat, ut, pat_high, pat_flags)) {
-        if (!acquire(sp)) {
+      // partner tiles; two single-term patterns are consumed together so their
+      // shared-memory loads overlap
+      for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;) {
+        const int pn = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
+        const int ta = pat_start[p];
+        if (pn < npat && pat_start[p + 1] - ta == 1 && pat_start[pn + 1] - pat_start[pn] == 1 &&
+            term_odd[ta] == term_even[ta] && term_odd[pat_start[pn]] == term_even[pat_start[pn]]) {
+          const unsigned char* sp2;
+          if (!acquire(sp, 0) || !acquire(sp2, 1)) {
+            aborted = true;
+            break;
+          }
+          const int tb = pat_start[pn];
+          apply2_uniform<T, VW, RPT>(y, roff, reinterpret_cast<const T*>(sp), (int)term_low[ta] * BS,
+                                     term_odd[ta], reinterpret_cast<const T*>(sp2),
+                                     (int)term_low[tb] * BS, term_odd[tb]);
+          release();
+          release();
+          p = tiled_next(pn + 1, npat, ut, pat_high, pat_flags);
+          continue;
+        }
+        if (!acquire(sp, 0)) {
           aborted = true;
           break;
         }
         const T* P = reinterpret_cast<const T*>(sp);
         const uint32_t hi_bits = pat_high[p] << kTileBits;
         const int te = pat_start[p + 1];
-        for (int t = pat_start[p]; t < te; ++t) {
+        for (int t = ta; t < te;) {
           const uint32_t ml = term_low[t];
-          const uint32_t mfull = ml | hi_bits;
           const T co = term_odd[t], ce = term_even[t];
-          if (co == ce) {
-#pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-              const int r = rg + RG * m;
-              T xp[VW];
-              VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
-#pragma unroll
-              for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-              const int r = rg + RG * m;
-              const T c = (__popc((row0 + (uint32_t)r) & mfull) & 1) ? co : ce;
-              if (c != (T)0) {
-                T xp[VW];
-                VecIO<T, VW>::ld_rw(xp, P + (r ^ (int)ml) * BS + lane * VW);
-#pragma unroll
-                for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
-              }
-            }
+          if (co == ce && t + 1 < te && term_odd[t + 1] == term_even[t + 1]) {
+            apply2_uniform<T, VW, RPT>(y, roff, P, (int)ml * BS, co, P, (int)term_low[t + 1] * BS,
+                                       term_odd[t + 1]);
+            t += 2;
+            continue;
           }
+          apply_term<T, VW, RPT, RG>(y, roff, rg, P, ml | hi_bits, (int)ml * BS, ml, co, ce, row0);
+          ++t;
         }
         release();
+        p = pn;
       }
       if (aborted) break;
       // Z = (H W) M + W_prev Cp, row by row, with the W_j^T Z partial sums
       const T* Pp = nullptr;
       if (has_prev) {
-        if (!acquire(sp)) {
+        if (!acquire(sp, 0)) {
           aborted = true;
           break;
         }
@@ -805,7 +857,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           }
         if (has_prev) {
           T xp[VW];
-          VecIO<T, VW>::ld_rw(xp, Pp + r * BS + lane * VW);
+          VecIO<T, VW>::ld_rw(xp, Pp + roff[m]);
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -1444,9 +1496,10 @@ static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a0, cudaStream_
   }
   // Deepest ring (up to 6 slots) that fits beside this Hamiltonian's term tables.
   SpmmArgs a = a0;
-  a.stages = 6;
-  while (a.stages > 2 && tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages) > (size_t)optin)
-    --a.stages;
+  a.stages = 6;  // a multiple of kProducerWarps
+  while (a.stages > kProducerWarps &&
+         tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages) > (size_t)optin)
+    a.stages -= kProducerWarps;
   const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages);
   k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
