@@ -198,9 +198,11 @@ rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta, int n_v, 
 /* Y = H X for a caller-owned device block of n_cols columns stored state-major,
  * vector-minor (element (s, c) at s*n_cols + c), float64 (RDM_FP64) or float32
  * (RDM_FP32). n_cols must be 2^m times 4 (FP32) or 2 (FP64), at most 32 (FP32) or
- * 16 (FP64). X and Y must not overlap. Asynchronous on the context's stream. This
- * is the SpMM of the hot path (the matrix-vector products of Sec. 2.4), exposed
- * for verification. */
+ * 16 (FP64). X and Y must not overlap. Asynchronous on the context's stream,
+ * except when the block takes the tiled SpMM (32-byte rows: n_cols = 8 FP32 or
+ * 4 FP64, N >= 10): then the call waits for the kernel to read back its copy-ring
+ * status (RDM_ECUDA if a copy wait gave up). This is the SpMM of the hot path (the
+ * matrix-vector products of Sec. 2.4), exposed for verification. */
 rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const void* x, void* y,
                                  int n_cols);
 

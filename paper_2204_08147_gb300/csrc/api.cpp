@@ -99,6 +99,33 @@ rdm_status compile_model(const rdm_model* m, HostModel* out) {
   return RDM_OK;
 }
 
+// Sorted distinct m_lo of the diagonal terms with both a high and a low part (TileDiag).
+static std::vector<uint32_t> tile_diag_mlo(const HostModel& h) {
+  std::vector<uint32_t> lo;
+  for (const DiagTerm& d : h.diags)
+    if ((d.mask >> kTileBits) != 0 && (d.mask & (uint32_t)(kTileRows - 1)) != 0)
+      lo.push_back(d.mask & (uint32_t)(kTileRows - 1));
+  std::sort(lo.begin(), lo.end());
+  lo.erase(std::unique(lo.begin(), lo.end()), lo.end());
+  return lo;
+}
+
+// Row layout of the A table (TileDiag) for the sorted groups mlo: A_q takes one entry
+// per row group when its sign depends on the row group, else one entry. Returns the
+// entries per tile.
+static int tile_diag_layout(const std::vector<uint32_t>& mlo, uint32_t* dep, int off[8]) {
+  constexpr uint32_t kRG = 1u << kTileRegShift;
+  *dep = 0;
+  for (uint32_t m : mlo)
+    if (m & (kRG - 1)) *dep |= 1u << (m >> kTileRegShift);
+  int n = 0;
+  for (int q = 0; q < 8; ++q) {
+    off[q] = n;
+    n += ((*dep >> q) & 1u) ? (int)kRG : 1;
+  }
+  return n;
+}
+
 // Groups the flip terms by m_high = mask >> kTileBits for the tiled SpMM.
 void make_term_image(const HostModel& h, TermImage* img) {
   std::map<uint32_t, std::vector<const FlipTerm*>> groups;
@@ -130,6 +157,46 @@ void make_term_image(const HostModel& h, TermImage* img) {
     pat_flags.push_back(flags);
   }
   pat_start.push_back((int)term_low.size());
+  // The diagonal split of the tiled SpMM: low table, K_0 terms, mixed groups by m_lo
+  // (std::map keeps them in ascending m_lo, hence ascending m_lo >> kTileRegShift).
+  std::vector<double> dg_low(kTileRows, 0.0);
+  std::vector<uint32_t> dg_thi, dg_mlo;
+  std::vector<double> dg_tc;
+  std::vector<int> dg_slot{0}, dg_hstart(9, 0);
+  {
+    std::map<uint32_t, std::vector<const DiagTerm*>> mixed;
+    std::vector<const DiagTerm*> k0;
+    for (const DiagTerm& d : h.diags) {
+      const uint32_t hi = d.mask >> kTileBits, lo = d.mask & (uint32_t)(kTileRows - 1);
+      if (hi == 0) {
+        for (uint32_t r = 0; r < (uint32_t)kTileRows; ++r)
+          dg_low[r] += (__builtin_popcount(r & lo) & 1) ? -d.c : d.c;
+      } else if (lo == 0) {
+        k0.push_back(&d);
+      } else {
+        mixed[lo].push_back(&d);
+      }
+    }
+    for (const DiagTerm* d : k0) {
+      dg_thi.push_back(d->mask >> kTileBits);
+      dg_tc.push_back(d->c);
+    }
+    dg_slot.push_back((int)dg_thi.size());
+    for (auto& kv : mixed) {
+      dg_mlo.push_back(kv.first);
+      for (const DiagTerm* d : kv.second) {
+        dg_thi.push_back(d->mask >> kTileBits);
+        dg_tc.push_back(d->c);
+      }
+      dg_slot.push_back((int)dg_thi.size());
+    }
+    for (int hh = 0; hh <= 8; ++hh) {
+      int g = 0;
+      while (g < (int)dg_mlo.size() && (int)(dg_mlo[g] >> kTileRegShift) < hh) ++g;
+      dg_hstart[hh] = g;
+    }
+  }
+  img->dg_entries = tile_diag_layout(dg_mlo, &img->dg_dep, img->dg_off);
   const bool tiled = h.n >= kTileBits;
   img->n_pat = tiled ? (int)pat_high.size() : 0;
   img->n_terms = tiled ? (int)term_low.size() : 0;
@@ -149,6 +216,14 @@ void make_term_image(const HostModel& h, TermImage* img) {
   img->off_term_low = put(term_low.data(), term_low.size() * 4);
   img->off_term_odd = put(term_odd.data(), term_odd.size() * 8);
   img->off_term_even = put(term_even.data(), term_even.size() * 8);
+  img->n_dg_groups = (int)dg_mlo.size();
+  img->n_dg_terms = (int)dg_thi.size();
+  img->off_dg_low = put(dg_low.data(), dg_low.size() * 8);
+  img->off_dg_mlo = put(dg_mlo.data(), dg_mlo.size() * 4);
+  img->off_dg_hstart = put(dg_hstart.data(), dg_hstart.size() * 4);
+  img->off_dg_thi = put(dg_thi.data(), dg_thi.size() * 4);
+  img->off_dg_tc = put(dg_tc.data(), dg_tc.size() * 8);
+  img->off_dg_slot = put(dg_slot.data(), dg_slot.size() * 4);
 }
 
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
@@ -163,6 +238,18 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   t.term_low = reinterpret_cast<const uint32_t*>(dev + img.off_term_low);
   t.term_odd = reinterpret_cast<const double*>(dev + img.off_term_odd);
   t.term_even = reinterpret_cast<const double*>(dev + img.off_term_even);
+  TileDiag& d = t.dg;
+  d.n_groups = img.n_dg_groups;
+  d.n_terms = img.n_dg_terms;
+  d.dep = img.dg_dep;
+  for (int q = 0; q < 8; ++q) d.off[q] = img.dg_off[q];
+  d.n_entries = img.dg_entries;
+  d.low = reinterpret_cast<const double*>(dev + img.off_dg_low);
+  d.mlo = reinterpret_cast<const uint32_t*>(dev + img.off_dg_mlo);
+  d.hstart = reinterpret_cast<const int*>(dev + img.off_dg_hstart);
+  d.thi = reinterpret_cast<const uint32_t*>(dev + img.off_dg_thi);
+  d.tc = reinterpret_cast<const double*>(dev + img.off_dg_tc);
+  d.slot_start = reinterpret_cast<const int*>(dev + img.off_dg_slot);
 }
 
 // ---------------------------------------------------------------- layout
@@ -260,6 +347,7 @@ struct Plan {
   int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
   bool gauss;                         // Gaussian bath vectors are generated once into a buffer
   bool store;                         // keep all k+1 Krylov blocks (no second pass)
+  size_t tk_bytes;                    // K table of the tiled diagonal (0 if untiled)
 };
 
 static size_t plan_bytes(const Plan& p) {
@@ -275,7 +363,7 @@ static size_t plan_bytes(const Plan& p) {
   a.take<double>((size_t)p.nbc * ng * nv);
   a.take<double>((size_t)p.n_v_pad * 65);
   a.take<uint32_t>(4);
-  a.take<char>((size_t)L.D * L.elem);  // diagonal of H
+  a.take<char>(p.tk_bytes);
   if (p.gauss) a.take<char>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits) * L.elem);
   return a.off + 256;
 }
@@ -295,6 +383,15 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   p.nbc = 1;
   p.gauss = o->vec_dist == RDM_GAUSS;
   p.store = false;
+  if (layout_tiled(p.L)) {
+    uint32_t dep;
+    int off[8];
+    const int n_entries = tile_diag_layout(tile_diag_mlo(hm), &dep, off);
+    p.tk_bytes = (size_t)(p.L.D >> kTileBits) * (size_t)tile_diag_stride(n_entries, p.L.elem) *
+                 (size_t)p.L.elem;
+  } else {
+    p.tk_bytes = 0;
+  }
   if (o->passes != RDM_PASSES_RECOMPUTE) {
     Plan q = p;
     q.store = true;
@@ -437,6 +534,8 @@ extern "C" void rdm_destroy_hamiltonian(rdm_ham* ham) {
   if (!ham) return;
   cudaSetDevice(ham->ctx->device);
   if (ham->d_terms) cudaFree(ham->d_terms);
+  for (void* p : ham->d_apply_aux)
+    if (p) cudaFree(p);
   delete ham;
 }
 
@@ -488,10 +587,40 @@ extern "C" rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const v
   a.n_diag = (int)ham->model.diags.size();
   a.w = x;
   a.z = y;
+  cudaStream_t s = ham->ctx->stream;
+  const bool tiled = layout_tiled(L) && ham->tiled.n_pat > 0;
+  uint32_t* err = nullptr;
+  if (tiled) {
+    // The tiled SpMM reads the K table of the diagonal and reports copy-ring
+    // failures in an error word; both are kept per Hamiltonian and precision.
+    const int pi = precision == RDM_FP32 ? 1 : 0;
+    if (!ham->d_apply_aux[pi]) {
+      const size_t tk = (size_t)(L.D >> kTileBits) *
+                        (size_t)tile_diag_stride(ham->tiled.dg.n_entries, L.elem) * (size_t)L.elem;
+      void* p = nullptr;
+      CK(cudaMalloc(&p, 256 + tk));
+      ham->d_apply_aux[pi] = p;
+      CK(launch_tile_diag(L, ham->tiled.dg, static_cast<char*>(p) + 256, s));
+    }
+    err = static_cast<uint32_t*>(ham->d_apply_aux[pi]);
+    a.tiled = ham->tiled;
+    a.tile_k = static_cast<char*>(ham->d_apply_aux[pi]) + 256;
+    a.err = err;
+    CK(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  }
   Profiler& pr = ham->ctx->prof;
-  const int ev = pr.begin(kKApply, ham->ctx->stream, true);
-  CK(launch_spmm(L, kModeApply, a, ham->ctx->stream));
-  pr.end(kKApply, ev, ham->ctx->stream, 2.0 * (double)bytes);
+  const int ev = pr.begin(kKApply, s, true);
+  CK(launch_spmm(L, kModeApply, a, s));
+  pr.end(kKApply, ev, s, 2.0 * (double)bytes);
+  if (tiled) {
+    uint32_t h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h_err) {
+      set_error("rdm_apply_hamiltonian: a bulk-copy wait in the SpMM kernel gave up (device error)");
+      return RDM_ECUDA;
+    }
+  }
   return RDM_OK;
 }
 
@@ -619,7 +748,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   double* d_gram = ar.take<double>((size_t)p.nbc * ng * nv);
   double* d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
   uint32_t* d_flags = ar.take<uint32_t>(4);
-  char* d_diag = ar.take<char>((size_t)L.D * L.elem);
+  char* d_tk = ar.take<char>(p.tk_bytes);
   char* d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
   const size_t cstride = (size_t)ng * nv;
   auto MZ = [&](int j) { return coef + (size_t)j * cstride; };                   // j = 1..k+1
@@ -638,7 +767,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   sa.diags = ham->d_diags;
   sa.n_diag = (int)hm.diags.size();
   sa.tiled = ham->tiled;
-  sa.diag = d_diag;
+  sa.tile_k = p.tk_bytes ? d_tk : nullptr;
   sa.err = d_flags + 1;
 
   const double blk_b = (double)L.block_bytes();
@@ -655,8 +784,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   };
   uint64_t h2d = 0, d2h = 0;
 
-  // Once per estimate: the diagonal of H and (Gaussian case) the bath vectors.
-  CK(counted([&] { return launch_diag(L, ham->d_diags, (int)hm.diags.size(), d_diag, s); }));
+  // Once per estimate: the per-tile diagonal table and (Gaussian case) the bath vectors.
+  if (p.tk_bytes) CK(counted([&] { return launch_tile_diag(L, ham->tiled.dg, d_tk, s); }));
   if (p.gauss) {
     CK(counted([&] {
       return launch_gauss_norms(d_b, n_v, seed, o->first_vector, d_norm + p.n_v_pad, d_norm, s);

@@ -114,23 +114,33 @@ __device__ __forceinline__ unsigned group_mask(int tpr) {
 
 // Fixed-order block reduction of NV float64 values per thread into per-block
 // partials: partials[((slice*gridx + bx)*G_s + lane*NG + g)*NVG + v] where
-// vals[g*NVG + v] belongs to group g of the thread.
+// vals[g*NVG + v] belongs to group g of the thread and lane = threadIdx.x % tpr
+// (tpr <= 8, a power of two). A butterfly over the lanes of a warp with the same
+// lane, then the warps' sums added in warp order: the same order on every run.
 template <int NG, int NVG>
 __device__ void block_reduce_store(const double* vals, int tpr, double* partials, int gs) {
   constexpr int NV = NG * NVG;
-  __shared__ double red[kThreads * NV];
-  for (int v = 0; v < NV; ++v) red[threadIdx.x * NV + v] = vals[v];
+  constexpr int kWarps = kThreads / 32;
+  __shared__ double red[kWarps * 8 * NV];
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  double v[NV];
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    double x = vals[e];
+    for (int o = tpr; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[e] = x;
+  }
+  if (wl < tpr) {
+#pragma unroll
+    for (int e = 0; e < NV; ++e) red[(warp * tpr + wl) * NV + e] = v[e];
+  }
   __syncthreads();
-  const int rpb = kThreads / tpr;
-  if ((int)threadIdx.x < tpr) {
-    const int lane = threadIdx.x;
-    const size_t base =
-        ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * gs + (size_t)lane * NG) * NVG;
-    for (int v = 0; v < NV; ++v) {
-      double s = 0.0;
-      for (int r = 0; r < rpb; ++r) s += red[(r * tpr + lane) * NV + v];
-      partials[base + v] = s;
-    }
+  if ((int)threadIdx.x < tpr * NV) {
+    const int lane = threadIdx.x / NV, e = threadIdx.x % NV;
+    double sum = 0.0;
+    for (int w = 0; w < kWarps; ++w) sum += red[(w * tpr + lane) * NV + e];
+    const size_t base = ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * gs + (size_t)lane * NG) * NVG;
+    partials[base + e] = sum;
   }
 }
 
@@ -216,22 +226,36 @@ __global__ void k_gauss_fill(int64_t d_b, uint64_t seed, int64_t l0, const doubl
   }
 }
 
+// A table of the tiled diagonal (TileDiag): one block per tile (grid stride). The block
+// first sums K_0 .. K_G of the tile (float64, shared memory), then thread rg writes
+// A_q(tile, rg) of every row-group-dependent character q and thread 0 the others.
 template <typename T>
-__global__ void k_diag(int64_t D, const DiagTerm* diags, int nd, T* out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* c = reinterpret_cast<double*>(smem_raw);
-  uint32_t* m = reinterpret_cast<uint32_t*>(c + nd);
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    c[i] = diags[i].c;
-    m[i] = diags[i].mask;
-  }
-  __syncthreads();
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < D;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t su = (uint32_t)s;
-    double d = 0.0;
-    for (int t = 0; t < nd; ++t) d += (__popc(su & m[t]) & 1) ? -c[t] : c[t];
-    out[s] = (T)d;
+__global__ void __launch_bounds__(kThreads) k_tile_diag(int64_t tiles, TileDiag dg, int stride, T* out) {
+  extern __shared__ __align__(16) unsigned char smem_k[];
+  double* sK = reinterpret_cast<double*>(smem_k);  // [G + 1]
+  constexpr int kRG = 1 << kTileRegShift;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint32_t ut = (uint32_t)t;
+    for (int g = threadIdx.x; g <= dg.n_groups; g += blockDim.x) {
+      double k = 0.0;
+      for (int i = dg.slot_start[g]; i < dg.slot_start[g + 1]; ++i)
+        k += (__popc(ut & dg.thi[i]) & 1) ? -dg.tc[i] : dg.tc[i];
+      sK[g] = k;
+    }
+    __syncthreads();
+    T* o = out + t * stride;
+    for (int rg = threadIdx.x; rg < kRG; rg += blockDim.x) {
+      for (int q = 0; q < 8; ++q) {
+        const bool dep = (dg.dep >> q) & 1u;
+        if (!dep && rg != 0) continue;
+        double a = q == 0 ? sK[0] : 0.0;
+        for (int g = dg.hstart[q]; g < dg.hstart[q + 1]; ++g)
+          a += (__popc((uint32_t)rg & dg.mlo[g]) & 1) ? -sK[1 + g] : sK[1 + g];
+        o[dg.off[q] + (dep ? rg : 0)] = (T)a;
+      }
+    }
+    for (int e = dg.n_entries + threadIdx.x; e < stride; e += blockDim.x) o[e] = (T)0;
+    __syncthreads();
   }
 }
 
@@ -382,14 +406,15 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
 
 // ---------------------------------------------------------------- tiled SpMM
 //
-// Same result as k_spmm, organised around 256-state tiles of one slice (256 rows x
-// 128 bytes = 32 KB) held in shared memory. The own tile and, one after another,
-// every partner tile tile ^ m_high that an active term needs are fetched with TMA
-// bulk copies (cp.async.bulk, completion on an mbarrier), double-buffered so the
-// next partner streams in while the current one is consumed. Every flip term is
-// then a shared-memory read. Blocks walk the slices in order and the tiles of a
-// slice with a grid stride, so all SMs work on neighbouring tiles of one slice and
-// partner tiles are mostly served from L2.
+// Same result as k_spmm, organised around tiles of 2^kTileBits consecutive states of
+// one slice (32 KB) held in shared memory. The own tile and, one after another, every
+// partner tile tile ^ m_high that an active term needs are fetched with TMA bulk
+// copies (cp.async.bulk, completion on an mbarrier) through a ring of slots, so later
+// tiles stream in while the current one is consumed. Every flip term is then a
+// shared-memory (or register) read; the diagonal is rebuilt per tile from a small
+// table (TileDiag). The blocks walk the (slice, tile) pairs with one grid stride,
+// slice by slice, so all SMs work on neighbouring tiles of one slice and partner
+// tiles are mostly served from L2.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -406,13 +431,6 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 // Bulk copy with an L2 eviction-priority policy (createpolicy value).
 __device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
@@ -442,39 +460,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after a fixed number of polls (the copy engine never
-// needs more than microseconds; giving up means something is broken).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
-// Producer/consumer layout of the tiled SpMM: warp 8 issues TMA bulk copies into a
-// ring of kStages shared-memory slots; the consumer warps read them. A slot holds one
-// 32 KB tile (kTileRows rows of a slice) plus, for the own tile, its kTileRows
-// diagonal entries. Per tile the stage sequence is: own tile, each needed partner tile,
-// then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes) and
-// empty barriers (one arrival per consumer warp) order the ring.
+// Producer/consumer layout of the tiled SpMM: warps 8 and 9 issue TMA bulk copies
+// into a ring of shared-memory slots; the consumer warps read them. A slot holds one
+// 32 KB tile (kTileRows rows of a slice) plus, for the own tile, its row of the K
+// table of the diagonal. Per tile the stage sequence is: own tile, each needed partner
+// tile, then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes)
+// and empty barriers (one arrival per consumer warp) order the ring.
 constexpr int kConsumerWarps = 8;
 constexpr int kProducerWarps = 2;  // each issues the copies of every other ring slot
 constexpr int kTiledThreads = (kConsumerWarps + kProducerWarps) * 32;
 constexpr uint32_t kTileBytes = (uint32_t)kTileRows * kTiledLanes * 16;  // 32 KB
-template <typename T>
-__host__ __device__ constexpr uint32_t slot_bytes() {
-  return kTileBytes + (uint32_t)kTileRows * (uint32_t)sizeof(T);
-}
 constexpr int kMaxStages = 8;
+// Slot = tile + the A-table row of the diagonal (rounded to 128 bytes).
+__host__ __device__ inline uint32_t tiled_slot_bytes(int n_entries, int elem) {
+  return kTileBytes + ((uint32_t)(tile_diag_stride(n_entries, elem) * elem) + 127u) / 128u * 128u;
+}
 
 template <typename T>
-__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int stages) {
-  constexpr uint32_t kSlotBytes = slot_bytes<T>();
-  size_t off = (size_t)stages * kSlotBytes;
+__host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int n_entries, int stages) {
+  size_t off = (size_t)stages * tiled_slot_bytes(n_entries, (int)sizeof(T));
   off += 2 * kMaxStages * 8 + 64;                  // full/empty barriers, control
-  off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the 8 lanes
+  off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the lanes
   off += (size_t)kConsumerWarps * kTiledLanes * 16 * 8;  // reduction scratch
   off += (size_t)n_pat * 12 + 4;                   // pat_high, pat_flags, pat_start (+1)
   off = (off + 15) / 16 * 16;
+  off += (size_t)kTileRows * sizeof(T);            // low table of the diagonal
   off += (size_t)n_terms * (4 + 2 * sizeof(T));
   return off + 64;
 }
@@ -529,20 +540,41 @@ __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW]
   }
 }
 
+// Rows of a consumer thread and their partners: row rg + RG m (m = 0..7) of a tile sits
+// at element offset rgoff + m * kStep (rgoff = rg * BS + lane * VW, kStep = RG * BS,
+// both powers of two apart), so under an in-tile mask ml = (mh << log2 RG) | mlow its
+// partner row rg ^ mlow + RG (m ^ mh) sits at (rgoff ^ mlow * BS | mh * kStep) ^ m * kStep.
+// With mh = 0 that is a base plus a constant per row.
+template <int RG, int BS>
+__device__ __forceinline__ int partner_base(int rgoff, uint32_t ml) {
+  return (rgoff ^ (int)((ml & (uint32_t)(RG - 1)) * BS)) | (int)((ml / RG) * (uint32_t)(RG * BS));
+}
+
 // y[m] += c * P[row m ^ ml] for one term whose coefficient depends on the parity of
 // (row0 + row) & mparity (c_odd / c_even), rows of this thread.
-template <typename T, int VW, int RPT, int RG>
-__device__ __forceinline__ void apply_term(T (&y)[RPT][VW], const int (&roff)[RPT], int rg, const T* P,
-                                           uint32_t mparity, int mlb, uint32_t ml, T co, T ce,
-                                           uint32_t row0) {
-  (void)ml;
+template <typename T, int VW, int RPT, int RG, int BS>
+__device__ __forceinline__ void apply_term(T (&y)[RPT][VW], int rgoff, int rg, const T* P, uint32_t ml,
+                                           uint32_t mparity, T co, T ce, uint32_t row0) {
+  constexpr int kStep = RG * BS;
+  const int x = partner_base<RG, BS>(rgoff, ml);
+  const bool flat = ml < (uint32_t)RG;  // mh = 0: partner offsets x + m * kStep
   if (co == ce) {
+    if (flat) {
 #pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-      T xp[VW];
-      VecIO<T, VW>::ld_rw(xp, P + (roff[m] ^ mlb));
+      for (int m = 0; m < RPT; ++m) {
+        T xp[VW];
+        VecIO<T, VW>::ld_rw(xp, P + x + m * kStep);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+        for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        T xp[VW];
+        VecIO<T, VW>::ld_rw(xp, P + (x ^ (m * kStep)));
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
+      }
     }
   } else {
 #pragma unroll
@@ -551,7 +583,7 @@ __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], const int (&roff)[RP
       const T c = (__popc((row0 + r) & mparity) & 1) ? co : ce;
       if (c != (T)0) {
         T xp[VW];
-        VecIO<T, VW>::ld_rw(xp, P + (roff[m] ^ mlb));
+        VecIO<T, VW>::ld_rw(xp, P + (x ^ (m * kStep)));
 #pragma unroll
         for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
       }
@@ -560,17 +592,53 @@ __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], const int (&roff)[RP
 }
 
 // Two uniform-coefficient terms at once (loads of both issued before their FMAs).
-template <typename T, int VW, int RPT>
-__device__ __forceinline__ void apply2_uniform(T (&y)[RPT][VW], const int (&roff)[RPT], const T* PA, int mlbA,
-                                               T cA, const T* PB, int mlbB, T cB) {
+template <typename T, int VW, int RPT, int RG, int BS>
+__device__ __forceinline__ void apply2_uniform(T (&y)[RPT][VW], int rgoff, const T* PA, uint32_t mlA, T cA,
+                                               const T* PB, uint32_t mlB, T cB) {
+  constexpr int kStep = RG * BS;
+  const int xa = partner_base<RG, BS>(rgoff, mlA), xb = partner_base<RG, BS>(rgoff, mlB);
+  if (mlA < (uint32_t)RG && mlB < (uint32_t)RG) {
 #pragma unroll
-  for (int m = 0; m < RPT; ++m) {
-    T a[VW], b[VW];
-    VecIO<T, VW>::ld_rw(a, PA + (roff[m] ^ mlbA));
-    VecIO<T, VW>::ld_rw(b, PB + (roff[m] ^ mlbB));
+    for (int m = 0; m < RPT; ++m) {
+      T a[VW], b[VW];
+      VecIO<T, VW>::ld_rw(a, PA + xa + m * kStep);
+      VecIO<T, VW>::ld_rw(b, PB + xb + m * kStep);
 #pragma unroll
-    for (int v = 0; v < VW; ++v) y[m][v] = fma(cB, b[v], fma(cA, a[v], y[m][v]));
+      for (int v = 0; v < VW; ++v) y[m][v] = fma(cB, b[v], fma(cA, a[v], y[m][v]));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      T a[VW], b[VW];
+      VecIO<T, VW>::ld_rw(a, PA + (xa ^ (m * kStep)));
+      VecIO<T, VW>::ld_rw(b, PB + (xb ^ (m * kStep)));
+#pragma unroll
+      for (int v = 0; v < VW; ++v) y[m][v] = fma(cB, b[v], fma(cA, a[v], y[m][v]));
+    }
   }
+}
+
+// Diagonal of H on this thread's eight rows rg + RG m of a tile, from the tile's A-table
+// row hk (TileDiag): low[r] + sum_q A_q (-1)^popc(q & m), one 8-point Walsh-Hadamard
+// transform of the eight A_q.
+template <typename T, int RPT, int RG>
+__device__ __forceinline__ void tile_diagonal(T (&dg)[RPT], const T* low, const T* hk, int rg,
+                                              const TileDiag& td) {
+  static_assert(RPT == 8 && RG == (1 << kTileRegShift), "eight register rows per thread");
+  T A[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) A[q] = hk[td.off[q] + (((td.dep >> q) & 1u) ? rg : 0)];
+#pragma unroll
+  for (int len = 1; len < 8; len <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (!(i & len)) {
+        const T u = A[i], w = A[i | len];
+        A[i] = u + w;
+        A[i | len] = u - w;
+      }
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) dg[m] = low[rg + RG * m] + A[m];
 }
 
 template <typename T, int DS, int MODE>
@@ -585,12 +653,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   constexpr int RGL = (RG >= 256) ? 8 : (RG >= 128) ? 7 : (RG >= 64) ? 6 : 5;  // log2(RG)
   constexpr int RPT = kTileRows / RG;            // rows per consumer thread (8)
   const int kStages = a.stages;
-  constexpr uint32_t kSlotBytes = slot_bytes<T>();
   static_assert(RPT == 8, "eight rows per consumer thread");
-  static_assert((1 << RGL) == RG, "row groups are a power of two");
+  static_assert((1 << RGL) == RG && RGL == kTileRegShift, "row groups are the low tile bits");
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;
   const int npat = tt.n_pat, nterm = tt.n_terms;
+  const int hstride = tile_diag_stride(tt.dg.n_entries, (int)sizeof(T));
+  const uint32_t kSlotBytes = tiled_slot_bytes(tt.dg.n_entries, (int)sizeof(T));
   unsigned char* const ring = smem;
   uint64_t* const full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kSlotBytes);
   uint64_t* const empty = full + kMaxStages;
@@ -603,7 +672,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   int* const pat_start = reinterpret_cast<int*>(pat_flags + npat);
   size_t off = (size_t)(reinterpret_cast<unsigned char*>(pat_start + npat + 1) - smem);
   off = (off + 15) / 16 * 16;
-  T* const term_odd = reinterpret_cast<T*>(smem + off);
+  T* const s_low = reinterpret_cast<T*>(smem + off);
+  T* const term_odd = s_low + kTileRows;
   T* const term_even = term_odd + nterm;
   uint32_t* const term_low = reinterpret_cast<uint32_t*>(term_even + nterm);
 
@@ -617,6 +687,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     term_odd[i] = (T)tt.term_odd[i];
     term_even[i] = (T)tt.term_even[i];
   }
+  for (int i = threadIdx.x; i < kTileRows; i += blockDim.x) s_low[i] = (T)tt.dg.low[i];
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&full[i], 1);
@@ -628,7 +699,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   __syncthreads();
 
   const int warp = threadIdx.x >> 5;
-  const int64_t tps = L.D >> kTileBits;
+  const int tile_log = L.n_bits - kTileBits;  // tiles per slice = 2^tile_log
+  const int64_t n_tiles = (int64_t)L.n_slices << tile_log;
+  const uint32_t tile_mask = (uint32_t)(((int64_t)1 << tile_log) - 1);
   const bool has_prev = a.w_prev != nullptr;
 
   if (warp >= kConsumerWarps) {
@@ -642,51 +715,51 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     // W_{j-1} tiles are read once: let them leave first.
     const uint64_t keep = policy_evict_last();
     const uint64_t stream = policy_evict_first();
+    const uint32_t hk_bytes = (uint32_t)hstride * (uint32_t)sizeof(T);
+    const T* const hk_table = reinterpret_cast<const T*>(a.tile_k);
     uint32_t seq = 0;
     bool stop = false;
-    for (int slice = 0; slice < L.n_slices && !stop; ++slice) {
+    for (int64_t gt = blockIdx.x; gt < n_tiles && !stop; gt += gridDim.x) {
+      const int slice = (int)(gt >> tile_log);
+      const uint32_t ut = (uint32_t)gt & tile_mask;
       const size_t soff = (size_t)slice * L.D * BS;
       const T* W = reinterpret_cast<const T*>(a.w) + soff;
       const T* Wp = has_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
-      for (int64_t tix = blockIdx.x; tix < tps && !stop; tix += gridDim.x) {
-        const uint32_t ut = (uint32_t)tix;
-        // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
-        int kind = -1;
-        while (true) {
-          if (seq % kProducerWarps == q) {
-            const int slot = (int)(seq % (uint32_t)kStages);
-            if (seq >= (uint32_t)kStages &&
-                !ring_wait(&empty[slot], ((seq / (uint32_t)kStages) - 1u) & 1u, abort_flag)) {
-              stop = true;
-              break;
-            }
-            unsigned char* dst = ring + (size_t)slot * kSlotBytes;
-            fence_proxy_async();
-            if (kind == -1) {
-              mbar_expect_tx(&full[slot], kTileBytes + kTileRows * (uint32_t)sizeof(T));
-              bulk_load_hint(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], keep);
-              bulk_load_hint(dst + kTileBytes, reinterpret_cast<const T*>(a.diag) + ((size_t)ut << kTileBits),
-                             kTileRows * (uint32_t)sizeof(T), &full[slot], stream);
-            } else if (kind == -2) {
-              mbar_expect_tx(&full[slot], kTileBytes);
-              bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
-            } else {
-              mbar_expect_tx(&full[slot], kTileBytes);
-              bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
-                             &full[slot], keep);
-            }
-          }
-          ++seq;
-          // next stage of this tile
-          if (kind == -2) break;
-          const int p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
-          if (p < npat) {
-            kind = p;
-          } else if (has_prev) {
-            kind = -2;
-          } else {
+      // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
+      int kind = -1;
+      while (true) {
+        if (seq % kProducerWarps == q) {
+          const int slot = (int)(seq % (uint32_t)kStages);
+          if (seq >= (uint32_t)kStages &&
+              !ring_wait(&empty[slot], ((seq / (uint32_t)kStages) - 1u) & 1u, abort_flag)) {
+            stop = true;
             break;
           }
+          unsigned char* dst = ring + (size_t)slot * kSlotBytes;
+          fence_proxy_async();
+          if (kind == -1) {
+            mbar_expect_tx(&full[slot], kTileBytes + hk_bytes);
+            bulk_load_hint(dst, W + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], keep);
+            bulk_load_hint(dst + kTileBytes, hk_table + (size_t)ut * hstride, hk_bytes, &full[slot], keep);
+          } else if (kind == -2) {
+            mbar_expect_tx(&full[slot], kTileBytes);
+            bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
+          } else {
+            mbar_expect_tx(&full[slot], kTileBytes);
+            bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
+                           &full[slot], keep);
+          }
+        }
+        ++seq;
+        // next stage of this tile
+        if (kind == -2) break;
+        const int p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
+        if (p < npat) {
+          kind = p;
+        } else if (has_prev) {
+          kind = -2;
+        } else {
+          break;
         }
       }
     }
@@ -697,11 +770,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   // -------------------------------------------------- consumers
   const int lane = threadIdx.x % LPR;  // 16-byte column chunk of a row
   const int rg = threadIdx.x / LPR;    // row group: rows rg + RG*m
-  // Element offsets of this thread's rows in a tile; the partner of row r under an
-  // in-tile mask ml is at offset roff ^ (ml * BS) (BS is a power of two > lane*VW).
-  int roff[RPT];
-#pragma unroll
-  for (int m = 0; m < RPT; ++m) roff[m] = (rg + RG * m) * BS + lane * VW;
+  constexpr int kStep = RG * BS;        // elements between a thread's rows
+  const int rgoff = rg * BS + lane * VW;  // element offset of its first row in a tile
   const bool leader = (threadIdx.x & 31) == 0;
   uint32_t seq = 0;
   bool aborted = false;
@@ -718,129 +788,188 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     if (leader) mbar_arrive(&empty[seq % kStages]);
     ++seq;
   };
+  // Partials of W_j^T Z of this block for one slice (zero for a slice it has no tile
+  // of); every (slice, block) entry is written once.
+  const int gs = BS / DS;
+  auto partial_base = [&](int slice) -> size_t {
+    return ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
+  };
 
-  for (int slice = 0; slice < L.n_slices; ++slice) {
-    const size_t soff = (size_t)slice * L.D * BS;
-    T* __restrict__ Z = reinterpret_cast<T*>(a.z) + soff;
-    consumers_sync_or(false);
-    if (threadIdx.x < LPR * NV) {  // this slice's mixing coefficients
-      const int ln = threadIdx.x / NV, e = threadIdx.x % NV;
-      const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
-      s_mz[ln * 16 + e] = (T)a.mz[gidx];
-      s_cp[ln * 16 + e] = has_prev ? (T)a.cp[gidx] : (T)0;
-    }
-    consumers_sync_or(false);
-    T mz[NV], cp[NV];  // this lane's mixing coefficients, kept in registers
+  T acc[NV];  // W_j^T Z sums of this lane's bath-vector groups
 #pragma unroll
-    for (int e = 0; e < NV; ++e) {
-      mz[e] = s_mz[lane * 16 + e];
-      cp[e] = s_cp[lane * 16 + e];
-    }
-    T acc[NV];
-#pragma unroll
-    for (int e = 0; e < NV; ++e) acc[e] = (T)0;
+  for (int e = 0; e < NV; ++e) acc[e] = (T)0;
+  T* __restrict__ Z = nullptr;
+  int cur = -1;       // slice of the tiles in progress
+  int unwritten = 0;  // slices [unwritten, n_slices) have no partials yet
 
-    for (int64_t tix = blockIdx.x; tix < tps && !aborted; tix += gridDim.x) {
-      const uint32_t ut = (uint32_t)tix;
-      const uint32_t row0 = ut << kTileBits;
-      const unsigned char* sp;
-      // own tile: diagonal and in-tile terms
+  // The consumers walk the same (slice, tile) sequence as the producers. At every
+  // change of slice (and at the end) they close the finished slice; every consumer
+  // thread passes the same barriers, also after an abort.
+  for (int64_t gt = blockIdx.x;; gt += gridDim.x) {
+    const int slice = gt < n_tiles ? (int)(gt >> tile_log) : L.n_slices;
+    if (slice != cur) {
+      if (consumers_sync_or(aborted)) aborted = true;
+      if (MODE == kModePass1 && !aborted) {
+        if (cur >= 0) {
+          // fixed-order reduction: shuffles within a warp, then the warps in order
+          double v[NV];
+#pragma unroll
+          for (int e = 0; e < NV; ++e) {
+            double x = (double)acc[e];
+#pragma unroll
+            for (int o = LPR; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            v[e] = x;
+          }
+          if ((threadIdx.x & 31) < LPR) {
+#pragma unroll
+            for (int e = 0; e < NV; ++e) red[(warp * LPR + lane) * 16 + e] = v[e];
+          }
+          consumers_sync_or(false);
+          if (threadIdx.x < LPR) {
+            const size_t base = partial_base(cur);
+            for (int e = 0; e < NV; ++e) {
+              double sum = 0.0;
+              for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * LPR + threadIdx.x) * 16 + e];
+              a.partials[base + e] = sum;
+            }
+          }
+          unwritten = cur + 1;
+        }
+        if (threadIdx.x < LPR)
+          for (int c = unwritten; c < slice; ++c)
+            for (int e = 0; e < NV; ++e) a.partials[partial_base(c) + e] = 0.0;
+        unwritten = slice;
+      }
+      if (slice >= L.n_slices) break;
+      cur = slice;
+      Z = reinterpret_cast<T*>(a.z) + (size_t)slice * L.D * BS;
+      consumers_sync_or(false);  // the previous slice's coefficients have been read
+      if (MODE != kModeApply && threadIdx.x < LPR * NV) {
+        const int ln = threadIdx.x / NV, e = threadIdx.x % NV;
+        const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
+        s_mz[ln * 16 + e] = (T)a.mz[gidx];
+        s_cp[ln * 16 + e] = has_prev ? (T)a.cp[gidx] : (T)0;
+      }
+      consumers_sync_or(false);
+#pragma unroll
+      for (int e = 0; e < NV; ++e) acc[e] = (T)0;
+    }
+    if (aborted) continue;
+
+    const uint32_t ut = (uint32_t)gt & tile_mask;
+    const uint32_t row0 = ut << kTileBits;
+    const unsigned char* sp;
+    // own tile: diagonal and in-tile terms
+    if (!acquire(sp, 0)) {
+      aborted = true;
+      continue;
+    }
+    const T* own = reinterpret_cast<const T*>(sp);
+    T xo[RPT][VW], y[RPT][VW];
+    {
+      T dg[RPT];
+      tile_diagonal<T, RPT, RG>(dg, s_low, reinterpret_cast<const T*>(sp + kTileBytes), rg, tt.dg);
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        VecIO<T, VW>::ld_rw(xo[m], own + rgoff + m * kStep);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[m][v] = dg[m] * xo[m][v];
+      }
+    }
+    const int t1 = pat_start[1];
+    for (int t = pat_start[0]; t < t1;) {
+      const uint32_t ml = term_low[t];
+      const T co = term_odd[t], ce = term_even[t];
+      if ((ml & (uint32_t)(RG - 1)) == 0u) {
+        switch (ml >> RGL) {
+          case 1: reg_flip<1, RG>(y, xo, rg, ml, co, ce); break;
+          case 2: reg_flip<2, RG>(y, xo, rg, ml, co, ce); break;
+          case 3: reg_flip<3, RG>(y, xo, rg, ml, co, ce); break;
+          case 4: reg_flip<4, RG>(y, xo, rg, ml, co, ce); break;
+          case 5: reg_flip<5, RG>(y, xo, rg, ml, co, ce); break;
+          case 6: reg_flip<6, RG>(y, xo, rg, ml, co, ce); break;
+          default: reg_flip<7, RG>(y, xo, rg, ml, co, ce); break;
+        }
+        ++t;
+        continue;
+      }
+      if (co == ce && t + 1 < t1) {
+        const uint32_t ml2 = term_low[t + 1];
+        const T c2 = term_odd[t + 1];
+        if ((ml2 & (uint32_t)(RG - 1)) != 0u && c2 == term_even[t + 1]) {
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, own, ml, co, own, ml2, c2);
+          t += 2;
+          continue;
+        }
+      }
+      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, ml, ml, co, ce, 0u);
+      ++t;
+    }
+    release();
+    // partner tiles; two single-term patterns are consumed together so their
+    // shared-memory loads overlap
+    for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;) {
+      const int pn = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
+      const int ta = pat_start[p];
+      if (pn < npat && pat_start[p + 1] - ta == 1 && pat_start[pn + 1] - pat_start[pn] == 1 &&
+          term_odd[ta] == term_even[ta] && term_odd[pat_start[pn]] == term_even[pat_start[pn]]) {
+        const unsigned char* sp2;
+        if (!acquire(sp, 0) || !acquire(sp2, 1)) {
+          aborted = true;
+          break;
+        }
+        const int tb = pat_start[pn];
+        apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, reinterpret_cast<const T*>(sp), term_low[ta],
+                                           term_odd[ta], reinterpret_cast<const T*>(sp2), term_low[tb],
+                                           term_odd[tb]);
+        release();
+        release();
+        p = tiled_next(pn + 1, npat, ut, pat_high, pat_flags);
+        continue;
+      }
       if (!acquire(sp, 0)) {
         aborted = true;
         break;
       }
-      const T* own = reinterpret_cast<const T*>(sp);
-      const T* dgt = reinterpret_cast<const T*>(sp + kTileBytes);
-      T xo[RPT][VW], y[RPT][VW];
-#pragma unroll
-      for (int m = 0; m < RPT; ++m) {
-        VecIO<T, VW>::ld_rw(xo[m], own + roff[m]);
-        const T dg = dgt[rg + RG * m];
-#pragma unroll
-        for (int v = 0; v < VW; ++v) y[m][v] = dg * xo[m][v];
-      }
-      const int t1 = pat_start[1];
-      for (int t = pat_start[0]; t < t1;) {
+      const T* P = reinterpret_cast<const T*>(sp);
+      const uint32_t hi_bits = pat_high[p] << kTileBits;
+      const int te = pat_start[p + 1];
+      for (int t = ta; t < te;) {
         const uint32_t ml = term_low[t];
         const T co = term_odd[t], ce = term_even[t];
-        if ((ml & (uint32_t)(RG - 1)) == 0u) {
-          switch (ml >> RGL) {
-            case 1: reg_flip<1, RG>(y, xo, rg, ml, co, ce); break;
-            case 2: reg_flip<2, RG>(y, xo, rg, ml, co, ce); break;
-            case 3: reg_flip<3, RG>(y, xo, rg, ml, co, ce); break;
-            case 4: reg_flip<4, RG>(y, xo, rg, ml, co, ce); break;
-            case 5: reg_flip<5, RG>(y, xo, rg, ml, co, ce); break;
-            case 6: reg_flip<6, RG>(y, xo, rg, ml, co, ce); break;
-            default: reg_flip<7, RG>(y, xo, rg, ml, co, ce); break;
-          }
-          ++t;
+        if (co == ce && t + 1 < te && term_odd[t + 1] == term_even[t + 1]) {
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, P, ml, co, P, term_low[t + 1], term_odd[t + 1]);
+          t += 2;
           continue;
         }
-        if (co == ce && t + 1 < t1) {
-          const uint32_t ml2 = term_low[t + 1];
-          const T c2 = term_odd[t + 1];
-          if ((ml2 & (uint32_t)(RG - 1)) != 0u && c2 == term_even[t + 1]) {
-            apply2_uniform<T, VW, RPT>(y, roff, own, (int)ml * BS, co, own, (int)ml2 * BS, c2);
-            t += 2;
-            continue;
-          }
-        }
-        apply_term<T, VW, RPT, RG>(y, roff, rg, own, ml, (int)ml * BS, ml, co, ce, 0u);
+        apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, P, ml, ml | hi_bits, co, ce, row0);
         ++t;
       }
       release();
-      // partner tiles; two single-term patterns are consumed together so their
-      // shared-memory loads overlap
-      for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;) {
-        const int pn = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
-        const int ta = pat_start[p];
-        if (pn < npat && pat_start[p + 1] - ta == 1 && pat_start[pn + 1] - pat_start[pn] == 1 &&
-            term_odd[ta] == term_even[ta] && term_odd[pat_start[pn]] == term_even[pat_start[pn]]) {
-          const unsigned char* sp2;
-          if (!acquire(sp, 0) || !acquire(sp2, 1)) {
-            aborted = true;
-            break;
-          }
-          const int tb = pat_start[pn];
-          apply2_uniform<T, VW, RPT>(y, roff, reinterpret_cast<const T*>(sp), (int)term_low[ta] * BS,
-                                     term_odd[ta], reinterpret_cast<const T*>(sp2),
-                                     (int)term_low[tb] * BS, term_odd[tb]);
-          release();
-          release();
-          p = tiled_next(pn + 1, npat, ut, pat_high, pat_flags);
-          continue;
-        }
-        if (!acquire(sp, 0)) {
-          aborted = true;
-          break;
-        }
-        const T* P = reinterpret_cast<const T*>(sp);
-        const uint32_t hi_bits = pat_high[p] << kTileBits;
-        const int te = pat_start[p + 1];
-        for (int t = ta; t < te;) {
-          const uint32_t ml = term_low[t];
-          const T co = term_odd[t], ce = term_even[t];
-          if (co == ce && t + 1 < te && term_odd[t + 1] == term_even[t + 1]) {
-            apply2_uniform<T, VW, RPT>(y, roff, P, (int)ml * BS, co, P, (int)term_low[t + 1] * BS,
-                                       term_odd[t + 1]);
-            t += 2;
-            continue;
-          }
-          apply_term<T, VW, RPT, RG>(y, roff, rg, P, ml | hi_bits, (int)ml * BS, ml, co, ce, row0);
-          ++t;
-        }
-        release();
-        p = pn;
+      p = pn;
+    }
+    if (aborted) continue;
+    // Z = (H W) M + W_prev Cp, row by row, with the W_j^T Z partial sums
+    const T* Pp = nullptr;
+    if (has_prev) {
+      if (!acquire(sp, 0)) {
+        aborted = true;
+        continue;
       }
-      if (aborted) break;
-      // Z = (H W) M + W_prev Cp, row by row, with the W_j^T Z partial sums
-      const T* Pp = nullptr;
-      if (has_prev) {
-        if (!acquire(sp, 0)) {
-          aborted = true;
-          break;
-        }
-        Pp = reinterpret_cast<const T*>(sp);
+      Pp = reinterpret_cast<const T*>(sp);
+    }
+    if constexpr (MODE == kModeApply) {  // Z = H W
+#pragma unroll
+      for (int m = 0; m < RPT; ++m)
+        VecIO<T, VW>::st_cs(Z + (size_t)(row0 + (uint32_t)(rg + RG * m)) * BS + lane * VW, y[m]);
+    } else {
+      // this lane's mixing coefficients, read per tile (broadcast shared-memory reads)
+      // so they hold no registers while the partner tiles are consumed
+      T mz[NV], cp[NV];
+#pragma unroll
+      for (int e = 0; e < NV; ++e) {
+        mz[e] = s_mz[lane * 16 + e];
+        cp[e] = s_cp[lane * 16 + e];
       }
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
@@ -857,7 +986,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           }
         if (has_prev) {
           T xp[VW];
-          VecIO<T, VW>::ld_rw(xp, Pp + roff[m]);
+          VecIO<T, VW>::ld_rw(xp, Pp + rgoff + m * kStep);
 #pragma unroll
           for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -880,37 +1009,6 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         }
       }
       if (has_prev) release();
-    }
-    // Per-slice flush of the W_j^T Z partial sums: fixed-order reduction over the
-    // 32 row groups (shuffles within a warp, then shared memory across warps).
-    const bool any_abort = consumers_sync_or(aborted);
-    if (any_abort) {
-      aborted = true;
-      break;
-    }
-    if (MODE == kModePass1) {
-      double v[NV];
-#pragma unroll
-      for (int e = 0; e < NV; ++e) {
-        double x = (double)acc[e];
-#pragma unroll
-        for (int off = LPR; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        v[e] = x;
-      }
-      if ((threadIdx.x & 31) < LPR) {
-#pragma unroll
-        for (int e = 0; e < NV; ++e) red[(warp * LPR + lane) * 16 + e] = v[e];
-      }
-      consumers_sync_or(false);
-      if (threadIdx.x < LPR) {
-        const int gs = BS / DS;
-        const size_t base = ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
-        for (int e = 0; e < NV; ++e) {
-          double sum = 0.0;
-          for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * LPR + threadIdx.x) * 16 + e];
-          a.partials[base + e] = sum;
-        }
-      }
     }
   }
   if (aborted && threadIdx.x == 0) atomicOr(a.err, 1u);
@@ -1472,14 +1570,16 @@ cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void* diag,
-                        cudaStream_t st) {
-  const int gx = (int)std::min<int64_t>((L.D + 255) / 256, 4096);
-  const size_t sm = (size_t)std::max(n_diag, 1) * 12 + 16;
+cudaError_t launch_tile_diag(const Layout& L, const TileDiag& dg, void* out, cudaStream_t st) {
+  const int64_t tiles = L.D >> kTileBits;
+  const int stride = tile_diag_stride(dg.n_entries, L.elem);
+  const int gx = (int)std::min<int64_t>(tiles, 4096);
+  const size_t sm = (size_t)(dg.n_groups + 1) * sizeof(double);
+  if (sm > 48 * 1024) return cudaErrorInvalidValue;
   if (L.precision == RDM_FP32)
-    k_diag<float><<<gx, 256, sm, st>>>(L.D, diags, n_diag, reinterpret_cast<float*>(diag));
+    k_tile_diag<float><<<gx, kThreads, sm, st>>>(tiles, dg, stride, reinterpret_cast<float*>(out));
   else
-    k_diag<double><<<gx, 256, sm, st>>>(L.D, diags, n_diag, reinterpret_cast<double*>(diag));
+    k_tile_diag<double><<<gx, kThreads, sm, st>>>(tiles, dg, stride, reinterpret_cast<double*>(out));
   return cudaGetLastError();
 }
 
@@ -1496,27 +1596,32 @@ static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a0, cudaStream_
   }
   // Deepest ring (up to 6 slots) that fits beside this Hamiltonian's term tables.
   SpmmArgs a = a0;
+  const TiledTerms& tt = a.tiled;
   a.stages = 6;  // a multiple of kProducerWarps
   while (a.stages > kProducerWarps &&
-         tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages) > (size_t)optin)
+         tiled_smem_bytes<T>(tt.n_pat, tt.n_terms, tt.dg.n_entries, a.stages) > (size_t)optin)
     a.stages -= kProducerWarps;
-  const size_t sm = tiled_smem_bytes<T>(a.tiled.n_pat, a.tiled.n_terms, a.stages);
+  const size_t sm = tiled_smem_bytes<T>(tt.n_pat, tt.n_terms, tt.dg.n_entries, a.stages);
+  if (sm > (size_t)optin) return cudaErrorInvalidValue;
   k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st) {
-  if (mode != kModeApply && layout_tiled(L) && a.tiled.n_pat > 0 && a.diag) {
-    cudaError_t e = cudaSuccess;
-    if (L.precision == RDM_FP32) {
-      if (L.DS == 1) e = mode == kModePass1 ? launch_tiled<float, 1, kModePass1>(L, a, st) : launch_tiled<float, 1, kModePass2>(L, a, st);
-      else if (L.DS == 2) e = mode == kModePass1 ? launch_tiled<float, 2, kModePass1>(L, a, st) : launch_tiled<float, 2, kModePass2>(L, a, st);
-      else e = mode == kModePass1 ? launch_tiled<float, 4, kModePass1>(L, a, st) : launch_tiled<float, 4, kModePass2>(L, a, st);
-    } else {
-      if (L.DS == 1) e = mode == kModePass1 ? launch_tiled<double, 1, kModePass1>(L, a, st) : launch_tiled<double, 1, kModePass2>(L, a, st);
-      else e = mode == kModePass1 ? launch_tiled<double, 2, kModePass1>(L, a, st) : launch_tiled<double, 2, kModePass2>(L, a, st);
+  if (layout_tiled(L) && a.tiled.n_pat > 0 && a.tile_k) {
+    const bool f32 = L.precision == RDM_FP32;
+    if (mode == kModeApply) {
+      if (L.DS != 1) return cudaErrorInvalidValue;
+      return f32 ? launch_tiled<float, 1, kModeApply>(L, a, st) : launch_tiled<double, 1, kModeApply>(L, a, st);
     }
-    return e;
+    const bool p1 = mode == kModePass1;
+    if (f32) {
+      if (L.DS == 1) return p1 ? launch_tiled<float, 1, kModePass1>(L, a, st) : launch_tiled<float, 1, kModePass2>(L, a, st);
+      if (L.DS == 2) return p1 ? launch_tiled<float, 2, kModePass1>(L, a, st) : launch_tiled<float, 2, kModePass2>(L, a, st);
+      return p1 ? launch_tiled<float, 4, kModePass1>(L, a, st) : launch_tiled<float, 4, kModePass2>(L, a, st);
+    }
+    if (L.DS == 1) return p1 ? launch_tiled<double, 1, kModePass1>(L, a, st) : launch_tiled<double, 1, kModePass2>(L, a, st);
+    return p1 ? launch_tiled<double, 2, kModePass1>(L, a, st) : launch_tiled<double, 2, kModePass2>(L, a, st);
   }
   RDM_DISPATCH(L, {
     const size_t sm = terms_smem<T>(a.n_flip, a.n_diag);

@@ -69,6 +69,7 @@ struct rdm_ham {
   rdm::FlipTerm* d_flips = nullptr;
   rdm::DiagTerm* d_diags = nullptr;
   rdm::TiledTerms tiled{};
+  void* d_apply_aux[2] = {};  // tiled apply: error word + K table (float64, float32)
 };
 
 namespace rdm {
@@ -87,8 +88,11 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
 struct TermImage {
   std::vector<unsigned char> bytes;
   size_t off_flips = 0, off_diags = 0, off_pat_high = 0, off_pat_start = 0, off_pat_flags = 0,
-         off_term_low = 0, off_term_odd = 0, off_term_even = 0;
-  int n_pat = 0, n_terms = 0;
+         off_term_low = 0, off_term_odd = 0, off_term_even = 0, off_dg_low = 0, off_dg_mlo = 0,
+         off_dg_hstart = 0, off_dg_thi = 0, off_dg_tc = 0, off_dg_slot = 0;
+  int n_pat = 0, n_terms = 0, n_dg_groups = 0, n_dg_terms = 0, dg_entries = 0;
+  uint32_t dg_dep = 0;
+  int dg_off[8] = {};
 };
 void make_term_image(const HostModel& h, TermImage* img);
 // Points ham's device term pointers into `dev`, a device copy of img.bytes.

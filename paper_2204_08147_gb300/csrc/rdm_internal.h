@@ -105,6 +105,45 @@ constexpr int kTiledLanesLog = 1;
 constexpr int kTiledLanes = 1 << kTiledLanesLog;
 constexpr int kTileBits = 11 - kTiledLanesLog;
 constexpr int kTileRows = 1 << kTileBits;
+// A consumer thread of the tiled SpMM owns the rows r0 + m * 2^kTileRegShift of a
+// tile (m = 0..7): the top three tile bits index its registers.
+constexpr int kTileRegShift = kTileBits - 3;
+
+// The diagonal of H inside the tiled SpMM, rebuilt per tile from a short table instead
+// of read per state. For state s = (tile << kTileBits) | r and a diagonal term
+// c (1 - 2 parity(s & m)) with m = (m_hi << kTileBits) | m_lo, the sign factorises as
+// sigma(tile & m_hi) * sigma(r & m_lo), sigma(x) = 1 - 2 parity(x). So
+//   diag(s) = low[r] + K_0(tile) + sum_g K_g(tile) sigma(r & mlo_g),
+// where low[] sums the terms with m_hi = 0 (the same for every tile), K_0 the terms
+// with m_lo = 0, and K_g the terms whose m_lo is the g-th distinct value mlo_g among
+// the terms with both parts nonzero. A consumer thread of the SpMM owns the rows
+// r = rg + 2^kTileRegShift m (m = 0..7), so with q_g = mlo_g >> kTileRegShift,
+//   diag = low[r] + sum_q A_q(tile, rg) (-1)^popc(q & m),
+//   A_q = [q = 0] K_0 + sum_{g: q_g = q} sigma(rg & mlo_g) K_g,
+// an 8-point Walsh-Hadamard transform per thread. The A table holds, per tile, A_q for
+// every rg (2^kTileRegShift entries at off[q]) when bit q of dep is set (some group of
+// character q has a mask bit below kTileRegShift), else one entry (then the same for
+// every rg). It is filled once per estimate (launch_tile_diag); groups are sorted by
+// q_g, with hstart[q]..hstart[q+1] the groups of character q.
+struct TileDiag {
+  int n_groups;          // G: distinct mixed m_lo values
+  int n_terms;           // terms with m_hi != 0
+  uint32_t dep;          // bit q: A_q depends on the row group
+  int off[8];            // element offset of A_q in a table row
+  int n_entries;         // table entries per tile (before padding)
+  const double* low;     // [kTileRows]
+  const uint32_t* mlo;   // [G]
+  const int* hstart;     // [9]
+  const uint32_t* thi;   // [n_terms] m_hi, sorted by slot (0 = K_0, 1 + g = K_g)
+  const double* tc;      // [n_terms] coefficients
+  const int* slot_start; // [G + 2]
+};
+// Elements per tile row of the A table (n_entries rounded up to 16 bytes).
+RDM_HD inline int tile_diag_stride(int n_entries, int elem) {
+  const int per16 = 16 / elem;
+  return (n_entries + per16 - 1) / per16 * per16;
+}
+
 struct TiledTerms {
   int n_pat;
   int n_terms;
@@ -114,6 +153,7 @@ struct TiledTerms {
   const uint32_t* term_low;   // [n_terms]
   const double* term_odd;     // [n_terms]
   const double* term_even;    // [n_terms]
+  TileDiag dg;
 };
 
 struct SpmmArgs {
@@ -133,7 +173,7 @@ struct SpmmArgs {
   int nb;
   int psi_first;       // 1: psi = w E (no read)
   TiledTerms tiled;    // n_pat = 0: not available
-  const void* diag;    // [D] diagonal of H in the block's precision (tiled SpMM)
+  const void* tile_k;  // [tiles][stride] A table of the tiled diagonal (launch_tile_diag)
   uint32_t* err;       // bit 0 set if a bulk-copy wait gave up
   int stages;          // tiled SpMM: copy-ring depth (set by the launcher)
 };
@@ -143,15 +183,16 @@ struct SpmmArgs {
 inline bool layout_tiled(const Layout& L) {
   return L.VW * L.elem == 16 && L.Bs == L.VW * kTiledLanes && L.n_bits >= kTileBits;
 }
-// Blocks per slice of the tiled SpMM (one persistent block per SM).
+// Blocks of the tiled SpMM (one persistent block per SM; the blocks walk the
+// (slice, tile) pairs of the whole block with one stride).
 inline int spmm_tiled_grid(const Layout& L) {
-  const int64_t tps = L.D >> kTileBits;
-  return (int)(tps < 152 ? tps : 152);
+  const int64_t tiles = (L.D >> kTileBits) * L.n_slices;
+  return (int)(tiles < 152 ? tiles : 152);
 }
 
-// diag[s] = sum_t c_t (1 - 2 parity(s & m_t)), summed in float64, stored as T.
-cudaError_t launch_diag(const Layout& L, const DiagTerm* diags, int n_diag, void* diag,
-                        cudaStream_t st);
+// A table of the tiled diagonal (TileDiag), out[tile][0 .. stride): summed in float64,
+// stored in the layout's precision, padding zero.
+cudaError_t launch_tile_diag(const Layout& L, const TileDiag& dg, void* out, cudaStream_t st);
 
 enum SpmmMode { kModeApply = 0, kModePass1 = 1, kModePass2 = 2 };
 cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream_t st);

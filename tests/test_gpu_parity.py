@@ -56,6 +56,27 @@ def test_apply_bit_exact_index_logic_fp64(ctx, lib, n, n_sys, seed, ncols):
     np.testing.assert_array_equal(yd.cpu().numpy(), h @ x)
 
 
+@pytest.mark.parametrize("n,n_sys,seed", [(10, 1, 20), (11, 1, 21), (12, 2, 22), (13, 0, 23), (15, 1, 24)])
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_apply_tiled_bit_exact(ctx, lib, n, n_sys, seed, dtype):
+    """A 32-byte row per state (8 float32 / 4 float64 columns, N >= 10) takes the
+    tiled SpMM: 1024-state tiles, partner tiles by bulk copies, the diagonal rebuilt
+    per tile from its low-bit table and row-group coefficients. Integer couplings and
+    inputs make every sum exact, so the result must equal H x bit for bit."""
+    torch = _torch()
+    spec = _integer_model(n, n_sys, seed, lam=2.0)
+    h = spin_ops.sparse_hamiltonian(spec)
+    ncols = 8 if dtype == "float32" else 4
+    x = np.random.default_rng(seed).integers(-3, 4, size=(1 << n, ncols)).astype(np.float64)
+    ham = lib.Hamiltonian(ctx, spec)
+    xd = torch.from_numpy(x).to(getattr(torch, dtype)).cuda()
+    yd = torch.empty_like(xd)
+    ham.apply(xd, yd)
+    ham.apply(xd, yd)  # second call reuses the Hamiltonian's tile table
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(yd.double().cpu().numpy(), h @ x)
+
+
 @pytest.mark.parametrize("n,n_sys,seed", [(6, 1, 11), (10, 2, 12), (12, 0, 13)])
 @pytest.mark.parametrize("ncols,dtype", [(4, "float32"), (32, "float32"), (2, "float64"), (16, "float64")])
 def test_apply_real_couplings(ctx, lib, n, n_sys, seed, ncols, dtype):
@@ -239,6 +260,19 @@ def test_post_processing_of_gpu_rho(ctx, lib):
 
 # ---------------------------------------------------------------- c2-shaped, FP32 vs FP64 oracle
 
+@pytest.mark.parametrize("n,n_sys,n_v", [(12, 1, 6), (13, 0, 3)])
+def test_tiled_fp64_estimate_vs_oracle(ctx, lib, n, n_sys, n_v):
+    """float64 with d_s <= 2 runs the tiled SpMM (32-byte slice rows); every term kind of
+    a random model against the oracle at the float64 tolerance."""
+    spec = W.random_model(n, n_sys, 70 + n)
+    betas = [0.2, 1.0, 3.0]
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate(betas, n_v, 30, 5, precision="fp64", dist="gauss")
+    ref = lanczos.Estimator(spec).run(betas, n_v, 30, 5, "gauss")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], atol=1e-9, rtol=0)
+
+
 def test_lr_tfim_small_fp32_vs_oracle(ctx, lib):
     spec = W.long_range_tfim(12, 2, 1.5, 1.1)
     ham = lib.Hamiltonian(ctx, spec)
@@ -341,8 +375,9 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_shards_combine_to_the_whole_run(ctx, lib, prec, tol):
     """Three shards of the bath vectors (first_vector offsets), run one after another
-    on this GPU and folded on the host, equal the single run (float32: the shards'
-    narrower blocks take the untiled SpMM, so rounding differs at ~1e-7)."""
+    on this GPU and folded on the host, equal the single run (float32: the SpMM's
+    per-block reductions group the states differently with the number of slices, so
+    rounding differs at ~1e-7)."""
     from paper_2204_08147_gb300.sharded import combine, local_part
     spec = W.long_range_tfim(12, 2, 1.5, 0.9)
     ham = lib.Hamiltonian(ctx, spec)
