@@ -717,7 +717,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     const uint64_t stream = policy_evict_first();
     const uint32_t hk_bytes = (uint32_t)hstride * (uint32_t)sizeof(T);
     const T* const hk_table = reinterpret_cast<const T*>(a.tile_k);
-    uint32_t seq = 0;
+    // stage counter kept as (slot, round) so no division by the runtime ring depth
+    uint32_t seq = 0, round = 0;
+    int slot = 0;
     bool stop = false;
     for (int64_t gt = blockIdx.x; gt < n_tiles && !stop; gt += gridDim.x) {
       const int slice = (int)(gt >> tile_log);
@@ -729,9 +731,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       int kind = -1;
       while (true) {
         if (seq % kProducerWarps == q) {
-          const int slot = (int)(seq % (uint32_t)kStages);
-          if (seq >= (uint32_t)kStages &&
-              !ring_wait(&empty[slot], ((seq / (uint32_t)kStages) - 1u) & 1u, abort_flag)) {
+          if (round > 0 && !ring_wait(&empty[slot], (round - 1u) & 1u, abort_flag)) {
             stop = true;
             break;
           }
@@ -751,6 +751,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           }
         }
         ++seq;
+        if (++slot == kStages) {
+          slot = 0;
+          ++round;
+        }
         // next stage of this tile
         if (kind == -2) break;
         const int p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
@@ -773,20 +777,29 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   constexpr int kStep = RG * BS;        // elements between a thread's rows
   const int rgoff = rg * BS + lane * VW;  // element offset of its first row in a tile
   const bool leader = (threadIdx.x & 31) == 0;
-  uint32_t seq = 0;
+  // next unreleased ring stage as (slot, phase parity): no division by the runtime depth
+  int rslot = 0;
+  uint32_t rphase = 0;
   bool aborted = false;
-  // Waits for the ring slot `ahead` stages past the next unreleased one.
-  auto acquire = [&](const unsigned char*& slot_ptr, uint32_t ahead) -> bool {
-    const uint32_t q = seq + ahead;
-    const int slot = (int)(q % (uint32_t)kStages);
-    if (!ring_wait(&full[slot], (q / (uint32_t)kStages) & 1u, abort_flag)) return false;
+  // Waits for the ring slot `ahead` (0 or 1) stages past the next unreleased one.
+  auto acquire = [&](const unsigned char*& slot_ptr, int ahead) -> bool {
+    int slot = rslot + ahead;
+    uint32_t ph = rphase;
+    if (slot >= kStages) {
+      slot -= kStages;
+      ph ^= 1u;
+    }
+    if (!ring_wait(&full[slot], ph, abort_flag)) return false;
     slot_ptr = ring + (size_t)slot * kSlotBytes;
     return true;
   };
   auto release = [&]() {
     __syncwarp();
-    if (leader) mbar_arrive(&empty[seq % kStages]);
-    ++seq;
+    if (leader) mbar_arrive(&empty[rslot]);
+    if (++rslot == kStages) {
+      rslot = 0;
+      rphase ^= 1u;
+    }
   };
   // Partials of W_j^T Z of this block for one slice (zero for a slice it has no tile
   // of); every (slice, block) entry is written once.
