@@ -198,6 +198,11 @@ void make_term_image(const HostModel& h, TermImage* img) {
   }
   img->dg_entries = tile_diag_layout(dg_mlo, &img->dg_dep, img->dg_off);
   const bool tiled = h.n >= kTileBits;
+  img->all_active = 1;
+  for (size_t q = 1; q < pat_flags.size(); ++q) {
+    const uint32_t f = pat_flags[q];
+    if ((f & 1u) && !((f & 2u) && (f & 4u))) img->all_active = 0;  // skipped by some tiles
+  }
   img->n_pat = tiled ? (int)pat_high.size() : 0;
   img->n_terms = tiled ? (int)term_low.size() : 0;
   auto& b = img->bytes;
@@ -231,6 +236,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   ham->d_diags = reinterpret_cast<DiagTerm*>(dev + img.off_diags);
   TiledTerms& t = ham->tiled;
   t.n_pat = img.n_pat;
+  t.all_active = img.all_active;
   t.n_terms = img.n_terms;
   t.pat_high = reinterpret_cast<const uint32_t*>(dev + img.off_pat_high);
   t.pat_start = reinterpret_cast<const int*>(dev + img.off_pat_start);

@@ -477,26 +477,44 @@ __host__ __device__ inline uint32_t tiled_slot_bytes(int n_entries, int elem) {
   return kTileBytes + ((uint32_t)(tile_diag_stride(n_entries, elem) * elem) + 127u) / 128u * 128u;
 }
 
+// Shared-memory records of the tiled SpMM's term tables. A pattern record carries its
+// first term inline; `single` marks a pattern of one term with c_odd = c_even (one
+// coefficient for the whole tile), the common case of a transverse field.
+template <typename T>
+struct alignas(16) PatS {
+  uint32_t high;   // m_high: the partner tile is tile ^ high
+  uint32_t flags;  // bit0 uniform activity, bit1/bit2 some c_odd/c_even nonzero
+  int start, end;  // its terms
+  uint32_t low0;   // m_low of its first term
+  uint32_t single;
+  T c0;            // c_odd of its first term
+};
+template <typename T>
+struct alignas(16) TermS {
+  T co, ce;        // c_odd, c_even
+  uint32_t low;    // m_low
+};
+
 template <typename T>
 __host__ __device__ inline size_t tiled_smem_bytes(int n_pat, int n_terms, int n_entries, int stages) {
   size_t off = (size_t)stages * tiled_slot_bytes(n_entries, (int)sizeof(T));
   off += 2 * kMaxStages * 8 + 64;                  // full/empty barriers, control
   off += 2 * 8 * 16 * sizeof(T);                   // mixing coefficients of the lanes
   off += (size_t)kConsumerWarps * kTiledLanes * 16 * 8;  // reduction scratch
-  off += (size_t)n_pat * 12 + 4;                   // pat_high, pat_flags, pat_start (+1)
   off = (off + 15) / 16 * 16;
+  off += (size_t)n_pat * sizeof(PatS<T>);          // pattern records
   off += (size_t)kTileRows * sizeof(T);            // low table of the diagonal
-  off += (size_t)n_terms * (4 + 2 * sizeof(T));
+  off += (size_t)n_terms * sizeof(TermS<T>);       // term records
   return off + 64;
 }
 
 // First pattern >= p that tile tix needs (uniform patterns may be inactive).
-__device__ __forceinline__ int tiled_next(int p, int npat, uint32_t tix, const uint32_t* pat_high,
-                                          const uint32_t* pat_flags) {
+template <typename T>
+__device__ __forceinline__ int tiled_next(int p, int npat, uint32_t tix, const PatS<T>* pat) {
   for (; p < npat; ++p) {
-    const uint32_t f = pat_flags[p];
+    const uint32_t f = pat[p].flags;
     if (!(f & 1u)) return p;
-    const bool odd = (__popc(tix & pat_high[p]) & 1) != 0;
+    const bool odd = (__popc(tix & pat[p].high) & 1) != 0;
     if (odd ? (f & 2u) : (f & 4u)) return p;
   }
   return p;
@@ -667,25 +685,30 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   T* const s_mz = reinterpret_cast<T*>(smem + (size_t)kStages * kSlotBytes + 2 * kMaxStages * 8 + 64);
   T* const s_cp = s_mz + 8 * 16;
   double* const red = reinterpret_cast<double*>(s_cp + 8 * 16);
-  uint32_t* const pat_high = reinterpret_cast<uint32_t*>(red + kConsumerWarps * kTiledLanes * 16);
-  uint32_t* const pat_flags = pat_high + npat;
-  int* const pat_start = reinterpret_cast<int*>(pat_flags + npat);
-  size_t off = (size_t)(reinterpret_cast<unsigned char*>(pat_start + npat + 1) - smem);
+  size_t off = (size_t)(reinterpret_cast<unsigned char*>(red + kConsumerWarps * kTiledLanes * 16) - smem);
   off = (off + 15) / 16 * 16;
-  T* const s_low = reinterpret_cast<T*>(smem + off);
-  T* const term_odd = s_low + kTileRows;
-  T* const term_even = term_odd + nterm;
-  uint32_t* const term_low = reinterpret_cast<uint32_t*>(term_even + nterm);
+  PatS<T>* const pat = reinterpret_cast<PatS<T>*>(smem + off);
+  T* const s_low = reinterpret_cast<T*>(pat + npat);
+  TermS<T>* const term = reinterpret_cast<TermS<T>*>(s_low + kTileRows);
 
   for (int i = threadIdx.x; i < npat; i += blockDim.x) {
-    pat_high[i] = tt.pat_high[i];
-    pat_flags[i] = tt.pat_flags[i];
+    PatS<T> r;
+    r.high = tt.pat_high[i];
+    r.flags = tt.pat_flags[i];
+    r.start = tt.pat_start[i];
+    r.end = tt.pat_start[i + 1];
+    const bool any = r.start < r.end;
+    r.low0 = any ? tt.term_low[r.start] : 0u;
+    r.c0 = any ? (T)tt.term_odd[r.start] : (T)0;
+    r.single = (r.end - r.start == 1 && tt.term_odd[r.start] == tt.term_even[r.start]) ? 1u : 0u;
+    pat[i] = r;
   }
-  for (int i = threadIdx.x; i <= npat; i += blockDim.x) pat_start[i] = tt.pat_start[i];
   for (int i = threadIdx.x; i < nterm; i += blockDim.x) {
-    term_low[i] = tt.term_low[i];
-    term_odd[i] = (T)tt.term_odd[i];
-    term_even[i] = (T)tt.term_even[i];
+    TermS<T> r;
+    r.co = (T)tt.term_odd[i];
+    r.ce = (T)tt.term_even[i];
+    r.low = tt.term_low[i];
+    term[i] = r;
   }
   for (int i = threadIdx.x; i < kTileRows; i += blockDim.x) s_low[i] = (T)tt.dg.low[i];
   if (threadIdx.x == 0) {
@@ -703,6 +726,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   const int64_t n_tiles = (int64_t)L.n_slices << tile_log;
   const uint32_t tile_mask = (uint32_t)(((int64_t)1 << tile_log) - 1);
   const bool has_prev = a.w_prev != nullptr;
+  // every partner pattern is needed by every tile: the stage sequence is fixed
+  const bool all_active = tt.all_active != 0;
 
   if (warp >= kConsumerWarps) {
     // ------------------------------------------------ producers (lane 0 of each)
@@ -746,7 +771,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             bulk_load_hint(dst, Wp + ((size_t)ut << kTileBits) * BS, kTileBytes, &full[slot], stream);
           } else {
             mbar_expect_tx(&full[slot], kTileBytes);
-            bulk_load_hint(dst, W + ((size_t)(ut ^ pat_high[kind]) << kTileBits) * BS, kTileBytes,
+            bulk_load_hint(dst, W + ((size_t)(ut ^ pat[kind].high) << kTileBits) * BS, kTileBytes,
                            &full[slot], keep);
           }
         }
@@ -757,7 +782,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         }
         // next stage of this tile
         if (kind == -2) break;
-        const int p = tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat_high, pat_flags);
+        const int p = all_active ? (kind == -1 ? 1 : kind + 1) : tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat);
         if (p < npat) {
           kind = p;
         } else if (has_prev) {
@@ -889,73 +914,73 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         for (int v = 0; v < VW; ++v) y[m][v] = dg[m] * xo[m][v];
       }
     }
-    const int t1 = pat_start[1];
-    for (int t = pat_start[0]; t < t1;) {
-      const uint32_t ml = term_low[t];
-      const T co = term_odd[t], ce = term_even[t];
+    const int t1 = pat[0].end;
+    for (int t = pat[0].start; t < t1;) {
+      const TermS<T> d = term[t];
+      const uint32_t ml = d.low;
       if ((ml & (uint32_t)(RG - 1)) == 0u) {
         switch (ml >> RGL) {
-          case 1: reg_flip<1, RG>(y, xo, rg, ml, co, ce); break;
-          case 2: reg_flip<2, RG>(y, xo, rg, ml, co, ce); break;
-          case 3: reg_flip<3, RG>(y, xo, rg, ml, co, ce); break;
-          case 4: reg_flip<4, RG>(y, xo, rg, ml, co, ce); break;
-          case 5: reg_flip<5, RG>(y, xo, rg, ml, co, ce); break;
-          case 6: reg_flip<6, RG>(y, xo, rg, ml, co, ce); break;
-          default: reg_flip<7, RG>(y, xo, rg, ml, co, ce); break;
+          case 1: reg_flip<1, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          case 2: reg_flip<2, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          case 3: reg_flip<3, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          case 4: reg_flip<4, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          case 5: reg_flip<5, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          case 6: reg_flip<6, RG>(y, xo, rg, ml, d.co, d.ce); break;
+          default: reg_flip<7, RG>(y, xo, rg, ml, d.co, d.ce); break;
         }
         ++t;
         continue;
       }
-      if (co == ce && t + 1 < t1) {
-        const uint32_t ml2 = term_low[t + 1];
-        const T c2 = term_odd[t + 1];
-        if ((ml2 & (uint32_t)(RG - 1)) != 0u && c2 == term_even[t + 1]) {
-          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, own, ml, co, own, ml2, c2);
+      if (d.co == d.ce && t + 1 < t1) {
+        const TermS<T> d2 = term[t + 1];
+        if ((d2.low & (uint32_t)(RG - 1)) != 0u && d2.co == d2.ce) {
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, own, ml, d.co, own, d2.low, d2.co);
           t += 2;
           continue;
         }
       }
-      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, ml, ml, co, ce, 0u);
+      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, ml, ml, d.co, d.ce, 0u);
       ++t;
     }
     release();
     // partner tiles; two single-term patterns are consumed together so their
     // shared-memory loads overlap
-    for (int p = tiled_next(1, npat, ut, pat_high, pat_flags); p < npat;) {
-      const int pn = tiled_next(p + 1, npat, ut, pat_high, pat_flags);
-      const int ta = pat_start[p];
-      if (pn < npat && pat_start[p + 1] - ta == 1 && pat_start[pn + 1] - pat_start[pn] == 1 &&
-          term_odd[ta] == term_even[ta] && term_odd[pat_start[pn]] == term_even[pat_start[pn]]) {
-        const unsigned char* sp2;
-        if (!acquire(sp, 0) || !acquire(sp2, 1)) {
-          aborted = true;
-          break;
+    for (int p = all_active ? 1 : tiled_next(1, npat, ut, pat); p < npat;) {
+      const int pn = all_active ? p + 1 : tiled_next(p + 1, npat, ut, pat);
+      const PatS<T> A = pat[p];
+      if (pn < npat && A.single) {
+        const PatS<T> Bq = pat[pn];
+        if (Bq.single) {
+          const unsigned char* sp2;
+          if (!acquire(sp, 0) || !acquire(sp2, 1)) {
+            aborted = true;
+            break;
+          }
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, reinterpret_cast<const T*>(sp), A.low0, A.c0,
+                                             reinterpret_cast<const T*>(sp2), Bq.low0, Bq.c0);
+          release();
+          release();
+          p = all_active ? pn + 1 : tiled_next(pn + 1, npat, ut, pat);
+          continue;
         }
-        const int tb = pat_start[pn];
-        apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, reinterpret_cast<const T*>(sp), term_low[ta],
-                                           term_odd[ta], reinterpret_cast<const T*>(sp2), term_low[tb],
-                                           term_odd[tb]);
-        release();
-        release();
-        p = tiled_next(pn + 1, npat, ut, pat_high, pat_flags);
-        continue;
       }
       if (!acquire(sp, 0)) {
         aborted = true;
         break;
       }
       const T* P = reinterpret_cast<const T*>(sp);
-      const uint32_t hi_bits = pat_high[p] << kTileBits;
-      const int te = pat_start[p + 1];
-      for (int t = ta; t < te;) {
-        const uint32_t ml = term_low[t];
-        const T co = term_odd[t], ce = term_even[t];
-        if (co == ce && t + 1 < te && term_odd[t + 1] == term_even[t + 1]) {
-          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, P, ml, co, P, term_low[t + 1], term_odd[t + 1]);
-          t += 2;
-          continue;
+      const uint32_t hi_bits = A.high << kTileBits;
+      for (int t = A.start; t < A.end;) {
+        const TermS<T> d = term[t];
+        if (d.co == d.ce && t + 1 < A.end) {
+          const TermS<T> d2 = term[t + 1];
+          if (d2.co == d2.ce) {
+            apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, P, d.low, d.co, P, d2.low, d2.co);
+            t += 2;
+            continue;
+          }
         }
-        apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, P, ml, ml | hi_bits, co, ce, row0);
+        apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, P, d.low, d.low | hi_bits, d.co, d.ce, row0);
         ++t;
       }
       release();

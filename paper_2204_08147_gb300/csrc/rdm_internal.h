@@ -147,6 +147,7 @@ RDM_HD inline int tile_diag_stride(int n_entries, int elem) {
 struct TiledTerms {
   int n_pat;
   int n_terms;
+  int all_active;             // 1: every tile needs every partner pattern
   const uint32_t* pat_high;   // [n_pat]
   const int* pat_start;       // [n_pat + 1]
   const uint32_t* pat_flags;  // [n_pat]
