@@ -121,7 +121,7 @@ static int tile_diag_layout(const std::vector<uint32_t>& mlo, uint32_t* dep, int
   int n = 0;
   for (int q = 0; q < 8; ++q) {
     off[q] = n;
-    n += ((*dep >> q) & 1u) ? (int)kRG : 1;
+    if (q < (1 << kTileRegBits)) n += ((*dep >> q) & 1u) ? (int)kRG : 1;
   }
   return n;
 }

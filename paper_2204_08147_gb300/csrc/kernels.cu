@@ -467,7 +467,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // table of the diagonal. Per tile the stage sequence is: own tile, each needed partner
 // tile, then the W_{j-1} tile (if any). Full barriers (count 1, transaction bytes)
 // and empty barriers (one arrival per consumer warp) order the ring.
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = (kTileRows >> kTileRegBits) * kTiledLanes / 32;
 constexpr int kProducerWarps = 2;  // each issues the copies of every other ring slot
 constexpr int kTiledThreads = (kConsumerWarps + kProducerWarps) * 32;
 constexpr uint32_t kTileBytes = (uint32_t)kTileRows * kTiledLanes * 16;  // 32 KB
@@ -549,12 +549,13 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volati
 template <int K, int RG, typename T, int VW, int RPT>
 __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW], int rg, uint32_t ml,
                                          T co, T ce) {
+  if constexpr (K >= RPT) return;
 #pragma unroll
   for (int m = 0; m < RPT; ++m) {
     const uint32_t r = (uint32_t)(rg + RG * m);
     const T c = (co == ce) ? co : ((__popc(r & ml) & 1) ? co : ce);
 #pragma unroll
-    for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xo[m ^ K][v], y[m][v]);
+    for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xo[(m ^ K) & (RPT - 1)][v], y[m][v]);
   }
 }
 
@@ -636,20 +637,20 @@ __device__ __forceinline__ void apply2_uniform(T (&y)[RPT][VW], int rgoff, const
   }
 }
 
-// Diagonal of H on this thread's eight rows rg + RG m of a tile, from the tile's A-table
-// row hk (TileDiag): low[r] + sum_q A_q (-1)^popc(q & m), one 8-point Walsh-Hadamard
-// transform of the eight A_q.
+// Diagonal of H on this thread's RPT rows rg + RG m of a tile, from the tile's A-table
+// row hk (TileDiag): low[r] + sum_q A_q (-1)^popc(q & m), one RPT-point Walsh-Hadamard
+// transform of the A_q.
 template <typename T, int RPT, int RG>
 __device__ __forceinline__ void tile_diagonal(T (&dg)[RPT], const T* low, const T* hk, int rg,
                                               const TileDiag& td) {
-  static_assert(RPT == 8 && RG == (1 << kTileRegShift), "eight register rows per thread");
-  T A[8];
+  static_assert(RPT == (1 << kTileRegBits) && RG == (1 << kTileRegShift), "register rows per thread");
+  T A[RPT];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) A[q] = hk[td.off[q] + (((td.dep >> q) & 1u) ? rg : 0)];
+  for (int q = 0; q < RPT; ++q) A[q] = hk[td.off[q] + (((td.dep >> q) & 1u) ? rg : 0)];
 #pragma unroll
-  for (int len = 1; len < 8; len <<= 1)
+  for (int len = 1; len < RPT; len <<= 1)
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < RPT; ++i)
       if (!(i & len)) {
         const T u = A[i], w = A[i | len];
         A[i] = u + w;
@@ -669,9 +670,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   constexpr int NV = NG * NVG;
   constexpr int RG = kConsumerWarps * 32 / LPR;  // row groups
   constexpr int RGL = (RG >= 256) ? 8 : (RG >= 128) ? 7 : (RG >= 64) ? 6 : 5;  // log2(RG)
-  constexpr int RPT = kTileRows / RG;            // rows per consumer thread (8)
+  constexpr int RPT = kTileRows / RG;            // rows per consumer thread
   const int kStages = a.stages;
-  static_assert(RPT == 8, "eight rows per consumer thread");
+  static_assert(RPT == (1 << kTileRegBits), "rows per consumer thread");
   static_assert((1 << RGL) == RG && RGL == kTileRegShift, "row groups are the low tile bits");
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;

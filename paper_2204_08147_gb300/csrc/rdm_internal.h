@@ -106,8 +106,10 @@ constexpr int kTiledLanes = 1 << kTiledLanesLog;
 constexpr int kTileBits = 11 - kTiledLanesLog;
 constexpr int kTileRows = 1 << kTileBits;
 // A consumer thread of the tiled SpMM owns the rows r0 + m * 2^kTileRegShift of a
-// tile (m = 0..7): the top three tile bits index its registers.
-constexpr int kTileRegShift = kTileBits - 3;
+// tile (m = 0 .. 2^kTileRegBits - 1): the top kTileRegBits tile bits index its
+// registers.
+constexpr int kTileRegBits = 3;
+constexpr int kTileRegShift = kTileBits - kTileRegBits;
 
 // The diagonal of H inside the tiled SpMM, rebuilt per tile from a short table instead
 // of read per state. For state s = (tile << kTileBits) | r and a diagonal term
@@ -117,10 +119,10 @@ constexpr int kTileRegShift = kTileBits - 3;
 // where low[] sums the terms with m_hi = 0 (the same for every tile), K_0 the terms
 // with m_lo = 0, and K_g the terms whose m_lo is the g-th distinct value mlo_g among
 // the terms with both parts nonzero. A consumer thread of the SpMM owns the rows
-// r = rg + 2^kTileRegShift m (m = 0..7), so with q_g = mlo_g >> kTileRegShift,
+// r = rg + 2^kTileRegShift m (m < 2^kTileRegBits), so with q_g = mlo_g >> kTileRegShift,
 //   diag = low[r] + sum_q A_q(tile, rg) (-1)^popc(q & m),
 //   A_q = [q = 0] K_0 + sum_{g: q_g = q} sigma(rg & mlo_g) K_g,
-// an 8-point Walsh-Hadamard transform per thread. The A table holds, per tile, A_q for
+// a 2^kTileRegBits-point Walsh-Hadamard transform per thread. The A table holds, per tile, A_q for
 // every rg (2^kTileRegShift entries at off[q]) when bit q of dep is set (some group of
 // character q has a mask bit below kTileRegShift), else one entry (then the same for
 // every rg). It is filled once per estimate (launch_tile_diag); groups are sorted by
@@ -129,7 +131,7 @@ struct TileDiag {
   int n_groups;          // G: distinct mixed m_lo values
   int n_terms;           // terms with m_hi != 0
   uint32_t dep;          // bit q: A_q depends on the row group
-  int off[8];            // element offset of A_q in a table row
+  int off[8];            // element offset of A_q in a table row (q < 2^kTileRegBits)
   int n_entries;         // table entries per tile (before padding)
   const double* low;     // [kTileRows]
   const uint32_t* mlo;   // [G]
