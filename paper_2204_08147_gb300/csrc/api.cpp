@@ -203,6 +203,14 @@ void make_term_image(const HostModel& h, TermImage* img) {
     const uint32_t f = pat_flags[q];
     if ((f & 1u) && !((f & 2u) && (f & 4u))) img->all_active = 0;  // skipped by some tiles
   }
+  // Every partner pattern one term with m_low = 0 and c_odd = c_even != 0 (a
+  // transverse field): the partner row of a row is the same row of the partner tile.
+  img->partners_flat = img->all_active;
+  for (size_t q = 1; q < pat_high.size(); ++q) {
+    const int t = pat_start[q];
+    if (pat_start[q + 1] - t != 1 || term_low[t] != 0u || term_odd[t] != term_even[t] || term_odd[t] == 0.0)
+      img->partners_flat = 0;
+  }
   img->n_pat = tiled ? (int)pat_high.size() : 0;
   img->n_terms = tiled ? (int)term_low.size() : 0;
   auto& b = img->bytes;
@@ -237,6 +245,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   TiledTerms& t = ham->tiled;
   t.n_pat = img.n_pat;
   t.all_active = img.all_active;
+  t.partners_flat = img.partners_flat;
   t.n_terms = img.n_terms;
   t.pat_high = reinterpret_cast<const uint32_t*>(dev + img.off_pat_high);
   t.pat_start = reinterpret_cast<const int*>(dev + img.off_pat_start);

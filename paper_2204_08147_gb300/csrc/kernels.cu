@@ -729,6 +729,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   const bool has_prev = a.w_prev != nullptr;
   // every partner pattern is needed by every tile: the stage sequence is fixed
   const bool all_active = tt.all_active != 0;
+  const bool partners_flat = tt.partners_flat != 0;
 
   if (warp >= kConsumerWarps) {
     // ------------------------------------------------ producers (lane 0 of each)
@@ -823,6 +824,20 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     __syncwarp();
     if (leader) mbar_arrive(&empty[rslot]);
     if (++rslot == kStages) {
+      rslot = 0;
+      rphase ^= 1u;
+    }
+  };
+  auto release2 = [&]() {  // the next two stages
+    __syncwarp();
+    const int s2 = rslot + 1 == kStages ? 0 : rslot + 1;
+    if (leader) {
+      mbar_arrive(&empty[rslot]);
+      mbar_arrive(&empty[s2]);
+    }
+    if (s2 < rslot) rphase ^= 1u;
+    rslot = s2 + 1;
+    if (rslot == kStages) {
       rslot = 0;
       rphase ^= 1u;
     }
@@ -946,6 +961,45 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     release();
     // partner tiles; two single-term patterns are consumed together so their
     // shared-memory loads overlap
+    if (partners_flat) {
+      // one uniform term per partner tile, partner row = same row: no term records
+      int p = 1;
+      for (; p + 1 < npat; p += 2) {
+        const T cA = pat[p].c0, cB = pat[p + 1].c0;
+        const unsigned char* sb;
+        if (!acquire(sp, 0) || !acquire(sb, 1)) {
+          aborted = true;
+          break;
+        }
+        const T* PA = reinterpret_cast<const T*>(sp) + rgoff;
+        const T* PB = reinterpret_cast<const T*>(sb) + rgoff;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          T u[VW], w[VW];
+          VecIO<T, VW>::ld_rw(u, PA + m * kStep);
+          VecIO<T, VW>::ld_rw(w, PB + m * kStep);
+#pragma unroll
+          for (int v = 0; v < VW; ++v) y[m][v] = fma(cB, w[v], fma(cA, u[v], y[m][v]));
+        }
+        release2();
+      }
+      if (!aborted && p < npat) {
+        const T cA = pat[p].c0;
+        if (!acquire(sp, 0)) {
+          aborted = true;
+        } else {
+          const T* PA = reinterpret_cast<const T*>(sp) + rgoff;
+#pragma unroll
+          for (int m = 0; m < RPT; ++m) {
+            T u[VW];
+            VecIO<T, VW>::ld_rw(u, PA + m * kStep);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) y[m][v] = fma(cA, u[v], y[m][v]);
+          }
+          release();
+        }
+      }
+    } else
     for (int p = all_active ? 1 : tiled_next(1, npat, ut, pat); p < npat;) {
       const int pn = all_active ? p + 1 : tiled_next(p + 1, npat, ut, pat);
       const PatS<T> A = pat[p];

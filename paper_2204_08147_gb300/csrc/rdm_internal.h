@@ -150,6 +150,7 @@ struct TiledTerms {
   int n_pat;
   int n_terms;
   int all_active;             // 1: every tile needs every partner pattern
+  int partners_flat;          // 1: and each is one uniform term with m_low = 0
   const uint32_t* pat_high;   // [n_pat]
   const int* pat_start;       // [n_pat + 1]
   const uint32_t* pat_flags;  // [n_pat]
