@@ -131,6 +131,15 @@ void make_term_image(const HostModel& h, TermImage* img) {
   std::map<uint32_t, std::vector<const FlipTerm*>> groups;
   groups[0];  // pattern 0 always exists
   for (const FlipTerm& f : h.flips) groups[f.mask >> kTileBits].push_back(&f);
+  // In-tile terms whose mask only touches a consumer thread's register rows (no bit
+  // below kTileRegShift) first: the SpMM applies them from registers.
+  auto& g0 = groups[0];
+  std::stable_partition(g0.begin(), g0.end(), [](const FlipTerm* f) {
+    return (f->mask & ((1u << kTileRegShift) - 1u)) == 0u;
+  });
+  img->n_reg0 = 0;
+  for (const FlipTerm* f : g0)
+    if ((f->mask & ((1u << kTileRegShift) - 1u)) == 0u) ++img->n_reg0;
   std::vector<uint32_t> pat_high, pat_flags, term_low;
   std::vector<int> pat_start;
   std::vector<double> term_odd, term_even;
@@ -246,6 +255,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   t.n_pat = img.n_pat;
   t.all_active = img.all_active;
   t.partners_flat = img.partners_flat;
+  t.n_reg0 = img.n_reg0;
   t.n_terms = img.n_terms;
   t.pat_high = reinterpret_cast<const uint32_t*>(dev + img.off_pat_high);
   t.pat_start = reinterpret_cast<const int*>(dev + img.off_pat_start);

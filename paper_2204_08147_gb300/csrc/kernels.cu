@@ -550,10 +550,17 @@ template <int K, int RG, typename T, int VW, int RPT>
 __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW], int rg, uint32_t ml,
                                          T co, T ce) {
   if constexpr (K >= RPT) return;
+  if (co == ce) {
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xo[(m ^ K) & (RPT - 1)][v], y[m][v]);
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < RPT; ++m) {
     const uint32_t r = (uint32_t)(rg + RG * m);
-    const T c = (co == ce) ? co : ((__popc(r & ml) & 1) ? co : ce);
+    const T c = (__popc(r & ml) & 1) ? co : ce;
 #pragma unroll
     for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xo[(m ^ K) & (RPT - 1)][v], y[m][v]);
   }
@@ -730,6 +737,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   // every partner pattern is needed by every tile: the stage sequence is fixed
   const bool all_active = tt.all_active != 0;
   const bool partners_flat = tt.partners_flat != 0;
+  const int n_reg0 = tt.n_reg0;
 
   if (warp >= kConsumerWarps) {
     // ------------------------------------------------ producers (lane 0 of each)
@@ -930,32 +938,30 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         for (int v = 0; v < VW; ++v) y[m][v] = dg[m] * xo[m][v];
       }
     }
-    const int t1 = pat[0].end;
-    for (int t = pat[0].start; t < t1;) {
+    const int t1 = pat[0].end, tr = pat[0].start + n_reg0;
+    for (int t = pat[0].start; t < tr; ++t) {  // masks on the register rows only
       const TermS<T> d = term[t];
-      const uint32_t ml = d.low;
-      if ((ml & (uint32_t)(RG - 1)) == 0u) {
-        switch (ml >> RGL) {
-          case 1: reg_flip<1, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          case 2: reg_flip<2, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          case 3: reg_flip<3, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          case 4: reg_flip<4, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          case 5: reg_flip<5, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          case 6: reg_flip<6, RG>(y, xo, rg, ml, d.co, d.ce); break;
-          default: reg_flip<7, RG>(y, xo, rg, ml, d.co, d.ce); break;
-        }
-        ++t;
-        continue;
+      switch (d.low >> RGL) {
+        case 1: reg_flip<1, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 2: reg_flip<2, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 3: reg_flip<3, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 4: reg_flip<4, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 5: reg_flip<5, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 6: reg_flip<6, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        default: reg_flip<7, RG>(y, xo, rg, d.low, d.co, d.ce); break;
       }
+    }
+    for (int t = tr; t < t1;) {
+      const TermS<T> d = term[t];
       if (d.co == d.ce && t + 1 < t1) {
         const TermS<T> d2 = term[t + 1];
-        if ((d2.low & (uint32_t)(RG - 1)) != 0u && d2.co == d2.ce) {
-          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, own, ml, d.co, own, d2.low, d2.co);
+        if (d2.co == d2.ce) {
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, own, d.low, d.co, own, d2.low, d2.co);
           t += 2;
           continue;
         }
       }
-      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, ml, ml, d.co, d.ce, 0u);
+      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, d.low, d.low, d.co, d.ce, 0u);
       ++t;
     }
     release();
@@ -1051,10 +1057,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       }
       Pp = reinterpret_cast<const T*>(sp);
     }
+    T* const zrow = Z + (size_t)row0 * BS + rgoff;  // this thread's first row of the tile
     if constexpr (MODE == kModeApply) {  // Z = H W
 #pragma unroll
-      for (int m = 0; m < RPT; ++m)
-        VecIO<T, VW>::st_cs(Z + (size_t)(row0 + (uint32_t)(rg + RG * m)) * BS + lane * VW, y[m]);
+      for (int m = 0; m < RPT; ++m) VecIO<T, VW>::st_cs(zrow + m * kStep, y[m]);
     } else {
       // this lane's mixing coefficients, read per tile (broadcast shared-memory reads)
       // so they hold no registers while the partner tiles are consumed
@@ -1066,7 +1072,6 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       }
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
-        const int r = rg + RG * m;
         T z[VW];
 #pragma unroll
         for (int g = 0; g < NG; ++g)
@@ -1090,7 +1095,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
               z[g * DS + j] = t;
             }
         }
-        VecIO<T, VW>::st_cs(Z + (size_t)(row0 + (uint32_t)r) * BS + lane * VW, z);
+        VecIO<T, VW>::st_cs(zrow + m * kStep, z);
         if (MODE == kModePass1) {
 #pragma unroll
           for (int g = 0; g < NG; ++g)
