@@ -314,6 +314,7 @@ def run_ours(a):
         return 0
 
     peak, peak_kind = _peaks()
+    host_dense = stats.pop("host_small_dense", None)  # host wall time, not a kernel
     sp = [stats["spmm_pass1"], stats["spmm_pass2"]]
     sp_ms = sum(s["ms"] for s in sp)
     sp_launch = sum(s["launches"] for s in sp)
@@ -345,6 +346,8 @@ def run_ours(a):
                 "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["launches"]},
+        "host_small_dense_ms_per_solve": (host_dense["ms"] / host_dense["launches"])
+        if host_dense and host_dense["launches"] else None,
         "roofline": roof,
         "plain_fp64": plain,
         "precision_fp32_vs_fp64": precision,

@@ -167,7 +167,10 @@ typedef struct {
 
 /* enable != 0 starts recording (and clears earlier statistics); 0 stops. */
 rdm_status rdm_profile(rdm_ctx* ctx, int enable);
-/* Copies up to `max` entries into out; *n = number of kernel kinds recorded. */
+/* Copies up to `max` entries into out; *n = number of kinds recorded. The entry
+ * "host_small_dense" is not a kernel: its ms is the host wall time of the small dense
+ * step of rdm_estimate (eigen-solves of T_l and the Gram coefficients), launches the
+ * number of estimates. */
 rdm_status rdm_profile_stats(rdm_ctx* ctx, rdm_kernel_stat* out, int max, int* n);
 
 /* ---------------------------------------------------------------- model */

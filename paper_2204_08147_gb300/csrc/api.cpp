@@ -2,6 +2,7 @@
 // the orchestration of the estimator (Algorithm 1 twice, the small dense step in
 // between, the Gram at the end).
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -877,6 +878,12 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   std::vector<double> cstore((size_t)n_v * n_beta * n * ds);
   std::vector<double> tmin(n_v, 0.0);
   std::vector<char> okv(n_v, 1);
+  const auto host_t0 = std::chrono::steady_clock::now();
+  double host_ms = 0.0;
+  auto host_lap = [&]() {
+    const auto t1 = std::chrono::steady_clock::now();
+    return std::chrono::duration<double, std::milli>(t1 - host_t0).count();
+  };
   parallel_for(n_v, [&](int l) {
     std::vector<double> t;
     build_t(ds, k, ng, l, ta, tb, t);
@@ -890,6 +897,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     }
     e0 = std::min(e0, tmin[l]);
   }
+  host_ms += host_lap();
   // c[beta][l] = exp(-beta (t_min(l) - E0)/2) * (the t_min(l)-shifted c)
   auto coef_c = [&](int l, int bi, std::vector<double>& c) {
     const double* src = &cstore[((size_t)l * n_beta + bi) * n * ds];
@@ -904,6 +912,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   for (int b0 = 0; b0 < n_beta; b0 += p.nbc) {
     const int nb = std::min(p.nbc, n_beta - b0);
     std::fill(hE.begin(), hE.end(), 0.0);
+    const auto coef_t0 = std::chrono::steady_clock::now();
     parallel_for(n_v, [&](int l) {
       std::vector<double> c;
       for (int bi = 0; bi < nb; ++bi) {
@@ -928,6 +937,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
         }
       }
     });
+    host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - coef_t0).count();
     if (!want_gram) continue;
     CK(cudaMemcpyAsync(d_e, hE.data(), hE.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     h2d += hE.size() * sizeof(double);
@@ -985,7 +995,13 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   CK(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   d2h += sizeof flags;
-  if (prof) prof->collect();
+  if (prof) {
+    prof->collect();
+    if (prof->on) {
+      prof->launches[kKHostDense]++;
+      prof->ms[kKHostDense] += host_ms;
+    }
+  }
 
   // ---- normalisation (eq. rho_est) and ln Z_t.
   auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {

@@ -146,22 +146,99 @@ bool sym_eig(int n, const double* a_in, double* w, double* vt) {
 }
 
 
+// sqrt(x^2 + z^2): the plain formula where the squares can neither overflow nor
+// underflow, std::hypot (slower, scaled) elsewhere.
+static inline double rot_norm(double x, double z) {
+  const double m = std::max(std::fabs(x), std::fabs(z));
+  if (m > 1e-150 && m < 1e150) return std::sqrt(x * x + z * z);
+  return std::hypot(x, z);
+}
+
 // f(T) E1 for every beta of a grid without forming eigenvectors.
 //
-// T = Q S Q^T (Householder, Q = H_0 H_1 ... kept as reflectors), S = U Theta U^T
-// (implicit QR, U = G_1 G_2 ... kept as rotations). Then
+// T = Q S Q^T with S tridiagonal, S = U Theta U^T (implicit QR, U = G_1 G_2 ... kept
+// as rotations). Then
 //   c_beta = Q U exp(-beta (Theta - t_min)/2) U^T Q^T E1,
-// applied to the p columns of E1 only: O(n^3) for the reduction plus O(n^2 p) per
-// beta instead of the O(n^3) accumulation of full eigenvectors. The shift is this
-// matrix's own smallest eigenvalue t_min (no overflow); the caller rescales by
-// exp(-beta (t_min - E0)/2) once the common E0 is known.
+// applied to the p columns of E1 only instead of accumulating full eigenvectors.
+// Q comes from one of two reductions to tridiagonal form:
+//  * T banded with semi-bandwidth b < n - 2 (the block tridiagonal T_l of Algorithm 1
+//    has b = d_s): Givens rotations that zero the band column by column and chase
+//    each bulge they create down the band (Schwarz's band reduction, Golub & Van Loan
+//    Sec. 8.3 notes), O(n^2 b) work; Q = R_1^T R_2^T ... kept as rotations.
+//  * otherwise Householder reflectors, O(n^3); Q = H_0 H_1 ... kept as reflectors.
+// The shift is this matrix's own smallest eigenvalue t_min (no overflow); the caller
+// rescales by exp(-beta (t_min - E0)/2) once the common E0 is known.
 bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas, double* t_min,
                double* c_out) {
   std::vector<double> a(t_in, t_in + (size_t)n * n);
   auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
-  std::vector<double> hv((size_t)n * n, 0.0), hb(n, 0.0);  // reflector k: v in row k, beta
+  std::vector<double> hv, hb;  // Householder reflector k: v in row k, beta
   std::vector<double> p_(n), wv(n);
-  for (int k = 0; k + 2 < n; ++k) {
+  int band = 0;  // semi-bandwidth of T
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (A(i, j) != 0.0 || A(j, i) != 0.0) band = std::max(band, i - j);
+  const bool banded = band >= 2 && band < n - 2;
+  // y = Q^T E1 (n x p, row-major), built alongside the reduction.
+  std::vector<double> y((size_t)n * p, 0.0);
+  for (int i = 0; i < p && i < n; ++i) y[(size_t)i * p + i] = 1.0;
+  struct BandRot {
+    int q;  // plane (q - 1, q)
+    double c, s;
+  };
+  std::vector<BandRot> brots;
+  if (banded) {
+    // Rotation R in plane (q-1, q) with rows (c s; -s c): A <- R A R^T, y <- R y. Rows
+    // and columns q-1, q are nonzero only within band + 1 of the diagonal (the bulge),
+    // so only that window is touched.
+    auto rotate = [&](int q, double c, double s) {
+      const int pr = q - 1;
+      const int lo = std::max(0, pr - band - 2), hi = std::min(n, q + band + 3);
+      double* rp = &a[(size_t)pr * n];
+      double* rq = &a[(size_t)q * n];
+      for (int j = lo; j < hi; ++j) {
+        const double u = rp[j], w = rq[j];
+        rp[j] = c * u + s * w;
+        rq[j] = -s * u + c * w;
+      }
+      for (int i = lo; i < hi; ++i) {
+        double* ri = &a[(size_t)i * n];
+        const double u = ri[pr], w = ri[q];
+        ri[pr] = c * u + s * w;
+        ri[q] = -s * u + c * w;
+      }
+      double* yp = &y[(size_t)pr * p];
+      double* yq = &y[(size_t)q * p];
+      for (int t = 0; t < p; ++t) {
+        const double u = yp[t], w = yq[t];
+        yp[t] = c * u + s * w;
+        yq[t] = -s * u + c * w;
+      }
+      brots.push_back(BandRot{q, c, s});
+    };
+    for (int k = 0; k + 2 < n; ++k) {
+      for (int l = std::min(band, n - 1 - k); l >= 2; --l) {
+        // zero A(k + l, k) from row k + l - 1, then chase the bulge it leaves at
+        // (i + band, i - 1) down the band until it leaves the matrix
+        int i = k + l, col = k;
+        while (true) {
+          const double x = A(i - 1, col), z = A(i, col);
+          if (z != 0.0) {
+            const double r = rot_norm(x, z);
+            rotate(i, x / r, z / r);
+            A(i, col) = A(col, i) = 0.0;
+          }
+          if (i + band >= n) break;
+          col = i - 1;
+          i += band;
+        }
+      }
+    }
+  } else {
+    hv.assign((size_t)n * n, 0.0);
+    hb.assign(n, 0.0);
+  }
+  for (int k = 0; !banded && k + 2 < n; ++k) {
     double tail = 0.0;
     for (int i = k + 2; i < n; ++i) tail += A(i, k) * A(i, k);
     if (tail == 0.0) continue;
@@ -197,9 +274,7 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = A(i, i);
   for (int i = 0; i + 1 < n; ++i) e[i] = A(i + 1, i);
-  // y = Q^T E1 (n x p, row-major): apply H_0, H_1, ... in order.
-  std::vector<double> y((size_t)n * p, 0.0);
-  for (int i = 0; i < p && i < n; ++i) y[(size_t)i * p + i] = 1.0;
+  // Householder case: y = Q^T E1 by applying H_0, H_1, ... in order.
   auto apply_reflector = [&](int k, std::vector<double>& z) {
     if (hb[k] == 0.0) return;
     const double* v = &hv[(size_t)k * n];
@@ -210,7 +285,8 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
       for (int i = k + 1; i < n; ++i) z[(size_t)i * p + c] -= dot * v[i];
     }
   };
-  for (int k = 0; k + 2 < n; ++k) apply_reflector(k, y);
+  if (!banded)
+    for (int k = 0; k + 2 < n; ++k) apply_reflector(k, y);
   // Implicit QR with Wilkinson shift; each rotation is also applied to y (U^T y).
   struct Rot {
     int k;
@@ -250,7 +326,7 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
     double x = d[lo] - mu;
     double z = e[lo];
     for (int k = lo; k < hi; ++k) {
-      const double r = std::hypot(x, z);
+      const double r = rot_norm(x, z);
       const double c = r == 0.0 ? 1.0 : x / r;
       const double sn = r == 0.0 ? 0.0 : -z / r;
       if (k > lo) e[k - 1] = r;
@@ -288,7 +364,20 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
         zc[q] = -g.s * u + g.c * w;
       }
     }
-    for (int k = n - 3; k >= 0; --k) apply_reflector(k, zb);
+    if (banded) {  // Q z = R_1^T ... R_m^T z: transposed rotations in reverse order
+      for (size_t r = brots.size(); r-- > 0;) {
+        const BandRot& g = brots[r];
+        double* za = &zb[(size_t)(g.q - 1) * p];
+        double* zc = &zb[(size_t)g.q * p];
+        for (int q = 0; q < p; ++q) {
+          const double u = za[q], w = zc[q];
+          za[q] = g.c * u - g.s * w;
+          zc[q] = g.s * u + g.c * w;
+        }
+      }
+    } else {
+      for (int k = n - 3; k >= 0; --k) apply_reflector(k, zb);
+    }
     std::copy(zb.begin(), zb.end(), c_out + (size_t)b * n * p);
   }
   return true;

@@ -1063,7 +1063,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       for (int m = 0; m < RPT; ++m) VecIO<T, VW>::st_cs(zrow + m * kStep, y[m]);
     } else {
       // this lane's mixing coefficients, read per tile (broadcast shared-memory reads)
-      // so they hold no registers while the partner tiles are consumed
+      // so they hold no registers while the partner tiles are consumed. M_j is upper
+      // triangular (the inverse Cholesky factor, exact zeros below the diagonal), so
+      // z = y M_j skips the zero products: the same fma chain, ended early.
       T mz[NV], cp[NV];
 #pragma unroll
       for (int e = 0; e < NV; ++e) {
@@ -1079,7 +1081,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           for (int j = 0; j < DS; ++j) {
             T t = (T)0;
 #pragma unroll
-            for (int i = 0; i < DS; ++i) t = fma(y[m][g * DS + i], mz[g * NVG + i * DS + j], t);
+            for (int i = 0; i <= j; ++i) t = fma(y[m][g * DS + i], mz[g * NVG + i * DS + j], t);
             z[g * DS + j] = t;
           }
         if (has_prev) {

@@ -26,7 +26,9 @@ struct ServeState;
 
 // Launch statistics with CUDA-event timing on the launching stream.
 enum KernelKind {
-  kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply, kKNumKinds
+  kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply,
+  kKHostDense,  // not a kernel: host wall time of the small dense step (eigen + coefficients)
+  kKNumKinds
 };
 struct Profiler {
   bool on = false;
