@@ -391,6 +391,7 @@ static size_t plan_bytes(const Plan& p) {
   a.take<uint32_t>(4);
   a.take<char>(p.tk_bytes);
   if (p.gauss) a.take<char>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits) * L.elem);
+  if (p.gauss) a.take<double>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits));  // raw Gaussians
   return a.off + 256;
 }
 
@@ -776,6 +777,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   uint32_t* d_flags = ar.take<uint32_t>(4);
   char* d_tk = ar.take<char>(p.tk_bytes);
   char* d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
+  double* d_graw = p.gauss ? ar.take<double>((size_t)n_v * (size_t)d_b) : nullptr;
   const size_t cstride = (size_t)ng * nv;
   auto MZ = [&](int j) { return coef + (size_t)j * cstride; };                   // j = 1..k+1
   auto CP = [&](int j) { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; };
@@ -814,10 +816,10 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   if (p.tk_bytes) CK(counted([&] { return launch_tile_diag(L, ham->tiled.dg, d_tk, s); }));
   if (p.gauss) {
     CK(counted([&] {
-      return launch_gauss_norms(d_b, n_v, seed, o->first_vector, d_norm + p.n_v_pad, d_norm, s);
+      return launch_gauss_norms(d_b, n_v, seed, o->first_vector, d_norm + p.n_v_pad, d_norm, s, d_graw);
     }));
     if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
-    CK(counted([&] { return launch_gauss_fill(L, n_v, seed, o->first_vector, d_norm, d_vbuf, s); }));
+    CK(counted([&] { return launch_gauss_fill(L, n_v, seed, o->first_vector, d_norm, d_vbuf, s, d_graw); }));
   }
   auto init_block = [&](char* w) -> rdm_status {
     CK(timed(kKInit, blk_b, [&] {

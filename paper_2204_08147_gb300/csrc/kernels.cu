@@ -146,7 +146,7 @@ __device__ void block_reduce_store(const double* vals, int tpr, double* partials
 
 // ---------------------------------------------------------------- init
 
-__global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, int64_t l0, double* part) {
+__global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, int64_t l0, double* part, double* graw) {
   __shared__ double sh[kThreads];
   const int l = blockIdx.y;
   const int64_t chunk = (d_b + gridDim.x - 1) / gridDim.x;
@@ -155,6 +155,7 @@ __global__ void k_gauss_sumsq(int64_t d_b, uint64_t seed, int64_t l0, double* pa
   double acc = 0.0;
   for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
     const double g = gauss_raw(seed, (uint64_t)(l0 + l), (uint64_t)b);
+    if (graw) graw[(size_t)l * d_b + b] = g;
     acc += g * g;
   }
   sh[threadIdx.x] = acc;
@@ -214,11 +215,12 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
 }
 
 __global__ void k_gauss_fill(int64_t d_b, uint64_t seed, int64_t l0, const double* inv_norm,
-                             int precision, void* vbuf) {
+                             const double* graw, int precision, void* vbuf) {
   const int l = blockIdx.y;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < d_b;
        b += (int64_t)gridDim.x * blockDim.x) {
-    const double v = gauss_raw(seed, (uint64_t)(l0 + l), (uint64_t)b) * inv_norm[l];
+    const double g = graw ? graw[(size_t)l * d_b + b] : gauss_raw(seed, (uint64_t)(l0 + l), (uint64_t)b);
+    const double v = g * inv_norm[l];
     if (precision == RDM_FP32)
       reinterpret_cast<float*>(vbuf)[(size_t)l * d_b + b] = (float)v;
     else
@@ -1645,11 +1647,11 @@ static cudaError_t opt_in_smem(const void* func) {
   } while (0)
 
 cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, double* partials,
-                               double* inv_norm, cudaStream_t st) {
+                               double* inv_norm, cudaStream_t st, double* graw) {
   int gx = (int)((d_b + 4095) / 4096);
   if (gx > 64) gx = 64;
   if (gx < 1) gx = 1;
-  k_gauss_sumsq<<<dim3(gx, n_v), kThreads, 0, st>>>(d_b, seed, l0, partials);
+  k_gauss_sumsq<<<dim3(gx, n_v), kThreads, 0, st>>>(d_b, seed, l0, partials, graw);
   k_gauss_finish<<<(n_v + 127) / 128, 128, 0, st>>>(n_v, gx, partials, inv_norm);
   return cudaGetLastError();
 }
@@ -1663,10 +1665,10 @@ cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t 
 }
 
 cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
-                              const double* inv_norm, void* vbuf, cudaStream_t st) {
+                              const double* inv_norm, void* vbuf, cudaStream_t st, const double* graw) {
   const int64_t d_b = int64_t(1) << L.n_bath_bits;
   int gx = (int)std::min<int64_t>((d_b + 255) / 256, 1024);
-  k_gauss_fill<<<dim3(gx, n_v), 256, 0, st>>>(d_b, seed, l0, inv_norm, L.precision, vbuf);
+  k_gauss_fill<<<dim3(gx, n_v), 256, 0, st>>>(d_b, seed, l0, inv_norm, graw, L.precision, vbuf);
   return cudaGetLastError();
 }
 

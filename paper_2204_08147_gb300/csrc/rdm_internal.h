@@ -79,18 +79,21 @@ struct StepCoefs {
 // Zero vector blocks etc. are plain cudaMemsetAsync on the host side.
 
 // Gaussian bath-vector norms: inv_norm[l] = 1/||g_l|| for l < n_v (float64),
-// partials scratch of n_v * gx doubles.
+// partials scratch of n_v * gx doubles. If graw is not NULL the raw values are kept
+// there (graw[l][b], float64) for launch_gauss_fill.
 cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, double* partials,
-                               double* inv_norm, cudaStream_t st);
+                               double* inv_norm, cudaStream_t st, double* graw = nullptr);
 
 // W = [I_s (x) v_l] for l < n_v_real, zero columns beyond; vector l of the block is
 // vector l0 + l of the seeded sequence. Gaussian values come from inv_norm
 // (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T).
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
                               const double* inv_norm, const void* vbuf, void* W, cudaStream_t st);
-// vbuf[l][b] = normalised Gaussian bath vector l0 + l (T = the layout's precision).
+// vbuf[l][b] = normalised Gaussian bath vector l0 + l (T = the layout's precision),
+// from graw (the norm pass's raw values) when given, else regenerated.
 cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
-                              const double* inv_norm, void* vbuf, cudaStream_t st);
+                              const double* inv_norm, void* vbuf, cudaStream_t st,
+                              const double* graw = nullptr);
 
 // Flip terms grouped for the tiled SpMM. In the tiled layout a row of a slice is
 // kTiledLanes 16-byte vectors (32 bytes: 8 float32 / 4 float64 columns) and a tile
