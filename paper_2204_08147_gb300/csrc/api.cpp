@@ -1,12 +1,15 @@
 // Host side of the C ABI: contexts, Hamiltonian descriptors, workspace planning and
 // the orchestration of the estimator (Algorithm 1 twice, the small dense step in
 // between, the Gram at the end).
+#include <sched.h>
+
 #include <algorithm>
 #include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -720,9 +723,28 @@ static void build_t(int ds, int k, int ng, int l, const std::vector<double>& ta,
   }
 }
 
+// Host threads for the small dense step: the CPUs this process may run on (its
+// affinity mask, which a container's cpuset narrows), or RDM_HOST_THREADS if set.
+static int host_threads() {
+  static const int n = [] {
+    if (const char* e = std::getenv("RDM_HOST_THREADS")) {
+      const int v = std::atoi(e);
+      if (v > 0) return v;
+    }
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    if (sched_getaffinity(0, sizeof set, &set) == 0) {
+      const int c = CPU_COUNT(&set);
+      if (c > 0) return c;
+    }
+    return std::max(1, (int)std::thread::hardware_concurrency());
+  }();
+  return n;
+}
+
 template <typename F>
 static void parallel_for(int n, F&& f) {
-  int nt = (int)std::thread::hardware_concurrency();
+  int nt = host_threads();
   nt = std::max(1, std::min(nt, n));
   if (nt == 1) {
     for (int i = 0; i < n; ++i) f(i);
