@@ -48,6 +48,12 @@ def log_partition_chain(n: int, beta: float, j: float = 1.0, h: float = 0.3) -> 
     return float(beta * n * h / 2.0 + np.sum(np.logaddexp(0.0, -beta * lam)))
 
 
+def mean_energy_chain(n: int, beta: float, j: float = 1.0, h: float = 0.3) -> float:
+    """<H> = -d ln Z_N / d beta = -N h / 2 + sum_k lambda_k / (1 + exp(beta lambda_k))."""
+    lam = _lam(n, j, h)
+    return float(-n * h / 2.0 + np.sum(lam / (1.0 + np.exp(beta * lam))))
+
+
 def log_z_star(n: int, beta: float, j: float = 1.0, h: float = 0.3) -> float:
     """ln Z* = ln Z_N - ln Z_{N-2} (system = first two sites, bath = the open chain rest)."""
     return log_partition_chain(n, beta, j, h) - log_partition_chain(n - 2, beta, j, h)

@@ -371,3 +371,57 @@ def test_absolute_mean_force_matches_app_c():
 def test_mean_force_rejects_singular():
     with pytest.raises(ValueError):
         post.mean_force(np.diag([1.0, 0.0]), 1.0)
+
+
+# ---------------------------------------------------------------- bath partition, H* constant, energy deviation
+
+def test_mean_energy_chain_is_minus_dlnz_dbeta_and_matches_ed():
+    n, beta, j, h = 6, 0.9, 1.0, 0.3
+    eps = 1e-5
+    num = -(closed_form.log_partition_chain(n, beta + eps, j, h)
+            - closed_form.log_partition_chain(n, beta - eps, j, h)) / (2 * eps)
+    assert abs(closed_form.mean_energy_chain(n, beta, j, h) - num) < 1e-8
+    hm = spin_ops.dense_hamiltonian(W.xy_open_chain(n, 1, j, h))
+    w = np.linalg.eigvalsh(hm)
+    f = np.exp(-beta * (w - w[0]))
+    assert abs(closed_form.mean_energy_chain(n, beta, j, h) - float(np.sum(w * f) / f.sum())) < 1e-12
+
+
+def test_bath_spec_is_the_bare_bath():
+    spec = W.random_model(7, 2, 81)
+    b = W.bath_spec(spec)
+    assert b.n_sites == 5 and b.n_sys == 0
+    w = np.linalg.eigvalsh(spin_ops.dense_hamiltonian(b))
+    for beta in (0.3, 2.0):
+        ln_zb = float(np.log(np.sum(np.exp(-beta * (w - w[0])))) - beta * w[0])
+        assert abs(exact.bath_log_partition(spec, beta) - ln_zb) < 1e-12
+
+
+def test_energy_deviation_app_c_closed_form():
+    """App. C chain, N_s = 2: tr(H* rho*) = (S(rho*) - ln Z*)/beta from the closed-form
+    p_j and Z*, and tr(H_s rho_s) is the mean energy of the 2-site chain."""
+    n, beta, j, h = 8, 1.3, 1.0, 0.3
+    spec = W.xy_open_chain(n, 2, j, h)
+    rho, _ = exact.exact_rho(spec, [beta])
+    hstar = post.mean_force(rho[0], beta, closed_form.log_z_star(n, beta, j, h))
+    hs = np.real(spin_ops.subsystem_hamiltonian(spec, "sys"))
+    got = post.energy_deviation(rho[0], hstar, hs, beta)
+    p = closed_form.rho_eigenvalues(n, beta, j, h)
+    s = float(-np.sum(p * np.log(p)))
+    want = (s - closed_form.log_z_star(n, beta, j, h)) / beta - closed_form.mean_energy_chain(2, beta, j, h)
+    assert abs(got - want) < 1e-12
+
+
+def test_energy_deviation_vanishes_without_coupling():
+    """lambda = 0: H_t = H_s + H_b, so Z_t = Z_s Z_b, H* = H_s and the deviation is 0."""
+    spec = W.random_model(7, 1, 82, lam=0.0)
+    beta = 0.8
+    rho, lnz = exact.exact_rho(spec, [beta])
+    ln_zb = exact.bath_log_partition(spec, beta)
+    hs = np.real(spin_ops.subsystem_hamiltonian(spec, "sys"))
+    ws = np.linalg.eigvalsh(hs)
+    ln_zs = float(np.log(np.sum(np.exp(-beta * (ws - ws[0])))) - beta * ws[0])
+    assert abs(lnz[0] - (ln_zs + ln_zb)) < 1e-11
+    hstar = post.mean_force(rho[0], beta, lnz[0] - ln_zb)
+    np.testing.assert_allclose(hstar, hs, atol=1e-11)
+    assert abs(post.energy_deviation(rho[0], hstar, hs, beta)) < 1e-11

@@ -29,6 +29,7 @@ __all__ = [
     "long_range_xxz",
     "long_range_tfim",
     "random_model",
+    "bath_spec",
     "beta_grid",
     "config_c1",
     "config_c2",
@@ -124,6 +125,15 @@ def long_range_tfim(n: int, n_sys: int, alpha: float, g: float, lam: float = 1.0
             jz[a, b] = j / float(b - a) ** alpha
     gx[:] = g
     return ModelSpec(n, n_sys, jx, jy, jz, hz, gx, lam, f"lr_tfim_N{n}_g{g:.3f}")
+
+
+def bath_spec(spec: ModelSpec) -> ModelSpec:
+    """The bare bath of ``spec`` (its bath sites and the couplings among them) as a
+    model with no system sites; bath site q of ``spec`` becomes site q - n_sys."""
+    s = spec.n_sys
+    return ModelSpec(spec.n_sites - s, 0, spec.jx[s:, s:].copy(), spec.jy[s:, s:].copy(),
+                     spec.jz[s:, s:].copy(), spec.hz[s:].copy(), spec.gx[s:].copy(), 1.0,
+                     (spec.name + "_bath") if spec.name else "bath")
 
 
 def random_model(n: int, n_sys: int, seed: int, lam: float = 0.7, density: float = 0.6,
