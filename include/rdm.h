@@ -181,6 +181,21 @@ rdm_status rdm_profile_stats(rdm_ctx* ctx, rdm_kernel_stat* out, int max, int* n
 rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_ham** out);
 void rdm_destroy_hamiltonian(rdm_ham* ham);
 
+/* The bare bath Hamiltonian H_b of a model (Sec. 3.2): the terms of `model` acting on
+ * bath sites only (sites n_sys .. n_sites-1, renumbered from 0; the spin at bath site q
+ * keeps its bit, so bath basis states index alike), as a Hamiltonian with no system
+ * sites (d_s = 1). rdm_estimate on it with the same seed, n_v, vector distribution and
+ * first_vector as on the total model draws the same bath vectors v_l and returns in
+ * ln_z the Lanczos quadrature estimate of ln Z_b = ln tr exp(-beta H_b), the
+ * denominator of eq. H_est. Free with rdm_destroy_hamiltonian. Errors as
+ * rdm_build_hamiltonian. */
+rdm_status rdm_build_bath_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_ham** out);
+
+/* The bare system Hamiltonian H_s of a model (its terms on system sites only) as a
+ * dense d_s x d_s row-major real matrix, host, d_s = 2^n_sys (eq. Ht restricted to
+ * the system; the basis order of rho). RDM_EINVAL as rdm_build_hamiltonian. */
+rdm_status rdm_system_hamiltonian(const rdm_model* model, double* hs_out);
+
 /* Sizes and the bound ||H||_2 <= sum of |term coefficients| used to scale the
  * Lanczos breakdown tolerance. Any output pointer may be NULL. */
 rdm_status rdm_hamiltonian_info(const rdm_ham* ham, int* n_sites, int* n_sys,
@@ -243,6 +258,21 @@ rdm_status rdm_starting_block_noalloc(rdm_ham* ham, int precision, int n_v, uint
  * -(1/beta) ln Z*. RDM_ENOTPD if an eigenvalue of rho is <= 0. 1 <= d_s <= 64,
  * beta > 0. */
 rdm_status rdm_mean_force(const double* rho, int d_s, double beta, double* h_out);
+
+/* H*(beta) with its constant, eq. H_est (Sec. 3.2):
+ *   H* = -(1/beta) ln(Z_t rho* / Z_b) = -(1/beta) ln(rho*) - (1/beta)(ln Z_t - ln Z_b) I,
+ * from rho* and ln Z_t of rdm_estimate on the total model and ln Z_b of rdm_estimate on
+ * rdm_build_bath_hamiltonian of the same model (same bath vectors). Errors as
+ * rdm_mean_force; RDM_EINVAL for non-finite ln_z_t or ln_z_b. */
+rdm_status rdm_mean_force_abs(const double* rho, int d_s, double beta, double ln_z_t,
+                              double ln_z_b, double* h_out);
+
+/* Deviation of the system's internal energy by the coupling (Sec. 5.3.2, eq.
+ * deviation_of_Hamiltonian): tr(H* rho*) - tr(H_s rho_s) with
+ * rho_s = exp(-beta H_s) / tr exp(-beta H_s). h_star from rdm_mean_force_abs, h_s
+ * from rdm_system_hamiltonian, all d_s x d_s row-major host arrays. */
+rdm_status rdm_energy_deviation(const double* rho, const double* h_star, const double* h_s,
+                                int d_s, double beta, double* out);
 
 /* S = -tr(rho ln rho) = -sum_i p_i ln p_i with 0 ln 0 = 0 (Sec. 5.3.1). */
 rdm_status rdm_entropy(const double* rho, int d_s, double* s_out);

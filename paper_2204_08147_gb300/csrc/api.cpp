@@ -560,6 +560,74 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   return RDM_OK;
 }
 
+// The model restricted to sites [first, first + count), renumbered from 0, with no
+// system sites: the bath part (first = n_sys) or the system part (first = 0).
+namespace {
+struct PartModel {
+  std::vector<double> jx, jy, jz, hz, gx;
+  rdm_model m{};
+};
+rdm_status part_model(const rdm_model* model, int first, int count, PartModel* pm) {
+  const int n = model->n_sites;
+  pm->jx.assign((size_t)count * count, 0.0);
+  pm->jy = pm->jx;
+  pm->jz = pm->jx;
+  pm->hz.assign(count, 0.0);
+  pm->gx.assign(count, 0.0);
+  for (int a = 0; a < count; ++a) {
+    for (int b = a + 1; b < count; ++b) {
+      const size_t src = (size_t)(first + a) * n + (first + b), dst = (size_t)a * count + b;
+      if (model->jx) pm->jx[dst] = model->jx[src];
+      if (model->jy) pm->jy[dst] = model->jy[src];
+      if (model->jz) pm->jz[dst] = model->jz[src];
+    }
+    if (model->hz) pm->hz[a] = model->hz[first + a];
+    if (model->gx) pm->gx[a] = model->gx[first + a];
+  }
+  pm->m = rdm_model{count, 0, pm->jx.data(), pm->jy.data(), pm->jz.data(), pm->hz.data(), pm->gx.data(), 1.0};
+  return RDM_OK;
+}
+}  // namespace
+
+extern "C" rdm_status rdm_build_bath_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_ham** out) {
+  if (!ctx || !model || !out) {
+    set_error("rdm_build_bath_hamiltonian: NULL argument");
+    return RDM_EINVAL;
+  }
+  HostModel check;
+  rdm_status st = compile_model(model, &check);  // validates sizes and values
+  if (st != RDM_OK) return st;
+  PartModel pm;
+  part_model(model, model->n_sys, model->n_sites - model->n_sys, &pm);
+  return rdm_build_hamiltonian(ctx, &pm.m, out);
+}
+
+extern "C" rdm_status rdm_system_hamiltonian(const rdm_model* model, double* hs_out) {
+  if (!model || !hs_out) {
+    set_error("rdm_system_hamiltonian: NULL argument");
+    return RDM_EINVAL;
+  }
+  HostModel check;
+  rdm_status st = compile_model(model, &check);
+  if (st != RDM_OK) return st;
+  const int ns = model->n_sys, ds = 1 << ns;
+  std::fill(hs_out, hs_out + (size_t)ds * ds, 0.0);
+  if (ns == 0) return RDM_OK;
+  PartModel pm;
+  part_model(model, 0, ns, &pm);
+  HostModel hs;
+  st = compile_model(&pm.m, &hs);
+  if (st != RDM_OK) return st;
+  // the term convention of the SpMM (FlipTerm, DiagTerm), written out densely
+  for (uint32_t s = 0; s < (uint32_t)ds; ++s) {
+    for (const FlipTerm& f : hs.flips)
+      hs_out[(size_t)(s ^ f.mask) * ds + s] += (__builtin_popcount(s & f.mask) & 1) ? f.c_odd : f.c_even;
+    for (const DiagTerm& d : hs.diags)
+      hs_out[(size_t)s * ds + s] += (__builtin_popcount(s & d.mask) & 1) ? -d.c : d.c;
+  }
+  return RDM_OK;
+}
+
 extern "C" void rdm_destroy_hamiltonian(rdm_ham* ham) {
   if (!ham) return;
   cudaSetDevice(ham->ctx->device);

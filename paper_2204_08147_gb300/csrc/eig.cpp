@@ -444,6 +444,55 @@ extern "C" rdm_status rdm_mean_force(const double* rho, int d_s, double beta, do
   return RDM_OK;
 }
 
+extern "C" rdm_status rdm_mean_force_abs(const double* rho, int d_s, double beta, double ln_z_t,
+                                         double ln_z_b, double* h_out) {
+  if (!std::isfinite(ln_z_t) || !std::isfinite(ln_z_b)) {
+    set_error("rdm_mean_force_abs: ln_z_t and ln_z_b must be finite");
+    return RDM_EINVAL;
+  }
+  const rdm_status st = rdm_mean_force(rho, d_s, beta, h_out);
+  if (st != RDM_OK) return st;
+  // -(1/beta) ln(Z_t rho / Z_b) = -(1/beta) ln rho - (1/beta)(ln Z_t - ln Z_b) I
+  const double shift = (ln_z_t - ln_z_b) / beta;
+  for (int r = 0; r < d_s; ++r) h_out[r * d_s + r] -= shift;
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_energy_deviation(const double* rho, const double* h_star, const double* h_s,
+                                           int d_s, double beta, double* out) {
+  if (!rho || !h_star || !h_s || !out || d_s < 1 || d_s > 64 || !(beta > 0) || !std::isfinite(beta)) {
+    set_error("rdm_energy_deviation: need non-NULL arrays, 1 <= d_s <= 64 and finite beta > 0");
+    return RDM_EINVAL;
+  }
+  std::vector<double> hs, w(d_s), vt((size_t)d_s * d_s);
+  if (!symmetrised(h_s, d_s, hs)) {
+    set_error("rdm_energy_deviation: h_s has non-finite entries");
+    return RDM_ENUMERIC;
+  }
+  if (!rdm::sym_eig(d_s, hs.data(), w.data(), vt.data())) {
+    set_error("rdm_energy_deviation: eigensolver did not converge");
+    return RDM_ENUMERIC;
+  }
+  // tr(H_s rho_s) = sum_j w_j e^{-beta (w_j - w_0)} / sum_j e^{-beta (w_j - w_0)}
+  double z = 0.0, e_s = 0.0;
+  for (int j = 0; j < d_s; ++j) {
+    const double f = std::exp(-beta * (w[j] - w[0]));
+    z += f;
+    e_s += w[j] * f;
+  }
+  // tr(H* rho*) with both symmetrised
+  double e_star = 0.0;
+  for (int r = 0; r < d_s; ++r)
+    for (int c = 0; c < d_s; ++c)
+      e_star += 0.25 * (h_star[r * d_s + c] + h_star[c * d_s + r]) * (rho[c * d_s + r] + rho[r * d_s + c]);
+  if (!std::isfinite(e_star)) {
+    set_error("rdm_energy_deviation: h_star or rho has non-finite entries");
+    return RDM_ENUMERIC;
+  }
+  *out = e_star - e_s / z;
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_entropy(const double* rho, int d_s, double* s_out) {
   if (!rho || !s_out || d_s < 1 || d_s > 64) {
     set_error("rdm_entropy: need rho, s_out and 1 <= d_s <= 64");

@@ -80,6 +80,10 @@ _sig("rdm_apply_hamiltonian", C.c_int, _vp, C.c_int, _vp, _vp, C.c_int)
 _sig("rdm_starting_block", C.c_int, _vp, C.c_int, C.c_int, C.c_uint64, C.c_int, _vp)
 _sig("rdm_starting_block_noalloc", C.c_int, _vp, C.c_int, C.c_int, C.c_uint64, C.c_int, _vp)
 _sig("rdm_mean_force", C.c_int, _dp, C.c_int, C.c_double, _dp)
+_sig("rdm_build_bath_hamiltonian", C.c_int, _vp, C.POINTER(Model), C.POINTER(_vp))
+_sig("rdm_system_hamiltonian", C.c_int, C.POINTER(Model), _dp)
+_sig("rdm_mean_force_abs", C.c_int, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp)
+_sig("rdm_energy_deviation", C.c_int, _dp, _dp, _dp, C.c_int, C.c_double, _dp)
 _sig("rdm_entropy", C.c_int, _dp, C.c_int, _dp)
 _sig("rdm_symmetric_eig", C.c_int, C.c_int, _dp, _dp, _dp)
 _sig("rdm_serve_start", C.c_int, _vp, C.c_size_t, C.c_int)
@@ -275,15 +279,23 @@ class Context:
 class Hamiltonian:
     """A model compiled to term descriptors on the context's device."""
 
-    def __init__(self, ctx: Context, spec):
+    def __init__(self, ctx: Context, spec, part: str = "total"):
+        """part="total": the model; part="bath": its bare bath H_b (no system sites),
+        whose estimate with the same seed, n_v and distribution gives ln Z_b."""
         self.ctx = ctx
         self.spec = spec
         m = _ModelArrays(spec)
         h = _vp()
-        _check(_lib.rdm_build_hamiltonian(ctx.h, C.byref(m.struct), C.byref(h)), "rdm_build_hamiltonian")
+        if part == "total":
+            _check(_lib.rdm_build_hamiltonian(ctx.h, C.byref(m.struct), C.byref(h)), "rdm_build_hamiltonian")
+            self.n_sites, self.n_sys = int(spec.n_sites), int(spec.n_sys)
+        elif part == "bath":
+            _check(_lib.rdm_build_bath_hamiltonian(ctx.h, C.byref(m.struct), C.byref(h)),
+                   "rdm_build_bath_hamiltonian")
+            self.n_sites, self.n_sys = int(spec.n_sites) - int(spec.n_sys), 0
+        else:
+            raise ValueError("part must be 'total' or 'bath'")
         self.h = h
-        self.n_sites = int(spec.n_sites)
-        self.n_sys = int(spec.n_sys)
         self.d_s = 1 << self.n_sys
         self.dim = 1 << self.n_sites
 
@@ -357,6 +369,36 @@ def mean_force(rho: np.ndarray, beta: float) -> np.ndarray:
     out = np.zeros((d, d))
     _check(_lib.rdm_mean_force(_ptr(r), d, float(beta), _ptr(out)), "rdm_mean_force")
     return out
+
+
+def mean_force_abs(rho: np.ndarray, beta: float, ln_z_t: float, ln_z_b: float) -> np.ndarray:
+    """H* with its constant (eq. H_est): -(1/beta)(ln rho + (ln Z_t - ln Z_b) I)."""
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    d = r.shape[0]
+    out = np.zeros((d, d))
+    _check(_lib.rdm_mean_force_abs(_ptr(r), d, float(beta), float(ln_z_t), float(ln_z_b), _ptr(out)),
+           "rdm_mean_force_abs")
+    return out
+
+
+def system_hamiltonian(spec) -> np.ndarray:
+    """The bare system Hamiltonian H_s of a model, d_s x d_s (host)."""
+    m = _ModelArrays(spec)
+    d = 1 << int(spec.n_sys)
+    out = np.zeros((d, d))
+    _check(_lib.rdm_system_hamiltonian(C.byref(m.struct), _ptr(out)), "rdm_system_hamiltonian")
+    return out
+
+
+def energy_deviation(rho: np.ndarray, h_star: np.ndarray, h_s: np.ndarray, beta: float) -> float:
+    """tr(H* rho*) - tr(H_s rho_s) (Sec. 5.3.2)."""
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    hst = np.ascontiguousarray(h_star, dtype=np.float64)
+    hs = np.ascontiguousarray(h_s, dtype=np.float64)
+    out = C.c_double()
+    _check(_lib.rdm_energy_deviation(_ptr(r), _ptr(hst), _ptr(hs), r.shape[0], float(beta), C.byref(out)),
+           "rdm_energy_deviation")
+    return out.value
 
 
 def entropy(rho: np.ndarray) -> float:

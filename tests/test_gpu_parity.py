@@ -391,3 +391,85 @@ def test_shards_combine_to_the_whole_run(ctx, lib, prec, tol):
     # and against the oracle
     ref = lanczos.Estimator(spec).run(betas, 10, 24, 31, "gauss")
     np.testing.assert_allclose(res["rho"], ref["rho"], atol=TOL64 if prec == "fp64" else TOL32)
+
+
+# ---------------------------------------------------------------- bath partition, H* with its constant
+
+@pytest.mark.parametrize("dist", ["gauss", "rademacher"])
+def test_bath_hamiltonian_draws_the_same_bath_vectors(ctx, lib, dist):
+    """eq. H_est takes numerator and denominator over the same v_l: the bath model's
+    starting vectors equal the system-index-0 rows of the total model's block."""
+    torch = _torch()
+    spec = W.random_model(9, 2, 94)
+    tot = lib.Hamiltonian(ctx, spec)
+    bath = lib.Hamiltonian(ctx, spec, part="bath")
+    assert bath.n_sites == 7 and bath.d_s == 1
+    n_v, d_b = 4, 1 << 7
+    xt = torch.empty((1 << 9, 4 * n_v), dtype=torch.float64, device="cuda")
+    xb = torch.empty((d_b, n_v), dtype=torch.float64, device="cuda")
+    tot.starting_block(xt, n_v, 77, dist)
+    bath.starting_block(xb, n_v, 77, dist)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(xt.cpu().numpy()[:d_b, 0::4], xb.cpu().numpy())
+
+
+def test_bath_ln_z_exhaustive_is_exact(ctx, lib):
+    spec = W.random_model(9, 2, 95)
+    bath = lib.Hamiltonian(ctx, spec, part="bath")
+    betas = [0.2, 1.0, 3.0]
+    d_b = 1 << 7
+    out = bath.estimate(betas, d_b, d_b + 2, 0, precision="fp64", dist="basis")
+    for i, b in enumerate(betas):
+        assert abs(out["lnZ"][i] - exact.bath_log_partition(spec, b)) < 1e-9
+
+
+def test_bath_ln_z_matches_oracle_same_seed(ctx, lib):
+    """Lanczos quadrature for ln Z_b on the (tiled, N_b = 11) bath model against the
+    oracle run on the same Gaussian vectors."""
+    spec = W.random_model(12, 1, 96)
+    bath = lib.Hamiltonian(ctx, spec, part="bath")
+    betas = [0.5, 2.0]
+    out = bath.estimate(betas, 6, 30, 5, precision="fp64", dist="gauss")
+    ref = lanczos.Estimator(W.bath_spec(spec)).run(betas, 6, 30, 5, "gauss")
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], atol=1e-9, rtol=0)
+
+
+def test_absolute_mean_force_and_energy_deviation_app_c(ctx, lib):
+    """App. C chain, exhaustive bath vectors on both models: the eigenvalues of H*
+    with its constant and the internal-energy deviation against the closed form."""
+    n, j, h = 8, 1.0, 0.3
+    spec = W.xy_open_chain(n, 2, j, h)
+    tot = lib.Hamiltonian(ctx, spec)
+    bath = lib.Hamiltonian(ctx, spec, part="bath")
+    betas = [0.7, 1.3]
+    d_b = 1 << (n - 2)
+    rt = tot.estimate(betas, d_b, (1 << n) // 4 + 2, 0, precision="fp64", dist="basis")
+    rb = bath.estimate(betas, d_b, d_b + 2, 0, precision="fp64", dist="basis")
+    hs = lib.system_hamiltonian(spec)
+    for i, beta in enumerate(betas):
+        hstar = lib.mean_force_abs(rt["rho"][i], beta, rt["lnZ"][i], rb["lnZ"][i])
+        np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(hstar)),
+                                   np.sort(closed_form.mean_force_eigenvalues(n, beta, j, h)), atol=1e-9)
+        p = closed_form.rho_eigenvalues(n, beta, j, h)
+        want = (float(-np.sum(p * np.log(p))) - closed_form.log_z_star(n, beta, j, h)) / beta \
+            - closed_form.mean_energy_chain(2, beta, j, h)
+        assert abs(lib.energy_deviation(rt["rho"][i], hstar, hs, beta) - want) < 1e-9
+
+
+def test_energy_deviation_lr_tfim_fp32_vs_oracle(ctx, lib):
+    """float32 path end to end (rho*, ln Z_t, ln Z_b, H*, deviation) against the oracle
+    estimator on the same Gaussian vectors."""
+    spec = W.long_range_tfim(12, 2, 1.5, 0.8)
+    betas = [1.0]
+    n_v, k, seed = 16, 40, 31
+    rt = lib.Hamiltonian(ctx, spec).estimate(betas, n_v, k, seed, precision="fp32", dist="gauss")
+    rb = lib.Hamiltonian(ctx, spec, part="bath").estimate(betas, n_v, k, seed, precision="fp32", dist="gauss")
+    ot = lanczos.Estimator(spec).run(betas, n_v, k, seed, "gauss")
+    ob = lanczos.Estimator(W.bath_spec(spec)).run(betas, n_v, k, seed, "gauss")
+    hs = lib.system_hamiltonian(spec)
+    hstar = lib.mean_force_abs(rt["rho"][0], 1.0, rt["lnZ"][0], rb["lnZ"][0])
+    href = post.mean_force(ot["rho"][0], 1.0, ot["lnZ"][0] - ob["lnZ"][0])
+    np.testing.assert_allclose(hstar, href, atol=2e-3)
+    dev = lib.energy_deviation(rt["rho"][0], hstar, hs, 1.0)
+    dref = post.energy_deviation(ot["rho"][0], href, np.real(spin_ops.subsystem_hamiltonian(spec, "sys")), 1.0)
+    assert abs(dev - dref) < 2e-3

@@ -78,6 +78,39 @@ def test_mean_force_and_entropy_match_oracle(rdm):
     assert abs(rdm.entropy(np.diag([1.0, 0.0]))) == 0.0
 
 
+def test_absolute_mean_force_and_energy_deviation_match_oracle(rdm):
+    from oracle import post
+    rng = np.random.default_rng(3)
+    for d in (1, 2, 4):
+        x = rng.normal(size=(d, d))
+        rho = x @ x.T + 0.1 * np.eye(d)
+        rho /= np.trace(rho)
+        y = rng.normal(size=(d, d))
+        hs = y + y.T
+        beta, ln_zt, ln_zb = 0.7, 3.1, 2.4
+        hstar = rdm.mean_force_abs(rho, beta, ln_zt, ln_zb)
+        np.testing.assert_allclose(hstar, post.mean_force(rho, beta, ln_zt - ln_zb), atol=1e-12)
+        assert abs(rdm.energy_deviation(rho, hstar, hs, beta) - post.energy_deviation(rho, hstar, hs, beta)) < 1e-12
+    with pytest.raises(rdm.RdmError) as e:
+        rdm.mean_force_abs(np.eye(2) / 2, 1.0, float("nan"), 0.0)
+    assert e.value.status == rdm.EINVAL
+
+
+@pytest.mark.parametrize("n,n_sys,seed", [(5, 1, 90), (6, 2, 91), (4, 2, 92), (3, 0, 93)])
+def test_system_hamiltonian_matches_oracle(rdm, n, n_sys, seed):
+    """H_s in the SpMM's term convention against the oracle's Kronecker-product H_s."""
+    import workloads as W
+    from oracle import spin_ops
+    spec = W.random_model(n, n_sys, seed)
+    got = rdm.system_hamiltonian(spec)
+    if n_sys == 0:
+        np.testing.assert_array_equal(got, np.zeros((1, 1)))
+        return
+    want = spin_ops.subsystem_hamiltonian(spec, "sys")
+    assert np.abs(np.imag(want)).max() == 0.0
+    np.testing.assert_allclose(got, np.real(want), atol=1e-13)
+
+
 def test_mean_force_rejects_non_positive(rdm):
     with pytest.raises(rdm.RdmError) as e:
         rdm.mean_force(np.diag([1.0, 0.0]), 1.0)
