@@ -473,3 +473,30 @@ def test_energy_deviation_lr_tfim_fp32_vs_oracle(ctx, lib):
     dev = lib.energy_deviation(rt["rho"][0], hstar, hs, 1.0)
     dref = post.energy_deviation(ot["rho"][0], href, np.real(spin_ops.subsystem_hamiltonian(spec, "sys")), 1.0)
     assert abs(dev - dref) < 2e-3
+
+
+# ---------------------------------------------------------------- c3 / c5 shapes (reduced N)
+
+def test_c3_shape_two_pass_fp32_vs_oracle(ctx, lib):
+    """The c3 configuration's structure at N = 14: all-to-all XX+YY+ZZ (alpha = 1,
+    Delta = 1, h = 0.1; flip patterns with several terms and partner rows off the
+    diagonal of the tile), N_s = 1, Rademacher vectors, 32 betas in [0.1, 10],
+    recomputed basis, float32."""
+    spec = W.long_range_xxz(14, 1, alpha=1.0, delta=1.0, h=0.1)
+    betas = W.beta_grid(32, 0.1, 10.0)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate(betas, 16, 40, 20220420, precision="fp32", dist="rademacher", passes="recompute")
+    ref = lanczos.Estimator(spec).run(betas, 16, 40, 20220420, "rademacher")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], rtol=1e-5, atol=1e-4)
+
+
+def test_c5_shape_two_pass_fp32_vs_oracle(ctx, lib):
+    """The c5 configuration's structure at N = 15: alpha = 1.5, Delta = 0.5, N_s = 1,
+    n_v = 4 Rademacher (one 8-column slice), k = 50, beta = 2, recomputed basis."""
+    spec = W.long_range_xxz(15, 1, alpha=1.5, delta=0.5)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([2.0], 4, 50, 20220421, precision="fp32", dist="rademacher", passes="recompute")
+    ref = lanczos.Estimator(spec).run([2.0], 4, 50, 20220421, "rademacher")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], rtol=1e-5, atol=1e-4)
