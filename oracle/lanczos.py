@@ -24,7 +24,9 @@ Readings where the paper is silent (used identically by the CUDA library):
     satisfies r <= max(tau_abs * ||H||_bound, tau_rel * ||z_c||) is dropped
     (its Q column and its row of R set to zero) -- Krylov breakdown/deflation;
   * E0 = the smallest eigenvalue of all T_l (common to all l);
-  * each bath vector runs its own recurrence of block size d_s (eq. trB_est).
+  * each bath vector runs its own recurrence of block size d_s (eq. trB_est);
+    ``run(..., block=False)`` instead runs one recurrence of block size 1 per
+    column e_i (x) v_l (the per-vector variant of Sec. 4.2).
 """
 from __future__ import annotations
 
@@ -133,13 +135,17 @@ class Estimator:
         return starting_block(s.d_s, bath_vector(s.d_b, l, seed, dist))
 
     def run(self, betas, n_v: int, k: int, seed: int, dist: str, vectors=None,
-            gram: bool = True, e0=None):
+            gram: bool = True, e0=None, block: bool = True):
         """Returns a dict with rho, lnZ (Gram form), rho_quad, per-l grams, E0, T.
 
         ``vectors`` restricts the run to a subset of bath-vector indices (the
         estimator is a sum over l, so any subset can be checked on its own);
-        ``e0`` then supplies the shift the full run used.
+        ``e0`` then supplies the shift the full run used. ``block=False`` runs the
+        regular (block size 1) Lanczos algorithm on each column of the starting
+        block separately (Sec. 4.2, the alternative to block Lanczos).
         """
+        if not block:
+            return self._run_single(betas, n_v, k, seed, dist)
         s = self.spec
         p = s.d_s
         betas = np.atleast_1d(np.asarray(betas, dtype=np.float64))
@@ -170,6 +176,43 @@ class Estimator:
         if gram:
             out["gram_l"] = grams
             out["rho"], out["lnZ"] = _normalise(grams, betas, e0, s.d_b, len(ls))
+        return out
+
+
+    def _run_single(self, betas, n_v: int, k: int, seed: int, dist: str):
+        """Per-column Lanczos: for starting column v_i = e_i (x) v_l, T_{l,i} from
+        Algorithm 1 with block size 1; psi_{l,i} = Q_{l,i} exp(-beta (T_{l,i} - E0)/2) e1
+        and G_l[i, j] = psi_{l,i}^T psi_{l,j} (Gram form). The quadrature form has only
+        the diagonal e1^T exp(-beta (T_{l,i} - E0)) e1 (its off-diagonal entries are
+        not estimated by single-vector quadrature and are left zero). E0 is the
+        smallest eigenvalue of all T_{l,i}."""
+        s = self.spec
+        p = s.d_s
+        betas = np.atleast_1d(np.asarray(betas, dtype=np.float64))
+        cols, ts = {}, {}
+        for l in range(n_v):
+            v = self.starting_block(l, seed, dist)
+            for i in range(p):
+                cols[l, i] = v[:, i:i + 1]
+                ts[l, i] = assemble_t(*lanczos_coefficients(self.apply_h, cols[l, i], k, self.hnorm))
+        e0 = min(float(np.linalg.eigvalsh(t)[0]) for t in ts.values())
+        quad = np.zeros((len(betas), n_v, p, p))
+        grams = np.zeros((len(betas), n_v, p, p))
+        for l in range(n_v):
+            psis = []
+            for i in range(p):
+                coefs = []
+                for bi, beta in enumerate(betas):
+                    c = function_of_t_first_block(ts[l, i], 1, lambda x: np.exp(-beta * (x - e0) / 2.0))
+                    quad[bi, l, i, i] = float((c.T @ c)[0, 0])
+                    coefs.append(c)
+                psis.append(psi_gram_form(self.apply_h, cols[l, i], k, self.hnorm, coefs))
+            for bi in range(len(betas)):
+                m = np.hstack([psis[i][bi] for i in range(p)])
+                grams[bi, l] = m.T @ m
+        out = dict(e0=e0, quad_l=quad, gram_l=grams, betas=betas)
+        out["rho_quad"], out["lnZ_quad"] = _normalise(quad, betas, e0, s.d_b, n_v)
+        out["rho"], out["lnZ"] = _normalise(grams, betas, e0, s.d_b, n_v)
         return out
 
 

@@ -425,3 +425,48 @@ def test_energy_deviation_vanishes_without_coupling():
     hstar = post.mean_force(rho[0], beta, lnz[0] - ln_zb)
     np.testing.assert_allclose(hstar, hs, atol=1e-11)
     assert abs(post.energy_deviation(rho[0], hstar, hs, beta)) < 1e-11
+
+
+# ---------------------------------------------------------------- per-vector (block size 1) Lanczos
+
+def test_single_vector_lanczos_converges_to_exact_function_estimator():
+    """Sec. 4.2: regular Lanczos on each column e_i (x) v_l, Gram form with the cross
+    terms psi_i^T psi_j; at large k it equals eq. rho_est with the exact exp(-beta H/2)."""
+    spec = W.random_model(8, 2, 5)
+    betas = [0.5, 2.0]
+    s = lanczos.Estimator(spec).run(betas, 6, 30, 3, "gauss", block=False)
+    h = spin_ops.dense_hamiltonian(spec)
+    rho2, lnz2 = lanczos.exact_function_estimator(spec, h, betas, 6, 3, "gauss")
+    np.testing.assert_allclose(s["rho"], rho2, atol=1e-9)
+    np.testing.assert_allclose(s["lnZ"], lnz2, atol=1e-9)
+    # the cross terms carry information: zeroing them changes rho
+    assert np.abs(rho2[0] - np.diag(np.diag(rho2[0]))).max() > 1e-3
+
+
+def test_single_vector_equals_block_for_one_system_state():
+    spec = W.random_model(7, 0, 6)
+    b = lanczos.Estimator(spec).run([1.0], 5, 12, 4, "rademacher")
+    s = lanczos.Estimator(spec).run([1.0], 5, 12, 4, "rademacher", block=False)
+    np.testing.assert_allclose(s["gram_l"], b["gram_l"], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(s["lnZ"], b["lnZ"], rtol=1e-13, atol=0)
+
+
+def test_single_vector_exhaustive_is_exact():
+    spec = W.random_model(6, 1, 7)
+    betas = [0.4, 3.0]
+    s = lanczos.Estimator(spec).run(betas, spec.d_b, spec.dim + 2, 0, "basis", block=False)
+    rho, lnz = exact.exact_rho(spec, betas)
+    np.testing.assert_allclose(s["rho"], rho, atol=1e-10)
+    np.testing.assert_allclose(s["lnZ"], lnz, atol=1e-9)
+
+
+def test_block_lanczos_more_accurate_than_single_at_equal_k():
+    """The paper's remark (Sec. 4.2): at equal k block Lanczos is exact to a higher
+    polynomial degree; on this model its error is smaller at every k tried."""
+    spec = W.random_model(8, 2, 5)
+    h = spin_ops.dense_hamiltonian(spec)
+    rho2, _ = lanczos.exact_function_estimator(spec, h, [2.0], 6, 3, "gauss")
+    for k in (4, 6, 8):
+        b = lanczos.Estimator(spec).run([2.0], 6, k, 3, "gauss")
+        s = lanczos.Estimator(spec).run([2.0], 6, k, 3, "gauss", block=False)
+        assert np.abs(b["rho"] - rho2).max() < np.abs(s["rho"] - rho2).max()
