@@ -101,6 +101,19 @@ typedef struct {
  * Both give bit-identical results. */
 enum { RDM_PASSES_AUTO = 0, RDM_PASSES_STORE = 1, RDM_PASSES_RECOMPUTE = 2 };
 
+/* The Lanczos recurrences per bath vector:
+ *   RDM_BLOCK:  one block Lanczos recurrence of block size d_s on I_s (x) |v_l>
+ *               (Algorithm 1);
+ *   RDM_SINGLE: one regular Lanczos recurrence (block size 1) per column e_i (x) |v_l>,
+ *               the alternative named in Sec. 4.2 (exact for polynomials of lower degree
+ *               at equal k). The Gram form takes G_l[i][j] = psi_{l,i}^T psi_{l,j}
+ *               with psi_{l,i} = Q_{l,i} exp(-beta (T_{l,i} - E0)/2) e1; the quadrature
+ *               form has only the diagonal e1^T exp(-beta (T_{l,i} - E0)) e1 (its
+ *               off-diagonal entries are left zero). E0 is the smallest eigenvalue of all
+ *               T_{l,i}; t_a/t_b hold each column's scalar coefficients on the diagonal.
+ *               Needs float32, or float64 with d_s <= 2 (RDM_EINVAL otherwise). */
+enum { RDM_BLOCK = 0, RDM_SINGLE = 1 };
+
 typedef struct {
   int precision; /* RDM_FP64 | RDM_FP32 */
   int vec_dist;  /* RDM_RADEMACHER | RDM_GAUSS | RDM_BASIS */
@@ -109,6 +122,7 @@ typedef struct {
   int64_t first_vector; /* bath vectors l = first_vector .. first_vector+n_v-1 of the
                            seeded sequence (0 for a whole run; a shard of a run split
                            over GPUs starts further in, eq. trace_est is a sum over l) */
+  int recurrence; /* RDM_BLOCK | RDM_SINGLE */
 } rdm_opts;
 
 /* Outputs of rdm_estimate; every pointer is a caller-owned host array. rho is

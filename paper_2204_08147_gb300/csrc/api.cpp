@@ -290,7 +290,7 @@ static int ilog2_exact(int64_t x) {
 }
 
 // Chooses the slice geometry for n_v bath vectors of block size d_s.
-rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad) {
+rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad, int rec_ds) {
   if (precision != RDM_FP32 && precision != RDM_FP64) {
     set_error("precision must be RDM_FP32 or RDM_FP64");
     return RDM_EINVAL;
@@ -299,11 +299,11 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
   l.n_bits = h.n;
   l.n_bath_bits = h.n - h.ns;
   l.D = int64_t(1) << h.n;
-  l.DS = 1 << h.ns;
+  l.DS = rec_ds > 0 ? rec_ds : 1 << h.ns;  // block size of one recurrence
   l.precision = precision;
   l.elem = precision == RDM_FP32 ? 4 : 8;
   l.VW = precision == RDM_FP32 ? 4 : (l.DS == 4 ? 4 : 2);
-  int cols = l.DS * n_v;
+  int cols = (1 << h.ns) * n_v;
   int bcols;
   if (l.VW * l.elem == 16 && h.n >= kTileBits) {
     // tiled layout: narrow slices of kTiledLanes vectors per row
@@ -372,24 +372,43 @@ struct Arena {
 };
 
 struct Plan {
-  Layout L;
+  Layout L;   // the recurrences' layout (block size d_s, or 1 per column when single)
+  Layout Lg;  // the same memory grouped by d_s columns: the Gram view
+  bool single;                        // one block-size-1 recurrence per column
   int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
   bool gauss;                         // Gaussian bath vectors are generated once into a buffer
   bool store;                         // keep all k+1 Krylov blocks (no second pass)
   size_t tk_bytes;                    // K table of the tiled diagonal (0 if untiled)
 };
 
+// Float64 counts of the arrays whose size depends on the grouping: reduction partials
+// (4 slots), the E coefficients of a beta chunk and the Gram results of a chunk, each
+// large enough for the recurrences' layout and for the Gram view.
+struct PlanSizes {
+  size_t partials, e, gram;
+};
+static PlanSizes plan_sizes(const Plan& p) {
+  const Layout& L = p.L;
+  const Layout& G = p.Lg;
+  const size_t rec = (size_t)L.n_groups() * L.DS * L.DS, view = (size_t)G.n_groups() * G.DS * G.DS;
+  const size_t prec = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * L.DS * L.DS;
+  const size_t pview = (size_t)G.n_slices * G.gridx * G.groups_per_slice() * G.DS * G.DS;
+  return PlanSizes{std::max(prec, pview) * 4, (size_t)p.k * p.nbc * std::max(rec, view),
+                   (size_t)p.nbc * std::max(rec, view)};
+}
+
 static size_t plan_bytes(const Plan& p) {
   Arena a;  // dry run: only offsets
   const Layout& L = p.L;
   const size_t ng = L.n_groups(), nv = (size_t)L.DS * L.DS;
+  const PlanSizes z = plan_sizes(p);
   a.take<char>(L.block_bytes() * (p.store ? (size_t)p.k + 1 : 3));
   if (!p.store) a.take<char>(L.block_bytes() * p.nbc);
-  a.take<double>((size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv * 4);
+  a.take<double>(z.partials);
   a.take<double>((size_t)(p.k + 2) * ng * nv * 3);
   a.take<double>((size_t)p.k * ng * nv * 2);
-  a.take<double>((size_t)p.k * p.nbc * ng * nv);
-  a.take<double>((size_t)p.nbc * ng * nv);
+  a.take<double>(z.e);
+  a.take<double>(z.gram);
   a.take<double>((size_t)p.n_v_pad * 65);
   a.take<uint32_t>(4);
   a.take<char>(p.tk_bytes);
@@ -404,9 +423,23 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
     set_error("need n_beta >= 1, 1 <= n_v <= 4096, 1 <= k <= 512 (got %d, %d, %d)", n_beta, n_v, k);
     return RDM_EINVAL;
   }
+  if (o->recurrence != RDM_BLOCK && o->recurrence != RDM_SINGLE) {
+    set_error("recurrence must be RDM_BLOCK or RDM_SINGLE");
+    return RDM_EINVAL;
+  }
   Plan p{};
-  rdm_status st = plan_layout(hm, n_v, o->precision, &p.L, &p.n_v_pad);
+  p.single = o->recurrence == RDM_SINGLE && hm.ns > 0;
+  rdm_status st = plan_layout(hm, n_v, o->precision, &p.L, &p.n_v_pad, p.single ? 1 : -1);
   if (st != RDM_OK) return st;
+  p.Lg = p.L;
+  if (p.single) {
+    p.Lg.DS = 1 << hm.ns;
+    if (p.L.VW % p.Lg.DS != 0) {
+      set_error("RDM_SINGLE needs whole d_s-column groups per 16-byte vector (float32, or "
+                "float64 with d_s <= 2)");
+      return RDM_EINVAL;
+    }
+  }
   p.n_v = n_v;
   p.k = k;
   p.n_beta = n_beta;
@@ -426,7 +459,7 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
     Plan q = p;
     q.store = true;
     q.nbc = n_beta;
-    if (gram_stored_max_betas(q.L, k) >= 1 && plan_bytes(q) <= avail) {
+    if (gram_stored_max_betas(q.Lg, k) >= 1 && plan_bytes(q) <= avail) {
       *out = q;
       return RDM_OK;
     }
@@ -450,16 +483,19 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   return RDM_OK;
 }
 
-size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail) {
+size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail,
+                      rdm_status* status) {
   Plan p;
-  if (make_plan(h, n_beta, n_v, k, o, avail, &p) != RDM_OK) return 0;
+  const rdm_status st = make_plan(h, n_beta, n_v, k, o, avail, &p);
+  if (status) *status = st;
+  if (st != RDM_OK) return 0;
   return plan_bytes(p);
 }
 
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int passes, int nbc) {
+                          int passes, int nbc, int recurrence) {
   rdm_opts o{precision, dist, RDM_GRAM,
-             passes == RDM_PASSES_STORE ? RDM_PASSES_STORE : RDM_PASSES_RECOMPUTE, 0};
+             passes == RDM_PASSES_STORE ? RDM_PASSES_STORE : RDM_PASSES_RECOMPUTE, 0, recurrence};
   Plan p;
   if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
   if (!p.store) p.nbc = std::max(1, std::min(nbc, n_beta));
@@ -834,8 +870,12 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   Plan p;
   rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p);
   if (st != RDM_OK) return st;
-  const Layout& L = p.L;
+  const Layout& L = p.L;    // the recurrences (block size ds)
+  const Layout& Lg = p.Lg;  // the Gram view (groups of dso columns)
   const int ds = L.DS, nv = ds * ds, ng = L.n_groups();
+  const int dso = 1 << hm.ns, nvo = dso * dso, ngo = Lg.n_groups();
+  const int sub = p.single ? dso : 1;  // recurrences per bath vector
+  const int n_rec = n_v * sub;         // real recurrences
   const int64_t d_b = int64_t(1) << L.n_bath_bits;
   if (o->vec_dist == RDM_BASIS && o->first_vector + (int64_t)n_v > d_b) {
     set_error("RDM_BASIS needs first_vector + n_v <= d_b = %lld", (long long)d_b);
@@ -856,13 +896,15 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     for (int i = 0; i < nblk; ++i) blk[i] = base + (size_t)i * L.block_bytes();
   }
   char* psi = store ? nullptr : ar.take<char>(L.block_bytes() * p.nbc);
+  const PlanSizes psz = plan_sizes(p);
   const size_t pstride = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv;
-  double* partials = ar.take<double>(pstride * 4);
+  const size_t pstride_g = (size_t)Lg.n_slices * Lg.gridx * Lg.groups_per_slice() * nvo;
+  double* partials = ar.take<double>(psz.partials);
   double* coef = ar.take<double>((size_t)(k + 2) * ng * nv * 3);
   double* d_ta = ar.take<double>((size_t)k * ng * nv);
   double* d_tb = ar.take<double>((size_t)k * ng * nv);
-  double* d_e = ar.take<double>((size_t)k * p.nbc * ng * nv);
-  double* d_gram = ar.take<double>((size_t)p.nbc * ng * nv);
+  double* d_e = ar.take<double>(psz.e);
+  double* d_gram = ar.take<double>(psz.gram);
   double* d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
   uint32_t* d_flags = ar.take<uint32_t>(4);
   char* d_tk = ar.take<char>(p.tk_bytes);
@@ -913,7 +955,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   }
   auto init_block = [&](char* w) -> rdm_status {
     CK(timed(kKInit, blk_b, [&] {
-      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s);
+      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s, sub);
     }));
     return RDM_OK;
   };
@@ -937,7 +979,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     CK(timed(kKOrth1, blk_b * 3, [&] { return launch_orth(L, blk[cur], blk[nxt], CW(j), partials, s); }));
     CK(counted([&] {
       return launch_small_b(L, partials, MZ(j), d_tb + (size_t)(j - 1) * cstride, MZ(j + 1), CP(j + 1),
-                            thr_abs_sq, thr_rel_sq, n_v, d_flags, s);
+                            thr_abs_sq, thr_rel_sq, n_rec, d_flags, s);
     }));
     const int old_prev = prv;
     prv = cur;
@@ -964,43 +1006,49 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     return RDM_ENUMERIC;
   }
 
-  // ---- small dense step (host float64): f(T_l) E1 for every beta (eq. fT) with the
-  // per-vector shift t_min(l); E0 = min_l t_min(l) (Sec. 3.2), then rescaling.
+  // ---- small dense step (host float64): f(T_r) E1 for every beta (eq. fT) with the
+  // per-recurrence shift t_min(r); E0 = min_r t_min(r) (Sec. 3.2), then rescaling. A
+  // recurrence r is bath vector r (block) or column r = l dso + i (single).
   const int n = k * ds;
-  std::vector<double> cstore((size_t)n_v * n_beta * n * ds);
-  std::vector<double> tmin(n_v, 0.0);
-  std::vector<char> okv(n_v, 1);
+  std::vector<double> cstore((size_t)n_rec * n_beta * n * ds);
+  std::vector<double> tmin(n_rec, 0.0);
+  std::vector<char> okv(n_rec, 1);
   const auto host_t0 = std::chrono::steady_clock::now();
   double host_ms = 0.0;
   auto host_lap = [&]() {
     const auto t1 = std::chrono::steady_clock::now();
     return std::chrono::duration<double, std::milli>(t1 - host_t0).count();
   };
-  parallel_for(n_v, [&](int l) {
+  parallel_for(n_rec, [&](int r) {
     std::vector<double> t;
-    build_t(ds, k, ng, l, ta, tb, t);
-    okv[l] = tdense_fT(n, ds, t.data(), n_beta, betas, &tmin[l], &cstore[(size_t)l * n_beta * n * ds]);
+    build_t(ds, k, ng, r, ta, tb, t);
+    okv[r] = tdense_fT(n, ds, t.data(), n_beta, betas, &tmin[r], &cstore[(size_t)r * n_beta * n * ds]);
   });
   double e0 = INFINITY;
-  for (int l = 0; l < n_v; ++l) {
-    if (!okv[l]) {
-      set_error("eigensolver did not converge on T_%d", l);
+  for (int r = 0; r < n_rec; ++r) {
+    if (!okv[r]) {
+      set_error("eigensolver did not converge on T_%d", r);
       return RDM_ENUMERIC;
     }
-    e0 = std::min(e0, tmin[l]);
+    e0 = std::min(e0, tmin[r]);
   }
   host_ms += host_lap();
-  // c[beta][l] = exp(-beta (t_min(l) - E0)/2) * (the t_min(l)-shifted c)
-  auto coef_c = [&](int l, int bi, std::vector<double>& c) {
-    const double* src = &cstore[((size_t)l * n_beta + bi) * n * ds];
-    const double f = std::exp(-0.5 * betas[bi] * (tmin[l] - e0));
+  // c[beta][r] = exp(-beta (t_min(r) - E0)/2) * (the t_min(r)-shifted c)
+  auto coef_c = [&](int r, int bi, std::vector<double>& c) {
+    const double* src = &cstore[((size_t)r * n_beta + bi) * n * ds];
+    const double f = std::exp(-0.5 * betas[bi] * (tmin[r] - e0));
     c.resize((size_t)n * ds);
     for (size_t i = 0; i < c.size(); ++i) c[i] = f * src[i];
   };
-  std::vector<double> quad((size_t)n_beta * n_v * nv, 0.0), gram((size_t)n_beta * n_v * nv, 0.0);
-  const bool want_gram = true;
-  std::vector<double> hE((size_t)k * p.nbc * cstride);
-  std::vector<double> hg((size_t)p.nbc * cstride);
+  // Per bath vector and beta: quad = c^T c (its diagonal only for single recurrences)
+  // and E_{j,beta} = M_j c_{j,beta}; E goes to the recurrences' layout for pass 2 and
+  // to the Gram view (diagonal d_s x d_s blocks for single recurrences) for the
+  // stored-basis Gram.
+  const size_t cstride_g = (size_t)ngo * nvo;
+  const bool e_view = store;
+  std::vector<double> quad((size_t)n_beta * n_v * nvo, 0.0), gram((size_t)n_beta * n_v * nvo, 0.0);
+  std::vector<double> hE(psz.e);
+  std::vector<double> hg(psz.gram);
   for (int b0 = 0; b0 < n_beta; b0 += p.nbc) {
     const int nb = std::min(p.nbc, n_beta - b0);
     std::fill(hE.begin(), hE.end(), 0.0);
@@ -1008,42 +1056,57 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     parallel_for(n_v, [&](int l) {
       std::vector<double> c;
       for (int bi = 0; bi < nb; ++bi) {
-        coef_c(l, b0 + bi, c);
-        double* q = &quad[((size_t)(b0 + bi) * n_v + l) * nv];
-        for (int a = 0; a < ds; ++a)
-          for (int b = 0; b < ds; ++b) {
-            double sacc = 0.0;
-            for (int r = 0; r < n; ++r) sacc += c[(size_t)r * ds + a] * c[(size_t)r * ds + b];
-            q[a * ds + b] = sacc;
-          }
-        // E_{j,beta} = M_j c_{j,beta}
-        for (int j = 0; j < k; ++j) {
-          const double* M = &mz[(size_t)j * cstride + (size_t)l * nv];
-          double* Ej = &hE[(((size_t)j * p.nbc + bi) * ng + l) * nv];
+        double* q = &quad[((size_t)(b0 + bi) * n_v + l) * nvo];
+        if (!p.single) {
+          coef_c(l, b0 + bi, c);
           for (int a = 0; a < ds; ++a)
             for (int b = 0; b < ds; ++b) {
               double sacc = 0.0;
-              for (int m = 0; m < ds; ++m) sacc += M[a * ds + m] * c[(size_t)(j * ds + m) * ds + b];
-              Ej[a * ds + b] = sacc;
+              for (int r = 0; r < n; ++r) sacc += c[(size_t)r * ds + a] * c[(size_t)r * ds + b];
+              q[a * ds + b] = sacc;
             }
+          for (int j = 0; j < k; ++j) {
+            const double* M = &mz[(size_t)j * cstride + (size_t)l * nv];
+            double* Ej = &hE[(((size_t)j * p.nbc + bi) * ng + l) * nv];
+            for (int a = 0; a < ds; ++a)
+              for (int b = 0; b < ds; ++b) {
+                double sacc = 0.0;
+                for (int m = 0; m < ds; ++m) sacc += M[a * ds + m] * c[(size_t)(j * ds + m) * ds + b];
+                Ej[a * ds + b] = sacc;
+              }
+          }
+          continue;
+        }
+        for (int i = 0; i < dso; ++i) {  // single recurrences: column r = l dso + i
+          const int r = l * dso + i;
+          coef_c(r, b0 + bi, c);
+          double sacc = 0.0;
+          for (int m = 0; m < n; ++m) sacc += c[m] * c[m];
+          q[i * dso + i] = sacc;
+          for (int j = 0; j < k; ++j) {
+            const double e = mz[(size_t)j * cstride + r] * c[j];
+            if (e_view)
+              hE[(((size_t)j * p.nbc + bi) * ngo + l) * nvo + i * dso + i] = e;
+            else
+              hE[((size_t)j * p.nbc + bi) * ng + r] = e;
+          }
         }
       }
     });
     host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - coef_t0).count();
-    if (!want_gram) continue;
     CK(cudaMemcpyAsync(d_e, hE.data(), hE.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     h2d += hE.size() * sizeof(double);
     if (store) {
-      // ---- psi = sum_j W_j E_j over the stored blocks, Gram fused.
-      const int gmax = gram_stored_max_betas(L, k);
+      // ---- psi = sum_j W_j E_j over the stored blocks, Gram fused (Gram view).
+      const int gmax = gram_stored_max_betas(Lg, k);
       for (int q = 0; q < nb; q += gmax) {
         const int nq = std::min(gmax, nb - q);
         CK(timed(kKGram, blk_b * k, [&] {
-          return launch_gram_stored(L, blk[0], k, d_e, p.nbc, q, nq, partials, pstride, s);
+          return launch_gram_stored(Lg, blk[0], k, d_e, p.nbc, q, nq, partials, pstride_g, s);
         }));
         for (int i = 0; i < nq; ++i)
           CK(counted([&] {
-            return launch_reduce_gram(L, partials + (size_t)i * pstride, d_gram + (size_t)(q + i) * cstride, s);
+            return launch_reduce_gram(Lg, partials + (size_t)i * pstride_g, d_gram + (size_t)(q + i) * cstride_g, s);
           }));
       }
     } else {
@@ -1071,18 +1134,18 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
       nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
     }
     for (int bi = 0; bi < nb; ++bi) {
-      CK(timed(kKGram, blk_b, [&] { return launch_final_gram(L, psi + (size_t)bi * L.block_bytes(), partials, s); }));
-      CK(counted([&] { return launch_reduce_gram(L, partials, d_gram + (size_t)bi * cstride, s); }));
+      CK(timed(kKGram, blk_b, [&] { return launch_final_gram(Lg, psi + (size_t)bi * L.block_bytes(), partials, s); }));
+      CK(counted([&] { return launch_reduce_gram(Lg, partials, d_gram + (size_t)bi * cstride_g, s); }));
     }
     }
-    CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cstride * sizeof(double),
+    CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cstride_g * sizeof(double),
                        cudaMemcpyDeviceToHost, s));
-    d2h += (size_t)nb * cstride * sizeof(double);
+    d2h += (size_t)nb * cstride_g * sizeof(double);
     CK(cudaStreamSynchronize(s));
     for (int bi = 0; bi < nb; ++bi)
       for (int l = 0; l < n_v; ++l)
-        for (int v = 0; v < nv; ++v)
-          gram[((size_t)(b0 + bi) * n_v + l) * nv + v] = hg[((size_t)bi * ng + l) * nv + v];
+        for (int v = 0; v < nvo; ++v)
+          gram[((size_t)(b0 + bi) * n_v + l) * nvo + v] = hg[((size_t)bi * ngo + l) * nvo + v];
   }
   CK(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1099,15 +1162,15 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {
     bool ok = true;
     for (int bi = 0; bi < n_beta; ++bi) {
-      std::vector<double> sum(nv, 0.0);
+      std::vector<double> sum(nvo, 0.0);
       for (int l = 0; l < n_v; ++l)
-        for (int v = 0; v < nv; ++v) sum[v] += g[((size_t)bi * n_v + l) * nv + v];
+        for (int v = 0; v < nvo; ++v) sum[v] += g[((size_t)bi * n_v + l) * nvo + v];
       double tr = 0.0;
-      for (int i = 0; i < ds; ++i) tr += sum[i * ds + i];
+      for (int i = 0; i < dso; ++i) tr += sum[i * dso + i];
       ok = ok && std::isfinite(tr) && tr > 0;
-      for (int i = 0; i < ds; ++i)
-        for (int jj = 0; jj < ds; ++jj)
-          rho[(size_t)bi * nv + i * ds + jj] = 0.5 * (sum[i * ds + jj] + sum[jj * ds + i]) / tr;
+      for (int i = 0; i < dso; ++i)
+        for (int jj = 0; jj < dso; ++jj)
+          rho[(size_t)bi * nvo + i * dso + jj] = 0.5 * (sum[i * dso + jj] + sum[jj * dso + i]) / tr;
       if (lnz) lnz[bi] = std::log((double)d_b * tr / n_v) - betas[bi] * e0;
     }
     return ok;
@@ -1120,14 +1183,22 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   if (out->t_a || out->t_b)
     for (int l = 0; l < n_v; ++l)
       for (int j = 0; j < k; ++j)
-        for (int v = 0; v < nv; ++v) {
-          if (out->t_a) out->t_a[((size_t)l * k + j) * nv + v] = ta[((size_t)j * ng + l) * nv + v];
-          if (out->t_b) out->t_b[((size_t)l * k + j) * nv + v] = tb[((size_t)j * ng + l) * nv + v];
+        for (int v = 0; v < nvo; ++v) {
+          double a = 0.0, b = 0.0;
+          if (!p.single) {
+            a = ta[((size_t)j * ng + l) * nv + v];
+            b = tb[((size_t)j * ng + l) * nv + v];
+          } else if (v % (dso + 1) == 0) {  // diagonal: column l dso + v / dso
+            a = ta[(size_t)j * ng + (size_t)l * dso + v / dso];
+            b = tb[(size_t)j * ng + (size_t)l * dso + v / dso];
+          }
+          if (out->t_a) out->t_a[((size_t)l * k + j) * nvo + v] = a;
+          if (out->t_b) out->t_b[((size_t)l * k + j) * nvo + v] = b;
         }
   out->e0 = e0;
   out->h2d_bytes = h2d;
   out->d2h_bytes = d2h;
-  out->flags = (flags[0] & RDM_FLAG_DEFLATED) | (p.n_v_pad != n_v ? RDM_FLAG_PADDED : 0u);
+  out->flags = (flags[0] & RDM_FLAG_DEFLATED) | (p.n_v_pad != n_rec ? RDM_FLAG_PADDED : 0u);
   if (!ok) {
     set_error("the estimated tr(sum_l G_l) is not a positive finite number (underflow or breakdown)");
     return RDM_ENUMERIC;
@@ -1179,8 +1250,9 @@ extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t usable = (size_t)(0.85 * (double)(free_b + ctx->own_bytes));
-  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable);
-  if (need == 0) return RDM_ENOMEM;  // make_plan set the message
+  rdm_status pst = RDM_OK;
+  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst);
+  if (need == 0) return pst != RDM_OK ? pst : RDM_ENOMEM;  // make_plan set the message
   if (ctx->own_bytes < need) {
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->own_ws) CK(cudaFree(ctx->own_ws));

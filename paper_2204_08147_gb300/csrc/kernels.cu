@@ -178,7 +178,7 @@ __global__ void k_gauss_finish(int n_v, int gx, const double* part, double* inv_
 template <typename T, int DS, int VW>
 __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uint64_t seed,
                                                          int64_t l0, int nvr, const double* inv_norm,
-                                                         const T* vbuf, T* W) {
+                                                         const T* vbuf, T* W, int sub) {
   constexpr int NG = VW / DS;
   const int tpr = L.TPR, rpb = kThreads / tpr;
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
@@ -193,7 +193,9 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
     T v[VW];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
-      const int l = g0 + g;
+      // group g0 + g: bath vector l, system index ic of its column when the groups are
+      // single columns of sub-column bath vectors (per-column recurrences), else 0
+      const int l = (g0 + g) / sub, ic = (g0 + g) % sub;
       double val = 0.0;
       if (l < nvr) {
         const uint64_t lg = (uint64_t)(l0 + l);  // index in the seeded sequence
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
         }
       }
 #pragma unroll
-      for (int a = 0; a < DS; ++a) v[g * DS + a] = (a == i) ? (T)val : (T)0;
+      for (int a = 0; a < DS; ++a) v[g * DS + a] = (a + ic == i) ? (T)val : (T)0;
     }
     VecIO<T, VW>::st(base + (size_t)s * L.Bs, v);
   }
@@ -1657,10 +1659,11 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, 
 }
 
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
-                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st) {
+                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st,
+                              int sub) {
   RDM_DISPATCH(L, (k_init_block<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
                       L, dist, seed, l0, n_v_real, inv_norm, reinterpret_cast<const T*>(vbuf),
-                      reinterpret_cast<T*>(W))));
+                      reinterpret_cast<T*>(W), sub)));
   return cudaGetLastError();
 }
 

@@ -78,7 +78,9 @@ namespace rdm {
 
 void set_error(const char* fmt, ...);
 rdm_status compile_model(const rdm_model* m, HostModel* out);
-rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad);
+// rec_ds: block size of one recurrence (-1: d_s; 1: one recurrence per column)
+rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad,
+                       int rec_ds = -1);
 rdm_status check_estimate_args(const rdm_ham* ham, const double* betas, int n_beta,
                                const rdm_opts* opts, const rdm_result* out);
 // Runs the whole estimator on stream s, carving its scratch from ws/ws_bytes.
@@ -102,8 +104,9 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 // Bytes the estimator would use given `avail` bytes (0 if the sizes are invalid).
-size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail);
+size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail,
+                      rdm_status* status = nullptr);
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int passes, int nbc);
+                          int passes, int nbc, int recurrence = 0);
 
 }  // namespace rdm

@@ -86,9 +86,12 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, 
 
 // W = [I_s (x) v_l] for l < n_v_real, zero columns beyond; vector l of the block is
 // vector l0 + l of the seeded sequence. Gaussian values come from inv_norm
-// (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T).
+// (computed on the fly) or, if inv_norm is NULL, from vbuf[l][b] (T). With sub > 1 the
+// layout's groups are single columns (L.DS = 1) and column c = l sub + i holds
+// e_i (x) v_l (the per-column recurrences).
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
-                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st);
+                              const double* inv_norm, const void* vbuf, void* W, cudaStream_t st,
+                              int sub = 1);
 // vbuf[l][b] = normalised Gaussian bath vector l0 + l (T = the layout's precision),
 // from graw (the norm pass's raw values) when given, else regenerated.
 cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,

@@ -222,10 +222,10 @@ extern "C" rdm_status rdm_submit(rdm_ctx* ctx, const rdm_model* model, const dou
   // Footprint: all betas in one pass-2 sweep if that takes at most a quarter of
   // the budget, else halve the sweep until it does (results do not depend on it).
   int nbc = n_beta;
-  size_t fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc);
+  size_t fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc, opts->recurrence);
   while (nbc > 1 && fp > S->budget / 4) {
     nbc = (nbc + 1) / 2;
-    fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc);
+    fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc, opts->recurrence);
   }
   if (fp == 0) return RDM_EINVAL;  // make_plan set the error
   if (fp > S->budget) {

@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EBUSY, ENOTPD, ENOTFOUND = 0, -1,
 FP64, FP32 = 0, 1
 RADEMACHER, GAUSS, BASIS = 0, 1, 2
 GRAM, QUADRATURE = 0, 1
+BLOCK, SINGLE = 0, 1
 PASSES_AUTO, PASSES_STORE, PASSES_RECOMPUTE = 0, 1, 2
 FLAG_DEFLATED, FLAG_PADDED = 1, 2
 
@@ -41,7 +42,7 @@ class Model(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("vec_dist", C.c_int), ("form", C.c_int),
-                ("passes", C.c_int), ("first_vector", C.c_int64)]
+                ("passes", C.c_int), ("first_vector", C.c_int64), ("recurrence", C.c_int)]
 
 
 class Result(C.Structure):
@@ -140,8 +141,12 @@ _PASSES = {"auto": PASSES_AUTO, "store": PASSES_STORE, "recompute": PASSES_RECOM
            PASSES_AUTO: PASSES_AUTO, PASSES_STORE: PASSES_STORE, PASSES_RECOMPUTE: PASSES_RECOMPUTE}
 
 
-def _opts(precision, dist, form, passes="auto", first_vector=0) -> Opts:
-    return Opts(_PREC[precision], _DIST[dist], _FORM[form], _PASSES[passes], int(first_vector))
+_REC = {"block": BLOCK, "single": SINGLE, BLOCK: BLOCK, SINGLE: SINGLE}
+
+
+def _opts(precision, dist, form, passes="auto", first_vector=0, recurrence="block") -> Opts:
+    return Opts(_PREC[precision], _DIST[dist], _FORM[form], _PASSES[passes], int(first_vector),
+                _REC[recurrence])
 
 
 class _ResultArrays:
@@ -326,10 +331,12 @@ class Hamiltonian:
         return n.value
 
     def estimate(self, betas, n_v, k, seed, precision="fp32", dist="rademacher", form="gram",
-                 full=False, passes="auto", first_vector=0) -> dict:
+                 full=False, passes="auto", first_vector=0, recurrence="block") -> dict:
+        """recurrence="block": block Lanczos of block size d_s per bath vector (Algorithm 1);
+        "single": one block-size-1 Lanczos per column e_i (x) v_l (Sec. 4.2)."""
         b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
         res = _ResultArrays(len(b), n_v, k, self.d_s, full)
-        o = _opts(precision, dist, form, passes, first_vector)
+        o = _opts(precision, dist, form, passes, first_vector, recurrence)
         _check(_lib.rdm_estimate(self.h, _ptr(b), len(b), int(n_v), int(k), int(seed) & (2 ** 64 - 1),
                                  C.byref(o), C.byref(res.struct)), "rdm_estimate")
         return res.as_dict(o.form)

@@ -500,3 +500,73 @@ def test_c5_shape_two_pass_fp32_vs_oracle(ctx, lib):
     ref = lanczos.Estimator(spec).run([2.0], 4, 50, 20220421, "rademacher")
     np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32, rtol=0)
     np.testing.assert_allclose(out["lnZ"], ref["lnZ"], rtol=1e-5, atol=1e-4)
+
+
+# ---------------------------------------------------------------- per-column (block size 1) recurrences
+
+@pytest.mark.parametrize("passes", ["store", "recompute"])
+def test_single_recurrence_matches_oracle_fp64(ctx, lib, passes):
+    """recurrence="single": one Lanczos recurrence per column e_i (x) v_l (Sec. 4.2), Gram
+    cross terms psi_i^T psi_j, against the oracle's per-column run on the same vectors."""
+    spec = W.random_model(10, 1, 31)
+    betas = [0.5, 2.0]
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate(betas, 5, 20, 8, precision="fp64", dist="gauss", full=True, passes=passes,
+                       recurrence="single")
+    ref = lanczos.Estimator(spec).run(betas, 5, 20, 8, "gauss", block=False)
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], ref["lnZ"], atol=1e-9, rtol=0)
+    np.testing.assert_allclose(out["gram_l"], ref["gram_l"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(out["quad_l"], ref["quad_l"], rtol=1e-9, atol=1e-12)
+    assert abs(out["e0"] - ref["e0"]) < 1e-10
+
+
+def test_single_recurrence_store_and_recompute_bit_identical(ctx, lib):
+    spec = W.long_range_tfim(12, 2, 1.5, 0.6)
+    ham = lib.Hamiltonian(ctx, spec)
+    a = ham.estimate([0.5, 1.5], 8, 25, 3, precision="fp32", dist="gauss", full=True, passes="store",
+                     recurrence="single")
+    b = ham.estimate([0.5, 1.5], 8, 25, 3, precision="fp32", dist="gauss", full=True, passes="recompute",
+                     recurrence="single")
+    for key in ("rho", "lnZ", "gram_l", "quad_l", "t_a", "t_b"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_single_recurrence_fp32_tiled_vs_oracle(ctx, lib):
+    """d_s = 4 on the tiled SpMM with block size 1: 32 columns of 8 bath vectors."""
+    spec = W.long_range_tfim(12, 2, 1.5, 1.1)
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate([1.0], 8, 30, 20220418, precision="fp32", dist="gauss", recurrence="single")
+    ref = lanczos.Estimator(spec).run([1.0], 8, 30, 20220418, "gauss", block=False)
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=TOL32)
+    assert abs(out["lnZ"][0] - ref["lnZ"][0]) < 1e-3
+
+
+def test_single_recurrence_exhaustive_is_exact(ctx, lib):
+    spec = W.random_model(7, 1, 32)
+    betas = [0.3, 2.5]
+    ham = lib.Hamiltonian(ctx, spec)
+    out = ham.estimate(betas, spec.d_b, spec.dim + 2, 0, precision="fp64", dist="basis", recurrence="single")
+    rho, lnz = exact.exact_rho(spec, betas)
+    np.testing.assert_allclose(out["rho"], rho, atol=TOL64, rtol=0)
+    np.testing.assert_allclose(out["lnZ"], lnz, atol=1e-9, rtol=0)
+
+
+def test_single_recurrence_rejects_fp64_with_four_system_states(ctx, lib):
+    ham = lib.Hamiltonian(ctx, W.random_model(8, 2, 33))
+    with pytest.raises(lib.RdmError) as e:
+        ham.estimate([1.0], 2, 5, 1, precision="fp64", recurrence="single")
+    assert e.value.status == lib.EINVAL
+
+
+def test_block_recurrence_more_accurate_than_single(ctx, lib):
+    """Sec. 4.2's remark on the GPU path: at equal k the block recurrence is closer to
+    the exact-function estimator (same vectors) than per-column recurrences."""
+    spec = W.random_model(10, 2, 5)
+    h = spin_ops.dense_hamiltonian(spec)
+    rho2, _ = lanczos.exact_function_estimator(spec, h, [2.0], 6, 3, "gauss")
+    ham = lib.Hamiltonian(ctx, spec)
+    for k in (4, 6, 8):
+        b = ham.estimate([2.0], 6, k, 3, precision="fp32", dist="gauss")
+        s = ham.estimate([2.0], 6, k, 3, precision="fp32", dist="gauss", recurrence="single")
+        assert np.abs(b["rho"] - rho2).max() < np.abs(s["rho"] - rho2).max()
