@@ -346,40 +346,54 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
   double tmin = d[0];
   for (int i = 1; i < n; ++i) tmin = std::min(tmin, d[i]);
   *t_min = tmin;
-  // Per beta: z = exp(-beta (theta - t_min)/2) * y, then U z (rotations in reverse,
-  // untransposed), then Q z (reflectors in reverse).
-  std::vector<double> zb((size_t)n * p);
-  for (int b = 0; b < n_beta; ++b) {
-    for (int m = 0; m < n; ++m) {
+  // For every beta: z_beta = exp(-beta (theta - t_min)/2) * y, then U z (rotations in
+  // reverse, untransposed), then Q z. All betas go through the rotations together: row m
+  // of Z holds the p columns of every beta (width p * n_beta), so each rotation is one
+  // contiguous loop; every element sees the same operations as one beta alone.
+  const int w = p * n_beta;
+  std::vector<double> zb((size_t)n * w);
+  for (int m = 0; m < n; ++m)
+    for (int b = 0; b < n_beta; ++b) {
       const double f = std::exp(-0.5 * betas[b] * (d[m] - tmin));
-      for (int q = 0; q < p; ++q) zb[(size_t)m * p + q] = f * y[(size_t)m * p + q];
+      for (int q = 0; q < p; ++q) zb[(size_t)m * w + b * p + q] = f * y[(size_t)m * p + q];
     }
-    for (size_t r = rots.size(); r-- > 0;) {
-      const Rot& g = rots[r];
-      double* za = &zb[(size_t)g.k * p];
-      double* zc = &zb[(size_t)(g.k + 1) * p];
-      for (int q = 0; q < p; ++q) {
-        const double u = za[q], w = zc[q];
-        za[q] = g.c * u + g.s * w;
-        zc[q] = -g.s * u + g.c * w;
-      }
+  for (size_t r = rots.size(); r-- > 0;) {
+    const Rot& g = rots[r];
+    double* za = &zb[(size_t)g.k * w];
+    double* zc = &zb[(size_t)(g.k + 1) * w];
+    for (int q = 0; q < w; ++q) {
+      const double u = za[q], v = zc[q];
+      za[q] = g.c * u + g.s * v;
+      zc[q] = -g.s * u + g.c * v;
     }
-    if (banded) {  // Q z = R_1^T ... R_m^T z: transposed rotations in reverse order
-      for (size_t r = brots.size(); r-- > 0;) {
-        const BandRot& g = brots[r];
-        double* za = &zb[(size_t)(g.q - 1) * p];
-        double* zc = &zb[(size_t)g.q * p];
-        for (int q = 0; q < p; ++q) {
-          const double u = za[q], w = zc[q];
-          za[q] = g.c * u - g.s * w;
-          zc[q] = g.s * u + g.c * w;
-        }
-      }
-    } else {
-      for (int k = n - 3; k >= 0; --k) apply_reflector(k, zb);
-    }
-    std::copy(zb.begin(), zb.end(), c_out + (size_t)b * n * p);
   }
+  if (banded) {  // Q z = R_1^T ... R_m^T z: transposed rotations in reverse order
+    for (size_t r = brots.size(); r-- > 0;) {
+      const BandRot& g = brots[r];
+      double* za = &zb[(size_t)(g.q - 1) * w];
+      double* zc = &zb[(size_t)g.q * w];
+      for (int q = 0; q < w; ++q) {
+        const double u = za[q], v = zc[q];
+        za[q] = g.c * u - g.s * v;
+        zc[q] = g.s * u + g.c * v;
+      }
+    }
+  }
+  if (!banded) {
+    for (int k = n - 3; k >= 0; --k) {
+      if (hb[k] == 0.0) continue;
+      const double* v = &hv[(size_t)k * n];
+      for (int c = 0; c < w; ++c) {
+        double dot = 0.0;
+        for (int i = k + 1; i < n; ++i) dot += v[i] * zb[(size_t)i * w + c];
+        dot *= hb[k];
+        for (int i = k + 1; i < n; ++i) zb[(size_t)i * w + c] -= dot * v[i];
+      }
+    }
+  }
+  for (int b = 0; b < n_beta; ++b)
+    for (int m = 0; m < n; ++m)
+      for (int q = 0; q < p; ++q) c_out[((size_t)b * n + m) * p + q] = zb[(size_t)m * w + b * p + q];
   return true;
 }
 
