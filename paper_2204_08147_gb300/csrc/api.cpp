@@ -1049,9 +1049,32 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   std::vector<double> quad((size_t)n_beta * n_v * nvo, 0.0), gram((size_t)n_beta * n_v * nvo, 0.0);
   std::vector<double> hE(psz.e);
   std::vector<double> hg(psz.gram);
+  // Trailing Krylov steps whose coefficient blocks are below the working precision
+  // relative to the whole coefficient vector (|c_j| <= 1e-3 eps |c| for every vector, at
+  // one beta) cannot change psi = sum_j Q_j c_j at that precision. Their E_j are set to
+  // zero for that beta (so the result does not depend on how betas are chunked), and the
+  // Gram pass (stored basis) or the recurrence of pass 2 stops after the last step any
+  // beta of the chunk needs.
+  const double tau = 1e-3 * (o->precision == RDM_FP32 ? 1.1920928955078125e-07 : 2.220446049250313e-16);
+  auto last_significant = [&](const std::vector<double>& c, int width) -> int {
+    double tot = 0.0;
+    for (double x : c) tot += x * x;
+    int last = 0;
+    for (int j = 0; j < k; ++j) {
+      double sj = 0.0;
+      for (int t = 0; t < ds * width; ++t) {
+        const double x = c[(size_t)j * ds * width + t];
+        sj += x * x;
+      }
+      if (sj > tau * tau * tot) last = j + 1;
+    }
+    return last;
+  };
+  std::vector<int> jlast((size_t)p.nbc * n_v, 1);
   for (int b0 = 0; b0 < n_beta; b0 += p.nbc) {
     const int nb = std::min(p.nbc, n_beta - b0);
     std::fill(hE.begin(), hE.end(), 0.0);
+    std::fill(jlast.begin(), jlast.end(), 1);
     const auto coef_t0 = std::chrono::steady_clock::now();
     parallel_for(n_v, [&](int l) {
       std::vector<double> c;
@@ -1059,6 +1082,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
         double* q = &quad[((size_t)(b0 + bi) * n_v + l) * nvo];
         if (!p.single) {
           coef_c(l, b0 + bi, c);
+          jlast[(size_t)bi * n_v + l] = last_significant(c, ds);
           for (int a = 0; a < ds; ++a)
             for (int b = 0; b < ds; ++b) {
               double sacc = 0.0;
@@ -1080,6 +1104,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
         for (int i = 0; i < dso; ++i) {  // single recurrences: column r = l dso + i
           const int r = l * dso + i;
           coef_c(r, b0 + bi, c);
+          int& jl = jlast[(size_t)bi * n_v + l];
+          jl = std::max(i == 0 ? 1 : jl, last_significant(c, 1));
           double sacc = 0.0;
           for (int m = 0; m < n; ++m) sacc += c[m] * c[m];
           q[i * dso + i] = sacc;
@@ -1094,6 +1120,15 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
       }
     });
     host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - coef_t0).count();
+    int k_eff = 1;
+    for (int bi = 0; bi < nb; ++bi) {
+      const int kb = *std::max_element(jlast.begin() + (size_t)bi * n_v, jlast.begin() + (size_t)(bi + 1) * n_v);
+      k_eff = std::max(k_eff, kb);
+      for (int j = kb; j < k; ++j) {  // E_j of this beta beyond its last needed step
+        double* e0p = &hE[((size_t)j * p.nbc + bi) * (e_view ? ngo * nvo : ng * nv)];
+        std::fill(e0p, e0p + (size_t)(e_view ? ngo * nvo : ng * nv), 0.0);
+      }
+    }
     CK(cudaMemcpyAsync(d_e, hE.data(), hE.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     h2d += hE.size() * sizeof(double);
     if (store) {
@@ -1101,8 +1136,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
       const int gmax = gram_stored_max_betas(Lg, k);
       for (int q = 0; q < nb; q += gmax) {
         const int nq = std::min(gmax, nb - q);
-        CK(timed(kKGram, blk_b * k, [&] {
-          return launch_gram_stored(Lg, blk[0], k, d_e, p.nbc, q, nq, partials, pstride_g, s);
+        CK(timed(kKGram, blk_b * k_eff, [&] {
+          return launch_gram_stored(Lg, blk[0], k_eff, d_e, p.nbc, q, nq, partials, pstride_g, s);
         }));
         for (int i = 0; i < nq; ++i)
           CK(counted([&] {
@@ -1117,7 +1152,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     cur = 0;
     prv = -1;
     nxt = 1;
-    for (int j = 1; j < k; ++j) {
+    for (int j = 1; j < k_eff; ++j) {
       sa.w = blk[cur];
       sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
       sa.z = blk[nxt];
