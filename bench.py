@@ -51,6 +51,7 @@ def _args():
                    help="bath vectors per solve (32 = the benchmark; fewer only for profiling)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sub-benchmark")
     p.add_argument("--serving-requests", type=int, default=32)
+    p.add_argument("--no-small", action="store_true", help="skip the small-chain latency sub-benchmark")
     return p.parse_args()
 
 
@@ -307,6 +308,9 @@ def run_ours(a):
     serving = None
     if rank == 0 and not a.no_serving:
         serving = serving_bench(rdm, ctx, a.serving_requests)
+    small = None
+    if rank == 0 and not a.no_small:
+        small = small_chain_bench(rdm, ctx)
 
     if rank != 0:
         if dist:
@@ -352,6 +356,7 @@ def run_ours(a):
         "plain_fp64": plain,
         "precision_fp32_vs_fp64": precision,
         "serving": serving,
+        "small_chain": small,
     }
     if cpu_sample is not None:
         line["cpu_baseline"] = {"value": oracle_solves_per_s(cpu_sample), "unit": "solves/s", "cores": 1,
@@ -400,6 +405,40 @@ def serving_bench(rdm, ctx, n_req: int) -> dict:
                            "p99": 1000 * float(np.percentile(lat, 99))},
             "stream": "XXZ/LR-TFIM mix, N 12..18, N_s 1-2, 8-64 betas, n_v 8-64, k 30-100, float32",
             "max_inflight": 4, "budget_gib": budget >> 30}
+
+
+def small_chain_bench(rdm, ctx, n_solves: int = 50) -> dict:
+    """Latency of one small solve (periodic XXZ chain N=10, N_s=1, n_v=16 Rademacher,
+    k=40, 3 betas, float64: the whole problem is L2-resident, so launch and host
+    latency set the time). Each solve is timed on the host around the blocking call."""
+    c = W.config_c1()
+    ham = rdm.Hamiltonian(ctx, c["spec"])
+
+    def one():
+        return ham.estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64", dist=c["dist"])
+    for _ in range(3):
+        one()
+    ctx.synchronize()
+    lat = []
+    for _ in range(n_solves):
+        t0 = time.perf_counter()
+        one()
+        lat.append(time.perf_counter() - t0)
+    # launch count and host share from separately profiled solves (the per-kernel
+    # events would add to the latency above)
+    n_prof = 10
+    ctx.profile(True)
+    for _ in range(n_prof):
+        one()
+    stats = ctx.profile_stats()
+    ctx.profile(False)
+    host = stats.pop("host_small_dense", None)
+    ham.close()
+    return {"workload": "xxz_chain_N10_Ns1_nv16_k40_3beta_fp64", "solves": n_solves,
+            "us_per_solve_p50": 1e6 * float(np.percentile(lat, 50)),
+            "us_per_solve_p99": 1e6 * float(np.percentile(lat, 99)),
+            "launches_per_solve": sum(s["launches"] for s in stats.values()) / n_prof,
+            "host_small_dense_us_per_solve": 1e3 * host["ms"] / n_prof if host else None}
 
 
 def spmm_source_hash() -> str:

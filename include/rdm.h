@@ -165,6 +165,16 @@ rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v, int k,
 /* Waits for all device work issued on the context's stream. */
 rdm_status rdm_synchronize(rdm_ctx* ctx);
 
+/* Launch mode of rdm_estimate's first pass (Algorithm 1's k steps, four kernels per
+ * step). With enable != 0 (the default) a Hamiltonian handle records that launch
+ * sequence as a CUDA graph the second time it runs one configuration (same
+ * workspace, layout, k, precision and options) and replays the graph on later calls;
+ * 0 launches every kernel directly. The kernels, their arguments and their order are
+ * the same either way, so results are bit-identical. Graphs are not used while
+ * rdm_profile is recording (each launch is timed on its own) nor by the serving
+ * loop. The paper has no counterpart: this is launch overhead only. */
+rdm_status rdm_set_graphs(rdm_ctx* ctx, int enable);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rdm_last_error(void);
 

@@ -11,6 +11,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <condition_variable>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -583,6 +586,7 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   if (st != RDM_OK) return st;
   std::unique_ptr<rdm_ham> h(new rdm_ham());
   h->ctx = ctx;
+  h->device = ctx->device;
   h->model = std::move(hm);
   CK(cudaSetDevice(ctx->device));
   TermImage img;
@@ -664,12 +668,24 @@ extern "C" rdm_status rdm_system_hamiltonian(const rdm_model* model, double* hs_
   return RDM_OK;
 }
 
+void rdm::Pass1Graph::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  key.clear();
+}
+
+// Touches only the handle's own resources (not its context, which a caller may have
+// destroyed first). cudaFree waits for the device, so no launch of the recorded graph
+// is still running when it is destroyed.
 extern "C" void rdm_destroy_hamiltonian(rdm_ham* ham) {
   if (!ham) return;
-  cudaSetDevice(ham->ctx->device);
+  cudaSetDevice(ham->device);
   if (ham->d_terms) cudaFree(ham->d_terms);
   for (void* p : ham->d_apply_aux)
     if (p) cudaFree(p);
+  ham->graph.reset();
+  if (ham->graph.capture) cudaStreamDestroy(ham->graph.capture);
+  ham->graph.capture = nullptr;
   delete ham;
 }
 
@@ -846,21 +862,99 @@ static int host_threads() {
   return n;
 }
 
+// Persistent host worker threads for the small dense step (started on first use, one
+// fewer than the usable cores: the calling thread works too). Several callers (the
+// serving loop's workers) may run jobs at once; idle workers help the oldest job.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool(host_threads() - 1);
+    return pool;
+  }
+  // f(0) .. f(n-1), each exactly once, spread over the workers and the caller.
+  void run(int n, const std::function<void(int)>& f) {
+    if (n <= 0) return;
+    if (th_.empty() || n == 1) {
+      for (int i = 0; i < n; ++i) f(i);
+      return;
+    }
+    Job j;
+    j.f = &f;
+    j.n = n;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      jobs_.push_back(&j);
+    }
+    cv_.notify_all();
+    work(j);
+    std::unique_lock<std::mutex> lk(mu_);
+    drop(&j);
+    done_.wait(lk, [&] { return j.done == j.n && j.refs == 0; });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+
+ private:
+  struct Job {
+    const std::function<void(int)>* f = nullptr;
+    int n = 0;
+    std::atomic<int> next{0};
+    int done = 0;  // guarded by mu_
+    int refs = 0;  // workers inside work(); guarded by mu_
+  };
+  explicit HostPool(int workers) {
+    for (int t = 0; t < workers; ++t) th_.emplace_back([this] { loop(); });
+  }
+  void work(Job& j) {
+    int mine = 0;
+    for (int i; (i = j.next.fetch_add(1)) < j.n; ++mine) (*j.f)(i);
+    if (mine) {
+      std::lock_guard<std::mutex> lk(mu_);
+      j.done += mine;
+    }
+  }
+  void drop(Job* j) {  // with mu_ held
+    for (auto it = jobs_.begin(); it != jobs_.end(); ++it)
+      if (*it == j) {
+        jobs_.erase(it);
+        return;
+      }
+  }
+  void loop() {
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return stop_ || !jobs_.empty(); });
+      if (stop_) return;
+      Job* j = jobs_.front();
+      if (j->next.load() >= j->n) {  // every index taken: nothing left to help with
+        drop(j);
+        continue;
+      }
+      ++j->refs;
+      lk.unlock();
+      work(*j);
+      lk.lock();
+      if (--j->refs == 0) done_.notify_all();
+      else if (j->done == j->n) done_.notify_all();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  std::deque<Job*> jobs_;
+  std::vector<std::thread> th_;
+  bool stop_ = false;
+};
+
 template <typename F>
 static void parallel_for(int n, F&& f) {
-  int nt = host_threads();
-  nt = std::max(1, std::min(nt, n));
-  if (nt == 1) {
-    for (int i = 0; i < n; ++i) f(i);
-    return;
-  }
-  std::atomic<int> next(0);
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t)
-    th.emplace_back([&]() {
-      for (int i; (i = next.fetch_add(1)) < n;) f(i);
-    });
-  for (auto& x : th) x.join();
+  const std::function<void(int)> fn = std::forward<F>(f);
+  HostPool::get().run(n, fn);
 }
 
 rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
@@ -965,30 +1059,86 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   if (st != RDM_OK) return st;
   CK(counted([&] { return launch_coef_init(L, StepCoefs{MZ(1), CP(1), nullptr}, s); }));
   int cur = 0, prv = -1, nxt = 1;
-  for (int j = 1; j <= k; ++j) {
-    sa.w = blk[cur];
-    sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
-    sa.z = blk[nxt];
-    sa.mz = MZ(j);
-    sa.cp = CP(j);
-    sa.partials = partials;
-    CK(timed(kKSpmm1, blk_b * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(L, kModePass1, sa, s); }));
-    CK(counted([&] {
-      return launch_small_a(L, partials, MZ(j), d_ta + (size_t)(j - 1) * cstride, CW(j), d_flags, s);
-    }));
-    CK(timed(kKOrth1, blk_b * 3, [&] { return launch_orth(L, blk[cur], blk[nxt], CW(j), partials, s); }));
-    CK(counted([&] {
-      return launch_small_b(L, partials, MZ(j), d_tb + (size_t)(j - 1) * cstride, MZ(j + 1), CP(j + 1),
-                            thr_abs_sq, thr_rel_sq, n_rec, d_flags, s);
-    }));
-    const int old_prev = prv;
-    prv = cur;
-    cur = nxt;
-    if (store)
-      nxt = cur + 1;
-    else
-      nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+  // k steps; `launch` false only walks the buffer rotation (the launches are replayed
+  // from a graph).
+  auto pass1 = [&](cudaStream_t ls, bool launch) -> rdm_status {
+    for (int j = 1; j <= k; ++j) {
+      if (launch) {
+        sa.w = blk[cur];
+        sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
+        sa.z = blk[nxt];
+        sa.mz = MZ(j);
+        sa.cp = CP(j);
+        sa.partials = partials;
+        CK(timed(kKSpmm1, blk_b * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(L, kModePass1, sa, ls); }));
+        CK(counted([&] {
+          return launch_small_a(L, partials, MZ(j), d_ta + (size_t)(j - 1) * cstride, CW(j), d_flags, ls);
+        }));
+        CK(timed(kKOrth1, blk_b * 3, [&] { return launch_orth(L, blk[cur], blk[nxt], CW(j), partials, ls); }));
+        CK(counted([&] {
+          return launch_small_b(L, partials, MZ(j), d_tb + (size_t)(j - 1) * cstride, MZ(j + 1), CP(j + 1),
+                                thr_abs_sq, thr_rel_sq, n_rec, d_flags, ls);
+        }));
+      }
+      const int old_prev = prv;
+      prv = cur;
+      cur = nxt;
+      if (store)
+        nxt = cur + 1;
+      else
+        nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+    }
+    return RDM_OK;
+  };
+  // Graph path: not while kernels are being timed one by one, and only for handles of
+  // a context (the serving loop's per-request handles are used once).
+  bool replayed = false;
+  Pass1Graph& pg = ham->graph;
+  std::unique_lock<std::mutex> glk(pg.mu, std::defer_lock);
+  if (ham->ctx && ham->ctx->graphs && !(prof && prof->on) && glk.try_lock()) {
+    auto bits = [](double x) {
+      uint64_t u;
+      std::memcpy(&u, &x, sizeof u);
+      return u;
+    };
+    const std::vector<uint64_t> key = {
+        (uint64_t)(uintptr_t)s, (uint64_t)(uintptr_t)blk[0], (uint64_t)(uintptr_t)blk[1],
+        (uint64_t)(uintptr_t)(nblk > 2 ? blk[2] : nullptr), (uint64_t)nblk, (uint64_t)(uintptr_t)partials,
+        (uint64_t)(uintptr_t)coef, (uint64_t)(uintptr_t)d_ta, (uint64_t)(uintptr_t)d_tb,
+        (uint64_t)(uintptr_t)d_flags, (uint64_t)(uintptr_t)sa.tile_k, (uint64_t)k, (uint64_t)n_rec,
+        (uint64_t)store, bits(thr_abs_sq), bits(thr_rel_sq), (uint64_t)L.n_bits, (uint64_t)L.n_bath_bits,
+        (uint64_t)L.D, (uint64_t)L.DS, (uint64_t)L.B, (uint64_t)L.Bs, (uint64_t)L.n_slices, (uint64_t)L.VW,
+        (uint64_t)L.TPR, (uint64_t)L.gridx, (uint64_t)L.precision, (uint64_t)L.elem};
+    if (pg.exec && pg.key == key) {
+      CK(cudaGraphLaunch(pg.exec, s));
+      replayed = true;
+    } else if (pg.seen == key) {
+      // second call with this configuration: record it (on a private stream, since the
+      // legacy default stream cannot be captured), then run the recording on s
+      pg.reset();
+      if (!pg.capture) CK(cudaStreamCreateWithFlags(&pg.capture, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(pg.capture, cudaStreamCaptureModeRelaxed));
+      const int c0 = cur, p0 = prv, n0 = nxt;
+      const rdm_status rs = pass1(pg.capture, true);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(pg.capture, &g);
+      cudaGraphExec_t ex = nullptr;
+      if (rs == RDM_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        pg.exec = ex;
+        pg.key = key;
+        CK(cudaGraphLaunch(pg.exec, s));
+        replayed = true;
+      } else {
+        cudaGetLastError();  // fall back to direct launches below
+      }
+      cur = c0, prv = p0, nxt = n0;  // the walk below advances the rotation once
+      if (g) cudaGraphDestroy(g);
+    } else {
+      pg.seen = key;
+    }
   }
+  st = pass1(s, !replayed);
+  if (st != RDM_OK) return st;
   std::vector<double> ta((size_t)k * cstride), tb((size_t)k * cstride), mz((size_t)(k + 1) * cstride);
   uint32_t flags[4];
   CK(cudaMemcpyAsync(ta.data(), d_ta, ta.size() * sizeof(double), cudaMemcpyDeviceToHost, s));

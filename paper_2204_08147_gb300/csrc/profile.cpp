@@ -75,6 +75,15 @@ extern "C" rdm_status rdm_profile(rdm_ctx* ctx, int enable) {
   return RDM_OK;
 }
 
+extern "C" rdm_status rdm_set_graphs(rdm_ctx* ctx, int enable) {
+  if (!ctx) {
+    set_error("rdm_set_graphs: ctx is NULL");
+    return RDM_EINVAL;
+  }
+  ctx->graphs = enable != 0;
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_profile_stats(rdm_ctx* ctx, rdm_kernel_stat* out, int max, int* n) {
   if (!ctx || (!out && max > 0) || !n) {
     set_error("rdm_profile_stats: NULL argument");

@@ -60,18 +60,38 @@ struct rdm_ctx {
   size_t own_bytes = 0;
   std::unique_ptr<rdm::ServeState> serve;
   rdm::Profiler prof;
+  bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete
 };
 
+namespace rdm {
+// The pass-1 launch sequence of one estimator configuration (Algorithm 1's k steps:
+// SpMM, A_j, orthogonalisation, B_j) captured as a CUDA graph. Its kernels take only
+// device pointers and sizes fixed by the configuration, so a graph recorded for one
+// call replays any later call whose key (workspace pointers, layout, k, thresholds)
+// is the same. A configuration is captured on its second use, so one-off calls pay
+// no capture cost.
+struct Pass1Graph {
+  std::mutex mu;
+  std::vector<uint64_t> seen, key;  // last configuration run; the captured one
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;  // capture needs a stream other than the legacy default
+  void reset();
+  ~Pass1Graph() { reset(); }
+};
+}  // namespace rdm
+
 struct rdm_ham {
   rdm_ctx* ctx = nullptr;
+  int device = 0;
   rdm::HostModel model;
   void* d_terms = nullptr;  // owns flips, diags and the tiled tables
   rdm::FlipTerm* d_flips = nullptr;
   rdm::DiagTerm* d_diags = nullptr;
   rdm::TiledTerms tiled{};
   void* d_apply_aux[2] = {};  // tiled apply: error word + K table (float64, float32)
+  rdm::Pass1Graph graph;
 };
 
 namespace rdm {

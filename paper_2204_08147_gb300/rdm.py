@@ -95,6 +95,7 @@ _sig("rdm_poll", C.c_int, _vp, C.c_uint64, C.POINTER(C.c_int))
 _sig("rdm_wait", C.c_int, _vp, C.c_uint64, C.c_int, C.POINTER(C.c_int))
 _sig("rdm_request_times", C.c_int, _vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double))
 _sig("rdm_profile", C.c_int, _vp, C.c_int)
+_sig("rdm_set_graphs", C.c_int, _vp, C.c_int)
 _sig("rdm_profile_stats", C.c_int, _vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int))
 
 
@@ -213,6 +214,10 @@ class Context:
 
     def synchronize(self):
         _check(_lib.rdm_synchronize(self.h), "rdm_synchronize")
+
+    def set_graphs(self, enable: bool = True):
+        """Replay repeated first-pass launch sequences from CUDA graphs (default on)."""
+        _check(_lib.rdm_set_graphs(self.h, 1 if enable else 0), "rdm_set_graphs")
 
     def profile(self, enable: bool = True):
         """Starts (and clears) or stops per-kernel launch counting and event timing."""

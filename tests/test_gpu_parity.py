@@ -334,6 +334,41 @@ def test_serving_alone_equals_in_mix(ctx, lib):
         ctx.serve_stop()
 
 
+# ---------------------------------------------------------------- launch graphs
+
+@pytest.mark.parametrize("case", ["c1_fp64", "tfim_fp32_tiled", "single_fp32"])
+def test_graph_replay_is_bit_identical(ctx, lib, case):
+    """The first pass replayed from a recorded CUDA graph (second and later calls of
+    one configuration) gives the same bits as direct launches; a call with another
+    configuration in between neither replays the wrong graph nor disturbs it."""
+    if case == "c1_fp64":
+        c = W.config_c1()
+        spec, betas, n_v, k, seed, prec, dist, rec = c["spec"], c["betas"], c["n_v"], c["k"], c["seed"], \
+            "fp64", c["dist"], "block"
+    elif case == "tfim_fp32_tiled":
+        spec, betas, n_v, k, seed, prec, dist, rec = W.long_range_tfim(12, 2, 1.5, 0.9), [0.5, 2.0], 8, 25, \
+            11, "fp32", "gauss", "block"
+    else:
+        spec, betas, n_v, k, seed, prec, dist, rec = W.random_model(11, 2, 41), [1.0], 4, 12, 5, "fp32", \
+            "gauss", "single"
+    ham = lib.Hamiltonian(ctx, spec)
+
+    def run(kk):
+        return ham.estimate(betas, n_v, kk, seed, precision=prec, dist=dist, full=True, recurrence=rec)
+    keys = ("rho", "lnZ", "gram_l", "quad_l", "t_a", "t_b")
+    try:
+        ctx.set_graphs(False)
+        ref, ref2 = run(k), run(k + 3)
+        ctx.set_graphs(True)
+        outs = [run(k), run(k), run(k), run(k + 3), run(k), run(k + 3), run(k + 3)]
+    finally:
+        ctx.set_graphs(True)
+        ham.close()
+    for o, r in zip(outs, [ref, ref, ref, ref2, ref, ref2, ref2]):
+        for key in keys:
+            np.testing.assert_array_equal(o[key], r[key])
+
+
 # ---------------------------------------------------------------- storage modes
 
 def test_store_and_recompute_are_bit_identical(ctx, lib):
