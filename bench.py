@@ -305,6 +305,11 @@ def run_ours(a):
             "against": "float64 path of this library, same bath vectors (g index 0)",
         }
 
+    l2_rate = dram_rate = None
+    if rank == 0:
+        l2_rate = ctx.probe_copy_rate(32 << 20)
+        dram_rate = ctx.probe_copy_rate(4 << 30)
+
     serving = None
     if rank == 0 and not a.no_serving:
         serving = serving_bench(rdm, ctx, a.serving_requests)
@@ -334,6 +339,32 @@ def run_ours(a):
             "avg_launch_ms": sp_ms / max(1, sp_launch),
             "operand_gbs": ((n_flip + 2) * blk) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None,
             "share_of_timed_kernels": sp_ms / dev_ms_total if dev_ms_total else None}
+    # Whole Lanczos step against the compulsory traffic of Algorithm 1 (read Q_{j-1},
+    # Q_j, write Q_{j+1}: 3 blocks), and the SpMM's flops 2 D B (flips + 1) against the
+    # FP32 FMA peak (SMs x 128 lanes x 2 flops x max SM clock).
+    orth = stats.get("orth_pass1", {"ms": 0.0, "launches": 0})
+    step_ms = (stats["spmm_pass1"]["ms"] + orth["ms"]) / max(1, stats["spmm_pass1"]["launches"])
+    step_c = 3.0 * blk
+    roof["step"] = {"compulsory_bytes": step_c, "ms_spmm_plus_orth": step_ms,
+                    "gbs": step_c / (step_ms / 1000.0) / 1e9 if step_ms > 0 else None,
+                    "frac": (step_c / (step_ms / 1000.0) / 1e9) / peak if step_ms > 0 else None}
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    spmm_tflops = 2.0 * (1 << a.n_sites) * 4 * a.n_v * (n_flip + 1) / (sp_ms / sp_launch / 1000.0) / 1e12 \
+        if sp_ms > 0 else None
+    roof["spmm_fp32"] = {"tflops": spmm_tflops, "peak_tflops": fp32_peak,
+                         "frac": spmm_tflops / fp32_peak if spmm_tflops else None}
+    # On-chip level: the tiled SpMM copies, per 1024-state tile, its own tile, one
+    # partner tile per distinct high part of the flip masks and the W_{j-1} tile
+    # (none at j = 1) from L2 into shared memory; the denominator is the library's
+    # own bulk-copy probe on an L2-resident buffer, measured in this run.
+    if l2_rate:
+        units = 1 + _partner_tiles(cfgs[0]["spec"]) + (a.k - 1) / a.k
+        l2_gbs = units * blk / (sp_ms / sp_launch / 1000.0) / 1e9
+        roof["l2_to_smem"] = {"achieved": l2_gbs, "peak": l2_rate, "unit": "GB/s", "frac": l2_gbs / l2_rate,
+                              "tiles_per_tile": units, "dram_to_smem_probe": dram_rate,
+                              "peak_kind": "probe: rdm_probe_copy_rate, 32 MB L2-resident buffer, 32 KB "
+                                           "bulk copies, 6 in flight per SM"}
     launches = sum(s["launches"] for s in stats.values())
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
@@ -439,6 +470,23 @@ def small_chain_bench(rdm, ctx, n_solves: int = 50) -> dict:
             "us_per_solve_p99": 1e6 * float(np.percentile(lat, 99)),
             "launches_per_solve": sum(s["launches"] for s in stats.values()) / n_prof,
             "host_small_dense_us_per_solve": 1e3 * host["ms"] / n_prof if host else None}
+
+
+def _partner_tiles(spec, tile_bits: int = 10) -> int:
+    """Distinct nonzero high parts (mask >> tile_bits) of the flip masks of a model:
+    the partner tiles one 1024-state tile of the tiled SpMM needs (site q is bit N-1-q;
+    X on one site and XX/YY on a pair flip those bits)."""
+    n = spec.n_sites
+    highs = set()
+    for q in range(n):
+        if spec.gx[q] != 0:
+            highs.add((1 << (n - 1 - q)) >> tile_bits)
+    for i in range(n):
+        for j in range(i + 1, n):
+            if spec.jx[i, j] != 0 or spec.jy[i, j] != 0:
+                highs.add(((1 << (n - 1 - i)) | (1 << (n - 1 - j))) >> tile_bits)
+    highs.discard(0)
+    return len(highs)
 
 
 def spmm_source_hash() -> str:

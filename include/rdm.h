@@ -165,6 +165,17 @@ rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v, int k,
 /* Waits for all device work issued on the context's stream. */
 rdm_status rdm_synchronize(rdm_ctx* ctx);
 
+/* Measures the rate (GB/s into *gbs) at which TMA bulk copies fill shared memory: one
+ * block per SM keeps `stages` (1..8) 32 KB copies in flight from a device buffer of
+ * buffer_bytes (at least one 32 KB chunk per SM), >= 16 GB in total, timed with CUDA
+ * events on the context's stream after one untimed launch. A buffer of up to 64 MB
+ * stays in L2 (the L2 -> shared-memory rate, the level that feeds the tiled SpMM's
+ * partner tiles); a buffer larger than L2 gives the DRAM -> shared-memory rate.
+ * Allocates and frees its buffer; synchronous. RDM_ENOMEM if the buffer does not fit,
+ * RDM_ECUDA if a copy wait gave up. The paper has no counterpart: this is the
+ * denominator of the SpMM's on-chip roofline. */
+rdm_status rdm_probe_copy_rate(rdm_ctx* ctx, size_t buffer_bytes, int stages, double* gbs);
+
 /* Launch mode of rdm_estimate's first pass (Algorithm 1's k steps, four kernels per
  * step). With enable != 0 (the default) a Hamiltonian handle records that launch
  * sequence as a CUDA graph the second time it runs one configuration (same

@@ -1834,4 +1834,63 @@ cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- copy-rate probe
+//
+// The rate at which TMA bulk copies (the tiled SpMM's only way of filling shared
+// memory) move 32 KB chunks from device memory into shared memory: one block per SM,
+// one issuing thread, `stages` copies in flight in a ring of shared-memory slots (the
+// SpMM's ring depth); the copied data is not read. At step i block b takes chunk
+// (i * gridDim.x + b) mod n_chunks: the blocks sweep the buffer together, front to
+// back, so a buffer smaller than L2 measures L2 -> shared memory after its first pass
+// and a larger one DRAM -> shared memory (no chunk is read twice within a sweep).
+// Every wait is
+// bounded; a wait that gives up sets *err and the block still waits (bounded) for its
+// other copies before it exits.
+__global__ void __launch_bounds__(32, 1) k_probe_copy(const unsigned char* src, int64_t n_chunks, int iters,
+                                                      int stages, int keep_in_l2, uint32_t* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* const full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * kTileBytes);
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(full + kMaxStages);
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < stages; ++i) mbar_init(&full[i], 1);
+  *abort_flag = 0;
+  fence_mbar_init();
+  const uint64_t policy = keep_in_l2 ? policy_evict_last() : policy_evict_first();
+  bool ok = true;
+  int issued = 0;
+  for (int it = 0; it < iters && ok; ++it) {
+    const int slot = it % stages;
+    if (it >= stages && !ring_wait(&full[slot], (uint32_t)((it / stages - 1) & 1), abort_flag)) {
+      ok = false;
+      break;
+    }
+    const int64_t g = ((int64_t)it * gridDim.x + blockIdx.x) % n_chunks;
+    mbar_expect_tx(&full[slot], kTileBytes);
+    bulk_load_hint(smem + (size_t)slot * kTileBytes, src + (size_t)g * kTileBytes, kTileBytes, &full[slot],
+                   policy);
+    issued = it + 1;
+  }
+  // drain: the last min(stages, issued) copies (their slots' most recent phases)
+  for (int it = issued > stages ? issued - stages : 0; it < issued; ++it) {
+    const int slot = it % stages;
+    *abort_flag = 0;
+    if (!ring_wait(&full[slot], (uint32_t)((it / stages) & 1), abort_flag)) ok = false;
+  }
+  if (!ok) atomicOr(err, 1u);
+}
+
+cudaError_t launch_probe_copy(const void* src, int64_t n_chunks, int iters, int stages, bool keep_in_l2,
+                              uint32_t* err, cudaStream_t st) {
+  if (n_chunks <= 0 || iters <= 0 || stages < 1 || stages > kMaxStages) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = opt_in_smem(reinterpret_cast<const void*>(k_probe_copy));
+  if (e != cudaSuccess) return e;
+  const size_t sm = (size_t)stages * kTileBytes + kMaxStages * 8 + 16;
+  k_probe_copy<<<sms, 32, sm, st>>>(static_cast<const unsigned char*>(src), n_chunks, iters, stages,
+                                    keep_in_l2 ? 1 : 0, err);
+  return cudaGetLastError();
+}
+
 }  // namespace rdm

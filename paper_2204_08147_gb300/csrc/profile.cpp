@@ -1,4 +1,6 @@
-// Launch counting and CUDA-event timing of the hot-path kernels (rdm_profile*).
+// Launch counting and CUDA-event timing of the hot-path kernels (rdm_profile*), the
+// first-pass launch mode and the bulk-copy rate probe.
+#include <algorithm>
 #include <cstring>
 
 #include "rdm_api_internal.h"
@@ -73,6 +75,72 @@ extern "C" rdm_status rdm_profile(rdm_ctx* ctx, int enable) {
   if (enable) ctx->prof.reset();
   ctx->prof.on = enable != 0;
   return RDM_OK;
+}
+
+extern "C" rdm_status rdm_probe_copy_rate(rdm_ctx* ctx, size_t buffer_bytes, int stages, double* gbs) {
+  constexpr size_t kChunk = 32768;
+  if (!ctx || !gbs || stages < 1 || stages > 8) {
+    set_error("rdm_probe_copy_rate: ctx and gbs must be non-NULL and 1 <= stages <= 8");
+    return RDM_EINVAL;
+  }
+  *gbs = 0.0;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    set_error("rdm_probe_copy_rate: cudaSetDevice failed");
+    return RDM_ECUDA;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int64_t n_chunks = (int64_t)(buffer_bytes / kChunk);
+  if (sms <= 0 || n_chunks < sms) {
+    set_error("rdm_probe_copy_rate: buffer must hold at least one 32 KB chunk per SM");
+    return RDM_EINVAL;
+  }
+  // each block copies >= its share of the buffer once and >= 16 GB in total overall
+  const int64_t by_total = ((int64_t)16 << 30) / ((int64_t)sms * (int64_t)kChunk);
+  const int iters = (int)std::max<int64_t>((n_chunks + sms - 1) / sms, by_total);
+  const bool keep = buffer_bytes <= ((size_t)64 << 20);
+  char* buf = nullptr;
+  uint32_t* err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rdm_status st = RDM_OK;
+  float ms = 0.f;
+  uint32_t herr = 0;
+  cudaStream_t s = ctx->stream;
+  auto fail = [&](const char* what) {
+    set_error("rdm_probe_copy_rate: %s: %s", what, cudaGetErrorString(cudaGetLastError()));
+    st = RDM_ECUDA;
+  };
+  if (cudaMalloc(&buf, (size_t)n_chunks * kChunk) != cudaSuccess || cudaMalloc(&err, sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("rdm_probe_copy_rate: device allocation failed");
+    st = RDM_ENOMEM;
+  }
+  if (st == RDM_OK && (cudaMemsetAsync(buf, 0, (size_t)n_chunks * kChunk, s) != cudaSuccess ||
+                       cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess))
+    fail("memset");
+  if (st == RDM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    fail("event");
+  // one untimed launch (fills L2 for a small buffer), then the timed one
+  if (st == RDM_OK && launch_probe_copy(buf, n_chunks, iters, stages, keep, err, s) != cudaSuccess)
+    fail("launch");
+  if (st == RDM_OK && (cudaEventRecord(e0, s) != cudaSuccess ||
+                       launch_probe_copy(buf, n_chunks, iters, stages, keep, err, s) != cudaSuccess ||
+                       cudaEventRecord(e1, s) != cudaSuccess))
+    fail("timed launch");
+  if (st == RDM_OK && (cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    fail("readback");
+  if (st == RDM_OK && herr) {
+    set_error("rdm_probe_copy_rate: a bulk-copy wait gave up");
+    st = RDM_ECUDA;
+  }
+  if (st == RDM_OK) *gbs = (double)sms * iters * (double)kChunk / (ms * 1e-3) / 1e9;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  if (buf) cudaFree(buf);
+  if (err) cudaFree(err);
+  return st;
 }
 
 extern "C" rdm_status rdm_set_graphs(rdm_ctx* ctx, int enable) {

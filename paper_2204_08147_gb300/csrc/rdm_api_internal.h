@@ -66,6 +66,11 @@ struct rdm_ctx {
 };
 
 namespace rdm {
+// TMA bulk-copy rate probe (kernels.cu): `stages` 32 KB copies in flight per SM into
+// shared memory from n_chunks chunks of src, iters copies per block (one block per SM).
+cudaError_t launch_probe_copy(const void* src, int64_t n_chunks, int iters, int stages, bool keep_in_l2,
+                              uint32_t* err, cudaStream_t st);
+
 // The pass-1 launch sequence of one estimator configuration (Algorithm 1's k steps:
 // SpMM, A_j, orthogonalisation, B_j) captured as a CUDA graph. Its kernels take only
 // device pointers and sizes fixed by the configuration, so a graph recorded for one

@@ -96,6 +96,7 @@ _sig("rdm_wait", C.c_int, _vp, C.c_uint64, C.c_int, C.POINTER(C.c_int))
 _sig("rdm_request_times", C.c_int, _vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double))
 _sig("rdm_profile", C.c_int, _vp, C.c_int)
 _sig("rdm_set_graphs", C.c_int, _vp, C.c_int)
+_sig("rdm_probe_copy_rate", C.c_int, _vp, C.c_size_t, C.c_int, C.POINTER(C.c_double))
 _sig("rdm_profile_stats", C.c_int, _vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int))
 
 
@@ -214,6 +215,14 @@ class Context:
 
     def synchronize(self):
         _check(_lib.rdm_synchronize(self.h), "rdm_synchronize")
+
+    def probe_copy_rate(self, buffer_bytes: int, stages: int = 6) -> float:
+        """GB/s of 32 KB TMA bulk copies into shared memory (one block per SM, `stages`
+        in flight) from a buffer of buffer_bytes: <= 64 MB measures L2, larger DRAM."""
+        g = C.c_double()
+        _check(_lib.rdm_probe_copy_rate(self.h, int(buffer_bytes), int(stages), C.byref(g)),
+               "rdm_probe_copy_rate")
+        return g.value
 
     def set_graphs(self, enable: bool = True):
         """Replay repeated first-pass launch sequences from CUDA graphs (default on)."""

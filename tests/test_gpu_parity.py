@@ -334,6 +334,21 @@ def test_serving_alone_equals_in_mix(ctx, lib):
         ctx.serve_stop()
 
 
+# ---------------------------------------------------------------- copy-rate probe
+
+def test_copy_rate_probe(ctx, lib):
+    """The bulk-copy probe (the SpMM's on-chip roofline denominator) returns a finite
+    rate with L2 no slower than DRAM, and rejects invalid arguments."""
+    l2 = ctx.probe_copy_rate(32 << 20)
+    dram = ctx.probe_copy_rate(1 << 30)
+    assert 500.0 < dram < 100000.0 and 500.0 < l2 < 100000.0
+    assert l2 > 0.9 * dram
+    for bad in [(32 << 20, 0), (32 << 20, 9), (1 << 20, 6)]:
+        with pytest.raises(lib.RdmError) as e:
+            ctx.probe_copy_rate(*bad)
+        assert e.value.status == lib.EINVAL
+
+
 # ---------------------------------------------------------------- launch graphs
 
 @pytest.mark.parametrize("case", ["c1_fp64", "tfim_fp32_tiled", "single_fp32"])
