@@ -313,9 +313,10 @@ def run_ours(a):
     serving = None
     if rank == 0 and not a.no_serving:
         serving = serving_bench(rdm, ctx, a.serving_requests)
-    small = None
+    small = sweep = None
     if rank == 0 and not a.no_small:
         small = small_chain_bench(rdm, ctx)
+        sweep = sweep_bench(rdm, ctx)
 
     if rank != 0:
         if dist:
@@ -388,6 +389,7 @@ def run_ours(a):
         "precision_fp32_vs_fp64": precision,
         "serving": serving,
         "small_chain": small,
+        "sweep": sweep,
     }
     if cpu_sample is not None:
         line["cpu_baseline"] = {"value": oracle_solves_per_s(cpu_sample), "unit": "solves/s", "cores": 1,
@@ -487,6 +489,33 @@ def _partner_tiles(spec, tile_bits: int = 10) -> int:
                 highs.add(((1 << (n - 1 - i)) | (1 << (n - 1 - j))) >> tile_bits)
     highs.discard(0)
     return len(highs)
+
+
+def sweep_bench(rdm, ctx) -> dict:
+    """A parameter sweep shaped like the paper's entropy phase plot (Sec. 5.3.1):
+    long-range XY chain N=16, J/|i-j|, N_s=2, field h over 8 values in [0, 2.2],
+    n_v=400 Gaussian bath vectors, k=60, 8 betas in [0.5, 4], float32; one solve per
+    h value, back to back (each solve's Krylov block is 2^16 x 1600 columns)."""
+    hs = np.linspace(0.0, 2.2, 8)
+    betas = W.beta_grid(8, 0.5, 4.0)
+    hams = [rdm.Hamiltonian(ctx, W.long_range_xxz(16, 2, alpha=1.0, delta=0.0, h=float(h), lam=1.0)) for h in hs]
+
+    def one(i):
+        return hams[i].estimate(betas, 400, 60, 20220421, precision="fp32", dist="gauss")
+    one(0)
+    ctx.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(len(hs)):
+        t1 = time.perf_counter()
+        one(i)
+        lat.append(time.perf_counter() - t1)
+    wall = time.perf_counter() - t0
+    for h in hams:
+        h.close()
+    return {"workload": "lr_xy_N16_Ns2_alpha1_h0-2.2x8_nv400_k60_8beta_fp32", "solves": len(hs),
+            "solves_per_s": len(hs) / wall, "ms_per_solve_p50": 1000 * float(np.percentile(lat, 50)),
+            "block_mb": (1 << 16) * 1600 * 4 / 1e6}
 
 
 def spmm_source_hash() -> str:

@@ -112,27 +112,31 @@ __device__ __forceinline__ unsigned group_mask(int tpr) {
   return ((1u << tpr) - 1u) << (lane & ~(unsigned)(tpr - 1));
 }
 
-// Fixed-order block reduction of NV float64 values per thread into per-block
+// Fixed-order block reduction of NV values per thread into per-block float64
 // partials: partials[((slice*gridx + bx)*G_s + lane*NG + g)*NVG + v] where
 // vals[g*NVG + v] belongs to group g of the thread and lane = threadIdx.x % tpr
 // (tpr <= 8, a power of two). A butterfly over the lanes of a warp with the same
-// lane, then the warps' sums added in warp order: the same order on every run.
-template <int NG, int NVG>
-__device__ void block_reduce_store(const double* vals, int tpr, double* partials, int gs) {
+// lane in the type R of vals, then the warps' sums added in float64 in warp order:
+// the same order on every run. The per-step reductions of the float32 path use
+// R = float for the butterfly (the per-thread sums are float32 already): GB300's
+// float64 pipe is narrow, and a float64 butterfly over every block made short-block
+// launches float64-bound.
+template <int NG, int NVG, typename R = double>
+__device__ void block_reduce_store(const R* vals, int tpr, double* partials, int gs) {
   constexpr int NV = NG * NVG;
   constexpr int kWarps = kThreads / 32;
   __shared__ double red[kWarps * 8 * NV];
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  double v[NV];
+  R v[NV];
 #pragma unroll
   for (int e = 0; e < NV; ++e) {
-    double x = vals[e];
+    R x = vals[e];
     for (int o = tpr; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     v[e] = x;
   }
   if (wl < tpr) {
 #pragma unroll
-    for (int e = 0; e < NV; ++e) red[(warp * tpr + wl) * NV + e] = v[e];
+    for (int e = 0; e < NV; ++e) red[(warp * tpr + wl) * NV + e] = (double)v[e];
   }
   __syncthreads();
   if ((int)threadIdx.x < tpr * NV) {
@@ -397,14 +401,14 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
     }
   }
   if (MODE == kModePass1) {
-    double vals[NG * NVG];
+    T vals[NG * NVG];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int i = 0; i < DS; ++i)
 #pragma unroll
-        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
-    block_reduce_store<NG, NVG>(vals, tpr, a.partials, L.groups_per_slice());
+        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
+    block_reduce_store<NG, NVG, T>(vals, tpr, a.partials, L.groups_per_slice());
   }
 }
 
@@ -877,18 +881,19 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       if (consumers_sync_or(aborted)) aborted = true;
       if (MODE == kModePass1 && !aborted) {
         if (cur >= 0) {
-          // fixed-order reduction: shuffles within a warp, then the warps in order
-          double v[NV];
+          // fixed-order reduction: shuffles within a warp (in T, like the per-thread
+          // sums), then the warps in order in float64
+          T v[NV];
 #pragma unroll
           for (int e = 0; e < NV; ++e) {
-            double x = (double)acc[e];
+            T x = acc[e];
 #pragma unroll
             for (int o = LPR; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             v[e] = x;
           }
           if ((threadIdx.x & 31) < LPR) {
 #pragma unroll
-            for (int e = 0; e < NV; ++e) red[(warp * LPR + lane) * 16 + e] = v[e];
+            for (int e = 0; e < NV; ++e) red[(warp * LPR + lane) * 16 + e] = (double)v[e];
           }
           consumers_sync_or(false);
           if (threadIdx.x < LPR) {
@@ -1202,14 +1207,14 @@ __global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict
     }
   }
   if (PASS1) {
-    double vals[NG * NVG];
+    T vals[NG * NVG];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int i = 0; i < DS; ++i)
 #pragma unroll
-        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
-    block_reduce_store<NG, NVG>(vals, tpr, partials, L.groups_per_slice());
+        for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
+    block_reduce_store<NG, NVG, T>(vals, tpr, partials, L.groups_per_slice());
   }
 }
 
