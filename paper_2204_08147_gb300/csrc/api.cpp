@@ -227,6 +227,9 @@ void make_term_image(const HostModel& h, TermImage* img) {
     if (pat_start[q + 1] - t != 1 || term_low[t] != 0u || term_odd[t] != term_even[t] || term_odd[t] == 0.0)
       img->partners_flat = 0;
   }
+  img->all_uniform = 1;
+  for (size_t t = 0; t < term_odd.size(); ++t)
+    if (term_odd[t] != term_even[t]) img->all_uniform = 0;
   img->n_pat = tiled ? (int)pat_high.size() : 0;
   img->n_terms = tiled ? (int)term_low.size() : 0;
   auto& b = img->bytes;
@@ -262,6 +265,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   t.n_pat = img.n_pat;
   t.all_active = img.all_active;
   t.partners_flat = img.partners_flat;
+  t.all_uniform = img.all_uniform;
   t.n_reg0 = img.n_reg0;
   t.n_terms = img.n_terms;
   t.pat_high = reinterpret_cast<const uint32_t*>(dev + img.off_pat_high);

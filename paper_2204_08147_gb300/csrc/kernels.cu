@@ -117,10 +117,9 @@ __device__ __forceinline__ unsigned group_mask(int tpr) {
 // vals[g*NVG + v] belongs to group g of the thread and lane = threadIdx.x % tpr
 // (tpr <= 8, a power of two). A butterfly over the lanes of a warp with the same
 // lane in the type R of vals, then the warps' sums added in float64 in warp order:
-// the same order on every run. The per-step reductions of the float32 path use
-// R = float for the butterfly (the per-thread sums are float32 already): GB300's
-// float64 pipe is narrow, and a float64 butterfly over every block made short-block
-// launches float64-bound.
+// the same order on every run. The float32 path runs the butterfly in float32 (its
+// per-thread sums are float32 already): GB300's float64 pipe is narrow, and a float64
+// butterfly in every block made launches of many short blocks float64-bound.
 template <int NG, int NVG, typename R = double>
 __device__ void block_reduce_store(const R* vals, int tpr, double* partials, int gs) {
   constexpr int NV = NG * NVG;
@@ -554,11 +553,11 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, volati
 // In-tile flip whose partner rows belong to the same thread: the thread's rows
 // rg + RG m (m = 0..7) form a subcube over the top three tile bits, so a mask with
 // no bit below log2(RG) maps row m to row m ^ K of the same thread.
-template <int K, int RG, typename T, int VW, int RPT>
+template <int K, int RG, bool UNI, typename T, int VW, int RPT>
 __device__ __forceinline__ void reg_flip(T (&y)[RPT][VW], const T (&xo)[RPT][VW], int rg, uint32_t ml,
                                          T co, T ce) {
   if constexpr (K >= RPT) return;
-  if (co == ce) {
+  if (UNI || co == ce) {
 #pragma unroll
     for (int m = 0; m < RPT; ++m)
 #pragma unroll
@@ -586,13 +585,15 @@ __device__ __forceinline__ int partner_base(int rgoff, uint32_t ml) {
 
 // y[m] += c * P[row m ^ ml] for one term whose coefficient depends on the parity of
 // (row0 + row) & mparity (c_odd / c_even), rows of this thread.
-template <typename T, int VW, int RPT, int RG, int BS>
+// UNI: every term of the Hamiltonian has c_odd = c_even (a separate instantiation,
+// so the parity-dependent code below is not compiled into it).
+template <typename T, int VW, int RPT, int RG, int BS, bool UNI>
 __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], int rgoff, int rg, const T* P, uint32_t ml,
                                            uint32_t mparity, T co, T ce, uint32_t row0) {
   constexpr int kStep = RG * BS;
   const int x = partner_base<RG, BS>(rgoff, ml);
   const bool flat = ml < (uint32_t)RG;  // mh = 0: partner offsets x + m * kStep
-  if (co == ce) {
+  if (UNI || co == ce) {
     if (flat) {
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
@@ -610,16 +611,33 @@ __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], int rgoff, int rg, c
         for (int v = 0; v < VW; ++v) y[m][v] = fma(co, xp[v], y[m][v]);
       }
     }
-  } else {
-#pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-      const uint32_t r = (uint32_t)(rg + RG * m);
-      const T c = (__popc((row0 + r) & mparity) & 1) ? co : ce;
+  } else if constexpr (!UNI) {
+    // Row row0 + rg + RG m is row0 | rg | m << log2(RG) (disjoint bits), so its parity
+    // under mparity is p0 (that of row0 | rg) xor the parity of m & mh. With mh = 0 the
+    // coefficient is the same for all of this thread's rows: one test per term.
+    const uint32_t mh = (mparity / (uint32_t)RG) & (uint32_t)(RPT - 1);
+    const uint32_t p0 = (uint32_t)__popc((row0 + (uint32_t)rg) & mparity) & 1u;
+    if (mh == 0u) {
+      const T c = p0 ? co : ce;
       if (c != (T)0) {
-        T xp[VW];
-        VecIO<T, VW>::ld_rw(xp, P + (x ^ (m * kStep)));
 #pragma unroll
-        for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+        for (int m = 0; m < RPT; ++m) {
+          T xp[VW];
+          VecIO<T, VW>::ld_rw(xp, P + (x ^ (m * kStep)));
+#pragma unroll
+          for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        const T c = ((p0 ^ (uint32_t)__popc((uint32_t)m & mh)) & 1u) ? co : ce;
+        if (c != (T)0) {
+          T xp[VW];
+          VecIO<T, VW>::ld_rw(xp, P + (x ^ (m * kStep)));
+#pragma unroll
+          for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+        }
       }
     }
   }
@@ -675,7 +693,7 @@ __device__ __forceinline__ void tile_diagonal(T (&dg)[RPT], const T* low, const 
   for (int m = 0; m < RPT; ++m) dg[m] = low[rg + RG * m] + A[m];
 }
 
-template <typename T, int DS, int MODE>
+template <typename T, int DS, int MODE, bool UNI = false>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmArgs a) {
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int LPR = kTiledLanes;          // 16-byte vectors per row
@@ -951,13 +969,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     for (int t = pat[0].start; t < tr; ++t) {  // masks on the register rows only
       const TermS<T> d = term[t];
       switch (d.low >> RGL) {
-        case 1: reg_flip<1, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        case 2: reg_flip<2, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        case 3: reg_flip<3, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        case 4: reg_flip<4, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        case 5: reg_flip<5, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        case 6: reg_flip<6, RG>(y, xo, rg, d.low, d.co, d.ce); break;
-        default: reg_flip<7, RG>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 1: reg_flip<1, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 2: reg_flip<2, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 3: reg_flip<3, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 4: reg_flip<4, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 5: reg_flip<5, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        case 6: reg_flip<6, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
+        default: reg_flip<7, RG, UNI>(y, xo, rg, d.low, d.co, d.ce); break;
       }
     }
     for (int t = tr; t < t1;) {
@@ -970,7 +988,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
           continue;
         }
       }
-      apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, own, d.low, d.low, d.co, d.ce, 0u);
+      apply_term<T, VW, RPT, RG, BS, UNI>(y, rgoff, rg, own, d.low, d.low, d.co, d.ce, 0u);
       ++t;
     }
     release();
@@ -1050,7 +1068,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             continue;
           }
         }
-        apply_term<T, VW, RPT, RG, BS>(y, rgoff, rg, P, d.low, d.low | hi_bits, d.co, d.ce, row0);
+        apply_term<T, VW, RPT, RG, BS, UNI>(y, rgoff, rg, P, d.low, d.low | hi_bits, d.co, d.ce, row0);
         ++t;
       }
       release();
@@ -1278,14 +1296,14 @@ __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __re
 #pragma unroll
         for (int j = 0; j < DS; ++j) acc[g][i][j] = fma(p[g * DS + i], p[g * DS + j], acc[g][i][j]);
   }
-  double vals[NG * NVG];
+  T vals[NG * NVG];
 #pragma unroll
   for (int g = 0; g < NG; ++g)
 #pragma unroll
     for (int i = 0; i < DS; ++i)
 #pragma unroll
-      for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[g][i][j];
-  block_reduce_store<NG, NVG>(vals, tpr, partials, L.groups_per_slice());
+      for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
+  block_reduce_store<NG, NVG, T>(vals, tpr, partials, L.groups_per_slice());
 }
 
 // Stored-basis Gram: psi_beta = sum_{j=1..k} W_j E_{j,beta} row by row (the same
@@ -1440,14 +1458,14 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
 #pragma unroll
   for (int bi = 0; bi < NBT; ++bi) {  // static indices keep acc in registers
     if (bi < nb) {
-      double vals[NG * NVG];
+      T vals[NG * NVG];
 #pragma unroll
       for (int g = 0; g < NG; ++g)
 #pragma unroll
         for (int i = 0; i < DS; ++i)
 #pragma unroll
-          for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = (double)acc[bi][g][i][j];
-      block_reduce_store<NG, NVG>(vals, tpr, partials + (size_t)bi * pstride, gs);
+          for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[bi][g][i][j];
+      block_reduce_store<NG, NVG, T>(vals, tpr, partials + (size_t)bi * pstride, gs);
       __syncthreads();
     }
   }
@@ -1693,9 +1711,9 @@ cudaError_t launch_tile_diag(const Layout& L, const TileDiag& dg, void* out, cud
   return cudaGetLastError();
 }
 
-template <typename T, int DS, int MODE>
+template <typename T, int DS, int MODE, bool UNI = false>
 static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a0, cudaStream_t st) {
-  cudaError_t e = opt_in_smem(reinterpret_cast<const void*>(k_spmm_tiled<T, DS, MODE>));
+  cudaError_t e = opt_in_smem(reinterpret_cast<const void*>(k_spmm_tiled<T, DS, MODE, UNI>));
   if (e != cudaSuccess) return e;
   static int optin = 0;
   if (!optin) {
@@ -1713,7 +1731,7 @@ static cudaError_t launch_tiled(const Layout& L, const SpmmArgs& a0, cudaStream_
     a.stages -= kProducerWarps;
   const size_t sm = tiled_smem_bytes<T>(tt.n_pat, tt.n_terms, tt.dg.n_entries, a.stages);
   if (sm > (size_t)optin) return cudaErrorInvalidValue;
-  k_spmm_tiled<T, DS, MODE><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
+  k_spmm_tiled<T, DS, MODE, UNI><<<dim3((unsigned)spmm_tiled_grid(L), 1), kTiledThreads, sm, st>>>(L, a);
   return cudaGetLastError();
 }
 
@@ -1725,6 +1743,13 @@ cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream
       return f32 ? launch_tiled<float, 1, kModeApply>(L, a, st) : launch_tiled<double, 1, kModeApply>(L, a, st);
     }
     const bool p1 = mode == kModePass1;
+    if (f32 && a.tiled.all_uniform) {  // no parity-dependent coefficient anywhere
+      if (L.DS == 1)
+        return p1 ? launch_tiled<float, 1, kModePass1, true>(L, a, st) : launch_tiled<float, 1, kModePass2, true>(L, a, st);
+      if (L.DS == 2)
+        return p1 ? launch_tiled<float, 2, kModePass1, true>(L, a, st) : launch_tiled<float, 2, kModePass2, true>(L, a, st);
+      return p1 ? launch_tiled<float, 4, kModePass1, true>(L, a, st) : launch_tiled<float, 4, kModePass2, true>(L, a, st);
+    }
     if (f32) {
       if (L.DS == 1) return p1 ? launch_tiled<float, 1, kModePass1>(L, a, st) : launch_tiled<float, 1, kModePass2>(L, a, st);
       if (L.DS == 2) return p1 ? launch_tiled<float, 2, kModePass1>(L, a, st) : launch_tiled<float, 2, kModePass2>(L, a, st);

@@ -157,6 +157,7 @@ struct TiledTerms {
   int n_terms;
   int all_active;             // 1: every tile needs every partner pattern
   int partners_flat;          // 1: and each is one uniform term with m_low = 0
+  int all_uniform;            // 1: every term has c_odd = c_even
   int n_reg0;                 // leading in-tile terms that act on register rows only
   const uint32_t* pat_high;   // [n_pat]
   const int* pat_start;       // [n_pat + 1]
