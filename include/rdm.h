@@ -312,6 +312,19 @@ rdm_status rdm_energy_deviation(const double* rho, const double* h_star, const d
 /* S = -tr(rho ln rho) = -sum_i p_i ln p_i with 0 ln 0 = 0 (Sec. 5.3.1). */
 rdm_status rdm_entropy(const double* rho, int d_s, double* s_out);
 
+/* The small dense step of rdm_estimate for one recurrence (eq. fT, Sec. 3.1-3.2):
+ * c_beta = exp(-beta (T - t_min I) / 2) E1 for every beta of the grid, where T is the
+ * symmetric n x n matrix t (row-major; the block tridiagonal T_l of Algorithm 1 with
+ * blocks of p = d_s, n = k p), E1 its first p columns of the identity and t_min its
+ * smallest eigenvalue (returned in *t_min; rdm_estimate rescales by
+ * exp(-beta (t_min - E0) / 2) once the common E0 is known). c: n_beta * n * p, row-major
+ * per beta. Computed without eigenvectors: band or Householder reduction to
+ * tridiagonal form, implicit QR, rotations applied to E1 and back. Host float64;
+ * RDM_EINVAL for bad sizes, a negative or non-finite beta or a non-finite T,
+ * RDM_ENUMERIC if the QR iteration does not converge. */
+rdm_status rdm_function_of_t(int n, int p, const double* t, int n_beta, const double* betas,
+                             double* t_min, double* c);
+
 /* Eigendecomposition of a dense symmetric n x n matrix (row-major a), used by
  * the small dense step of the estimator: w ascending (n), v (n*n, row-major,
  * column j = eigenvector j; NULL for values only). Host float64. */

@@ -401,6 +401,29 @@ bool tdense_fT(int n, int p, const double* t_in, int n_beta, const double* betas
 
 using rdm::set_error;
 
+extern "C" rdm_status rdm_function_of_t(int n, int p, const double* t, int n_beta, const double* betas,
+                                        double* t_min, double* c) {
+  if (n < 1 || n > 8192 || p < 1 || p > n || n_beta < 1 || !t || !betas || !t_min || !c) {
+    set_error("rdm_function_of_t: need 1 <= p <= n <= 8192, n_beta >= 1 and non-NULL arrays");
+    return RDM_EINVAL;
+  }
+  for (int b = 0; b < n_beta; ++b)
+    if (!(betas[b] >= 0.0) || !std::isfinite(betas[b])) {
+      set_error("rdm_function_of_t: beta[%d] must be finite and >= 0", b);
+      return RDM_EINVAL;
+    }
+  for (size_t i = 0; i < (size_t)n * n; ++i)
+    if (!std::isfinite(t[i])) {
+      set_error("rdm_function_of_t: T has a non-finite entry");
+      return RDM_EINVAL;
+    }
+  if (!rdm::tdense_fT(n, p, t, n_beta, betas, t_min, c)) {
+    set_error("rdm_function_of_t: QR iteration did not converge");
+    return RDM_ENUMERIC;
+  }
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_symmetric_eig(int n, const double* a, double* w, double* v) {
   if (n < 1 || n > 8192 || !a || !w) {
     set_error("rdm_symmetric_eig: need 1 <= n <= 8192 and non-NULL a, w");

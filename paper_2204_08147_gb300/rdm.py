@@ -86,6 +86,7 @@ _sig("rdm_system_hamiltonian", C.c_int, C.POINTER(Model), _dp)
 _sig("rdm_mean_force_abs", C.c_int, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp)
 _sig("rdm_energy_deviation", C.c_int, _dp, _dp, _dp, C.c_int, C.c_double, _dp)
 _sig("rdm_entropy", C.c_int, _dp, C.c_int, _dp)
+_sig("rdm_function_of_t", C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _dp)
 _sig("rdm_symmetric_eig", C.c_int, C.c_int, _dp, _dp, _dp)
 _sig("rdm_serve_start", C.c_int, _vp, C.c_size_t, C.c_int)
 _sig("rdm_serve_stop", C.c_int, _vp)
@@ -427,6 +428,19 @@ def entropy(rho: np.ndarray) -> float:
     s = C.c_double()
     _check(_lib.rdm_entropy(_ptr(r), r.shape[0], C.byref(s)), "rdm_entropy")
     return s.value
+
+
+def function_of_t(t: np.ndarray, p: int, betas) -> tuple:
+    """(t_min, c) with c[b] = exp(-beta_b (T - t_min) / 2) E1 (n x p), the small dense
+    step of the estimator for one recurrence (eq. fT)."""
+    m = np.ascontiguousarray(t, dtype=np.float64)
+    n = m.shape[0]
+    b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
+    c = np.zeros((len(b), n, p))
+    tmin = C.c_double()
+    _check(_lib.rdm_function_of_t(n, int(p), _ptr(m), len(b), _ptr(b), C.byref(tmin), _ptr(c)),
+           "rdm_function_of_t")
+    return tmin.value, c
 
 
 def symmetric_eig(a: np.ndarray, vectors: bool = True):

@@ -64,6 +64,61 @@ def test_symmetric_eig_block_tridiagonal_and_degenerate(rdm):
     np.testing.assert_allclose(v.T @ v, np.eye(6), atol=1e-13)
 
 
+def _block_tridiagonal(rng, p, k, scale=1.0):
+    t = np.zeros((p * k, p * k))
+    for j in range(k):
+        a = rng.normal(size=(p, p)) * scale
+        t[j * p:(j + 1) * p, j * p:(j + 1) * p] = a + a.T
+        if j + 1 < k:
+            b = np.triu(rng.normal(size=(p, p))) * scale
+            t[(j + 1) * p:(j + 2) * p, j * p:(j + 1) * p] = b
+            t[j * p:(j + 1) * p, (j + 1) * p:(j + 2) * p] = b.T
+    return t
+
+
+@pytest.mark.parametrize("p,k", [(1, 40), (2, 30), (4, 25), (4, 60), (3, 7)])
+def test_function_of_t_matches_oracle(rdm, p, k):
+    """The small dense step (eq. fT) on block tridiagonal T (band reduction path) and on
+    a dense symmetric T (Householder path) against the oracle's eigendecomposition form."""
+    from oracle import lanczos
+    rng = np.random.default_rng(100 + p * k)
+    betas = [0.0, 0.3, 1.0, 4.0]
+    for t in (_block_tridiagonal(rng, p, k), None):
+        if t is None:
+            x = rng.normal(size=(p * k, p * k))
+            t = x + x.T
+        tmin, c = rdm.function_of_t(t, p, betas)
+        w = np.linalg.eigvalsh(t)
+        assert abs(tmin - w[0]) < 1e-12 * max(1.0, np.abs(w).max())
+        for bi, beta in enumerate(betas):
+            ref = lanczos.function_of_t_first_block(t, p, lambda x: np.exp(-beta * (x - tmin) / 2.0))
+            np.testing.assert_allclose(c[bi], ref, atol=1e-12 * np.sqrt(p * k), rtol=0)
+
+
+def test_function_of_t_degenerate_and_errors(rdm):
+    """Exactly degenerate spectra and decoupled blocks (a Krylov breakdown leaves B_j = 0),
+    and the argument checks."""
+    rng = np.random.default_rng(7)
+    q, _ = np.linalg.qr(rng.normal(size=(8, 8)))
+    t = q @ np.diag([1.0, 1.0, 1.0, -2.0, 0.5, 0.5, 3.0, 3.0]) @ q.T
+    tmin, c = rdm.function_of_t(t, 2, [1.5])
+    assert abs(tmin + 2.0) < 1e-13
+    w, v = np.linalg.eigh(t)
+    ref = (v * np.exp(-1.5 * (w - tmin) / 2)) @ v[:2, :].T
+    np.testing.assert_allclose(c[0], ref, atol=1e-13)
+    blk = _block_tridiagonal(rng, 2, 10)
+    blk[8:10, 6:8] = blk[6:8, 8:10] = 0.0  # B_4 = 0: T splits
+    tmin, c = rdm.function_of_t(blk, 2, [2.0])
+    w, v = np.linalg.eigh(blk)
+    np.testing.assert_allclose(c[0], (v * np.exp(-(w - tmin))) @ v[:2, :].T, atol=1e-12)
+    np.testing.assert_allclose(c[0][8:], 0.0, atol=1e-14)  # E1 never reaches the lower part
+    for bad in [(np.eye(3), 4, [1.0]), (np.eye(3), 1, [-1.0]), (np.eye(3), 1, [float("inf")]),
+                (np.full((3, 3), np.nan), 1, [1.0])]:
+        with pytest.raises(rdm.RdmError) as e:
+            rdm.function_of_t(*bad)
+        assert e.value.status == rdm.EINVAL
+
+
 def test_mean_force_and_entropy_match_oracle(rdm):
     from oracle import post
     rng = np.random.default_rng(2)
