@@ -106,6 +106,15 @@ def oracle_solves_per_s(sample: dict) -> float:
     return 1.0 / per_solve
 
 
+def _config(a, world: int) -> dict:
+    """The workload description both arms print (the benchmark, or a profiling case)."""
+    bench_case = (a.n_sites, a.k, a.n_v) == (22, 60, 32)
+    return {"workload": WORKLOAD if bench_case else f"profiling_N{a.n_sites}_k{a.k}_nv{a.n_v}",
+            "n_sites": a.n_sites, "n_sys": 2, "n_v": a.n_v, "k": a.k,
+            "beta": [1.0], "g_values": N_G, "block_columns": 4 * a.n_v, "l2": "inputs larger than L2",
+            "parallelism": f"replicas{world}"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -121,7 +130,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "data": "synthetic", "config": _config(a, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "per step: 2 Lanczos steps of bath vector 0 at full size "
                                    "(D=2^22, 4 columns, float64 NumPy), scaled to 32 vectors x "
@@ -372,11 +381,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if (a.n_sites, a.k, a.n_v) == (22, 60, 32)
-                   else f"profiling_N{a.n_sites}_k{a.k}_nv{a.n_v}",
-                   "n_sites": a.n_sites, "n_sys": 2, "n_v": a.n_v, "k": a.k,
-                   "beta": [1.0], "g_values": 16, "block_columns": 4 * a.n_v, "l2": "inputs larger than L2",
-                   "parallelism": f"replicas{world}"},
+        "config": _config(a, world),
         "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99))},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d / e2e_steps,
