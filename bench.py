@@ -52,6 +52,9 @@ def _args():
     p.add_argument("--no-serving", action="store_true", help="skip the serving sub-benchmark")
     p.add_argument("--serving-requests", type=int, default=32)
     p.add_argument("--no-small", action="store_true", help="skip the small-chain latency sub-benchmark")
+    p.add_argument("--model", default="tfim", choices=["tfim", "xxz"],
+                   help="profiling cases only: xxz = long-range XXZ (J/|i-j|, Delta=1, h=0.1, N_s=1, "
+                        "Rademacher), the all-to-all XX+YY shape of the 25- and 30-spin configurations")
     return p.parse_args()
 
 
@@ -106,12 +109,18 @@ def oracle_solves_per_s(sample: dict) -> float:
     return 1.0 / per_solve
 
 
+def _bench_case(a) -> bool:
+    return (a.n_sites, a.k, a.n_v, a.model) == (22, 60, 32, "tfim")
+
+
 def _config(a, world: int) -> dict:
     """The workload description both arms print (the benchmark, or a profiling case)."""
-    bench_case = (a.n_sites, a.k, a.n_v) == (22, 60, 32)
-    return {"workload": WORKLOAD if bench_case else f"profiling_N{a.n_sites}_k{a.k}_nv{a.n_v}",
-            "n_sites": a.n_sites, "n_sys": 2, "n_v": a.n_v, "k": a.k,
-            "beta": [1.0], "g_values": N_G, "block_columns": 4 * a.n_v, "l2": "inputs larger than L2",
+    bench_case = _bench_case(a)
+    xxz = a.model == "xxz"
+    return {"workload": WORKLOAD if bench_case else f"profiling_{a.model}_N{a.n_sites}_k{a.k}_nv{a.n_v}",
+            "n_sites": a.n_sites, "n_sys": 1 if xxz else 2, "n_v": a.n_v, "k": a.k,
+            "beta": [1.0], "g_values": 1 if xxz else N_G, "block_columns": (2 if xxz else 4) * a.n_v,
+            "l2": "inputs larger than L2",
             "parallelism": f"replicas{world}"}
 
 
@@ -216,9 +225,12 @@ def run_ours(a):
     from paper_2204_08147_gb300 import rdm
     ctx = rdm.Context(local)
     cfgs = [W.config_c2(g) for g in range(N_G)]
-    if (a.n_sites, a.k, a.n_v) != (22, 60, 32):  # profiling case, not a benchmark number
+    if not _bench_case(a):  # profiling case, not a benchmark number
         for c in cfgs:
-            c["spec"] = W.long_range_tfim(a.n_sites, 2, 1.5, float(c["spec"].gx[0]))
+            c["spec"] = (W.long_range_tfim(a.n_sites, 2, 1.5, float(c["spec"].gx[0])) if a.model == "tfim"
+                         else W.long_range_xxz(a.n_sites, 1, 1.0, 1.0, 0.1))
+            if a.model == "xxz":
+                c["dist"] = "rademacher"
             c["k"] = a.k
             c["n_v"] = a.n_v
     hams = [rdm.Hamiltonian(ctx, c["spec"]) for c in cfgs]
@@ -301,7 +313,7 @@ def run_ours(a):
 
     # Precision: float32 path against the float64 path on the same seeds (one g value).
     precision = None
-    if rank == 0 and (a.n_sites, a.k, a.n_v) == (22, 60, 32):
+    if rank == 0 and _bench_case(a):
         c = cfgs[0]
         r32 = hams[0].estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp32", dist=c["dist"])
         r64 = hams[0].estimate(c["betas"], c["n_v"], c["k"], c["seed"], precision="fp64", dist=c["dist"])
@@ -341,14 +353,19 @@ def run_ours(a):
     dev_ms_total = sum(s["ms"] for s in stats.values())
     achieved = (sp_bytes / sp_launch) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None
     n_flip = hams[0].info()["n_flip"]
-    blk = (1 << a.n_sites) * 4 * a.n_v * 4
+    d_s = 2 if a.model == "xxz" else 4
+    cols = d_s * a.n_v
+    blk = (1 << a.n_sites) * cols * 4
+    # flips applied per row: every transverse-field term; half of the XX+YY pair terms
+    # (only antiparallel pairs hop), N(N-1)/4 for all-to-all couplings
+    f_off = a.n_sites * (a.n_sites - 1) / 4 if a.model == "xxz" else n_flip
     roof = {"kernel": "k_spmm (pass 1 + pass 2)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": _traffic_from_profiles() if (a.n_sites, a.k, a.n_v) == (22, 60, 32) else None,
+            "traffic": _traffic_from_profiles() if _bench_case(a) else None,
             "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": sp_bytes / max(1, sp_launch),
             "avg_launch_ms": sp_ms / max(1, sp_launch),
-            "operand_gbs": ((n_flip + 2) * blk) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None,
+            "operand_gbs": ((f_off + 2) * blk) / (sp_ms / sp_launch / 1000.0) / 1e9 if sp_ms > 0 else None,
             "share_of_timed_kernels": sp_ms / dev_ms_total if dev_ms_total else None}
     # Whole Lanczos step against the compulsory traffic of Algorithm 1 (read Q_{j-1},
     # Q_j, write Q_{j+1}: 3 blocks), and the SpMM's flops 2 D B (flips + 1) against the
@@ -361,7 +378,7 @@ def run_ours(a):
                     "frac": (step_c / (step_ms / 1000.0) / 1e9) / peak if step_ms > 0 else None}
     sm_max = clk.get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    spmm_tflops = 2.0 * (1 << a.n_sites) * 4 * a.n_v * (n_flip + 1) / (sp_ms / sp_launch / 1000.0) / 1e12 \
+    spmm_tflops = 2.0 * (1 << a.n_sites) * cols * (f_off + 1) / (sp_ms / sp_launch / 1000.0) / 1e12 \
         if sp_ms > 0 else None
     roof["spmm_fp32"] = {"tflops": spmm_tflops, "peak_tflops": fp32_peak,
                          "frac": spmm_tflops / fp32_peak if spmm_tflops else None}
