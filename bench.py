@@ -52,6 +52,10 @@ def _args():
     p.add_argument("--no-serving", action="store_true", help="skip the serving sub-benchmark")
     p.add_argument("--serving-requests", type=int, default=32)
     p.add_argument("--no-small", action="store_true", help="skip the small-chain latency sub-benchmark")
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c5"],
+                   help="c2 = the benchmark line; c3 / c5 = one full-size solve of the long-range "
+                        "XXZ configurations (25 spins, 64 vectors, 32 betas; 30 spins, 4 vectors) "
+                        "timed once, one JSON line")
     p.add_argument("--model", default="tfim", choices=["tfim", "xxz"],
                    help="profiling cases only: xxz = long-range XXZ (J/|i-j|, Delta=1, h=0.1, N_s=1, "
                         "Rademacher), the all-to-all XX+YY shape of the 25- and 30-spin configurations")
@@ -570,10 +574,45 @@ def _traffic_from_profiles():
     return None
 
 
+def run_config(a):
+    """One full-size solve of c3 or c5 (float32, the basis recomputed in pass 2 since it
+    does not fit), timed on the host around the blocking call, with the per-kernel
+    split from rdm_profile."""
+    from paper_2204_08147_gb300 import rdm
+    cfg = W.config_c3() if a.config == "c3" else W.config_c5()
+    ctx = rdm.Context(0)
+    ham = rdm.Hamiltonian(ctx, cfg["spec"])
+    ctx.profile(True)
+    ctx.synchronize()
+    t0 = time.perf_counter()
+    out = ham.estimate(cfg["betas"], cfg["n_v"], cfg["k"], cfg["seed"], precision="fp32", dist=cfg["dist"])
+    secs = time.perf_counter() - t0
+    st = ctx.profile_stats()
+    ctx.profile(False)
+    sp = [st[k] for k in ("spmm_pass1", "spmm_pass2") if k in st]
+    rho = out["rho"]
+    names = {"c3": "lr_xxz_N25_alpha1_delta1_h0.1_Ns1_nv64_k80_32beta_fp32",
+             "c5": "lr_xxz_N30_alpha1.5_delta0.5_Ns1_nv4_k50_beta2_fp32"}
+    line = {"config": a.config, "workload": names[a.config], "n_sites": cfg["spec"].n_sites,
+            "n_v": cfg["n_v"], "k": cfg["k"], "n_beta": len(cfg["betas"]), "dtype": "f32",
+            "seconds_per_solve": secs,
+            "spmm_launches": sum(x["launches"] for x in sp),
+            "spmm_ms_per_launch": sum(x["ms"] for x in sp) / max(1, sum(x["launches"] for x in sp)),
+            "kernel_ms": {k: round(v["ms"], 1) for k, v in st.items() if v["launches"]},
+            "trace_minus_1": float(np.abs(np.trace(rho, axis1=1, axis2=2) - 1).max()),
+            "min_eig_rho": float(min(np.linalg.eigvalsh(r).min() for r in rho))}
+    print(json.dumps(line))
+    ham.close()
+    ctx.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.config != "c2":
+        return run_config(a)
     return run_ours(a)
 
 
