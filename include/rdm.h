@@ -46,7 +46,9 @@ typedef enum {
 
 /* Arithmetic of the Lanczos vectors and the matrix-free SpMM. Recurrence
  * scalars, the eigendecomposition of T, exp(-beta T/2), the Gram and ln Z are
- * float64 in both modes. */
+ * float64 in both modes; with RDM_FP32 the inner products behind the Gram are
+ * summed in float32 within a thread and a warp (the vectors' own precision) and in
+ * float64 across warps and blocks. */
 enum { RDM_FP64 = 0, RDM_FP32 = 1 };
 
 /* Distribution of the bath vectors |v_l> (Sec. 3.1, eq. trace_est), drawn from a
