@@ -327,6 +327,13 @@ rdm_status rdm_entropy(const double* rho, int d_s, double* s_out);
 rdm_status rdm_function_of_t(int n, int p, const double* t, int n_beta, const double* betas,
                              double* t_min, double* c);
 
+/* rdm_function_of_t for n_mat matrices at once (t: n_mat*n*n, t_min: n_mat,
+ * c: n_mat*n_beta*n*p), spread over the host worker pool that rdm_estimate's small
+ * dense step uses; several callers may run at once. Same per-matrix results as
+ * rdm_function_of_t; RDM_ENUMERIC names the first matrix that did not converge. */
+rdm_status rdm_function_of_t_batch(int n_mat, int n, int p, const double* t, int n_beta,
+                                   const double* betas, double* t_min, double* c);
+
 /* Eigendecomposition of a dense symmetric n x n matrix (row-major a), used by
  * the small dense step of the estimator: w ascending (n), v (n*n, row-major,
  * column j = eigenvector j; NULL for values only). Host float64. */

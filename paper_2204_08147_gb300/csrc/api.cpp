@@ -961,6 +961,36 @@ static void parallel_for(int n, F&& f) {
   HostPool::get().run(n, fn);
 }
 
+extern "C" rdm_status rdm_function_of_t_batch(int n_mat, int n, int p, const double* t, int n_beta,
+                                              const double* betas, double* t_min, double* c) {
+  if (n_mat < 1 || n < 1 || n > 8192 || p < 1 || p > n || n_beta < 1 || !t || !betas || !t_min || !c) {
+    set_error("rdm_function_of_t_batch: need n_mat >= 1, 1 <= p <= n <= 8192, n_beta >= 1, non-NULL arrays");
+    return RDM_EINVAL;
+  }
+  for (int b = 0; b < n_beta; ++b)
+    if (!(betas[b] >= 0.0) || !std::isfinite(betas[b])) {
+      set_error("rdm_function_of_t_batch: beta[%d] must be finite and >= 0", b);
+      return RDM_EINVAL;
+    }
+  const size_t nn = (size_t)n * n;
+  for (size_t i = 0; i < nn * (size_t)n_mat; ++i)
+    if (!std::isfinite(t[i])) {
+      set_error("rdm_function_of_t_batch: T has a non-finite entry");
+      return RDM_EINVAL;
+    }
+  std::vector<char> ok(n_mat, 1);
+  const size_t cstride = (size_t)n_beta * n * p;
+  parallel_for(n_mat, [&](int r) {
+    ok[r] = tdense_fT(n, p, t + r * nn, n_beta, betas, &t_min[r], c + r * cstride) ? 1 : 0;
+  });
+  for (int r = 0; r < n_mat; ++r)
+    if (!ok[r]) {
+      set_error("rdm_function_of_t_batch: QR iteration did not converge on matrix %d", r);
+      return RDM_ENUMERIC;
+    }
+  return RDM_OK;
+}
+
 rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
                          const double* betas, int n_beta, int n_v, int k, uint64_t seed,
                          const rdm_opts* o, rdm_result* out, Profiler* prof) {

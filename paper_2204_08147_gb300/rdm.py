@@ -87,6 +87,7 @@ _sig("rdm_mean_force_abs", C.c_int, _dp, C.c_int, C.c_double, C.c_double, C.c_do
 _sig("rdm_energy_deviation", C.c_int, _dp, _dp, _dp, C.c_int, C.c_double, _dp)
 _sig("rdm_entropy", C.c_int, _dp, C.c_int, _dp)
 _sig("rdm_function_of_t", C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _dp)
+_sig("rdm_function_of_t_batch", C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _dp)
 _sig("rdm_symmetric_eig", C.c_int, C.c_int, _dp, _dp, _dp)
 _sig("rdm_serve_start", C.c_int, _vp, C.c_size_t, C.c_int)
 _sig("rdm_serve_stop", C.c_int, _vp)
@@ -441,6 +442,19 @@ def function_of_t(t: np.ndarray, p: int, betas) -> tuple:
     _check(_lib.rdm_function_of_t(n, int(p), _ptr(m), len(b), _ptr(b), C.byref(tmin), _ptr(c)),
            "rdm_function_of_t")
     return tmin.value, c
+
+
+def function_of_t_batch(ts: np.ndarray, p: int, betas) -> tuple:
+    """function_of_t for a stack of matrices ts (n_mat, n, n) on the host worker pool:
+    (t_min (n_mat,), c (n_mat, n_beta, n, p))."""
+    m = np.ascontiguousarray(ts, dtype=np.float64)
+    n_mat, n = m.shape[0], m.shape[1]
+    b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
+    c = np.zeros((n_mat, len(b), n, p))
+    tmin = np.zeros(n_mat)
+    _check(_lib.rdm_function_of_t_batch(n_mat, n, int(p), _ptr(m), len(b), _ptr(b), _ptr(tmin), _ptr(c)),
+           "rdm_function_of_t_batch")
+    return tmin, c
 
 
 def symmetric_eig(a: np.ndarray, vectors: bool = True):

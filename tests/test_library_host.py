@@ -119,6 +119,39 @@ def test_function_of_t_degenerate_and_errors(rdm):
         assert e.value.status == rdm.EINVAL
 
 
+def test_function_of_t_batch_on_the_worker_pool(rdm):
+    """The batched small dense step (the host worker pool) equals the one-matrix call
+    bit for bit, also with several callers running jobs on the pool at once."""
+    import threading
+    rng = np.random.default_rng(11)
+    ts = np.stack([_block_tridiagonal(rng, 4, 20) for _ in range(13)])
+    betas = [0.5, 2.0]
+    ref = [rdm.function_of_t(t, 4, betas) for t in ts]
+    tmin, c = rdm.function_of_t_batch(ts, 4, betas)
+    for r, (tm, cr) in enumerate(ref):
+        assert tmin[r] == tm
+        np.testing.assert_array_equal(c[r], cr)
+    outs, errs = [None] * 6, []
+
+    def worker(i):
+        try:
+            outs[i] = rdm.function_of_t_batch(ts[i:i + 8], 4, betas)
+        except Exception as e:  # noqa: BLE001
+            errs.append(e)
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(6)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs
+    for i, (tm, cc) in enumerate(outs):
+        np.testing.assert_array_equal(tm, tmin[i:i + 8])
+        np.testing.assert_array_equal(cc, c[i:i + 8])
+    with pytest.raises(rdm.RdmError) as e:
+        rdm.function_of_t_batch(np.full((2, 3, 3), np.nan), 1, [1.0])
+    assert e.value.status == rdm.EINVAL
+
+
 def test_mean_force_and_entropy_match_oracle(rdm):
     from oracle import post
     rng = np.random.default_rng(2)
