@@ -501,48 +501,34 @@ def small_chain_bench(rdm, ctx, n_solves: int = 50) -> dict:
             "host_small_dense_us_per_solve": 1e3 * host["ms"] / n_prof if host else None}
 
 
-def _partner_tiles(spec, tile_bits: int = 10) -> int:
-    """Distinct nonzero high parts (mask >> tile_bits) of the flip masks of a model:
-    the partner tiles one 1024-state tile of the tiled SpMM needs (site q is bit N-1-q;
-    X on one site and XX/YY on a pair flip those bits)."""
+def _partner_tiles(spec, tile_bits: int = 10) -> float:
+    """Partner tiles one 1024-state tile of the tiled SpMM copies, on average over tiles.
+    Flip masks are grouped by their high part (mask >> tile_bits; site q is bit N-1-q;
+    X on one site and XX/YY on a pair flip those bits). A group is copied by every tile
+    unless all its masks lie above the tile bits and its one coefficient depends on the
+    parity of the flipped spins (c_odd or c_even zero, e.g. XX+YY with J^x = J^y, which
+    only hops antiparallel pairs): then only the tiles where that parity gives a nonzero
+    coefficient copy it, half of them."""
     n = spec.n_sites
-    highs = set()
+    groups = {}
     for q in range(n):
         if spec.gx[q] != 0:
-            highs.add((1 << (n - 1 - q)) >> tile_bits)
+            m = 1 << (n - 1 - q)
+            groups.setdefault(m >> tile_bits, []).append((m, 1.0, 1.0))
     for i in range(n):
         for j in range(i + 1, n):
-            if spec.jx[i, j] != 0 or spec.jy[i, j] != 0:
-                highs.add(((1 << (n - 1 - i)) | (1 << (n - 1 - j))) >> tile_bits)
-    highs.discard(0)
-    return len(highs)
-
-
-def sweep_bench(rdm, ctx) -> dict:
-    """A parameter sweep shaped like the paper's entropy phase plot (Sec. 5.3.1):
-    long-range XY chain N=16, J/|i-j|, N_s=2, field h over 8 values in [0, 2.2],
-    n_v=400 Gaussian bath vectors, k=60, 8 betas in [0.5, 4], float32; one solve per
-    h value, back to back (each solve's Krylov block is 2^16 x 1600 columns)."""
-    hs = np.linspace(0.0, 2.2, 8)
-    betas = W.beta_grid(8, 0.5, 4.0)
-    hams = [rdm.Hamiltonian(ctx, W.long_range_xxz(16, 2, alpha=1.0, delta=0.0, h=float(h), lam=1.0)) for h in hs]
-
-    def one(i):
-        return hams[i].estimate(betas, 400, 60, 20220421, precision="fp32", dist="gauss")
-    one(0)
-    ctx.synchronize()
-    lat = []
-    t0 = time.perf_counter()
-    for i in range(len(hs)):
-        t1 = time.perf_counter()
-        one(i)
-        lat.append(time.perf_counter() - t1)
-    wall = time.perf_counter() - t0
-    for h in hams:
-        h.close()
-    return {"workload": "lr_xy_N16_Ns2_alpha1_h0-2.2x8_nv400_k60_8beta_fp32", "solves": len(hs),
-            "solves_per_s": len(hs) / wall, "ms_per_solve_p50": 1000 * float(np.percentile(lat, 50)),
-            "block_mb": (1 << 16) * 1600 * 4 / 1e6}
+            jx, jy = spec.jx[i, j], spec.jy[i, j]
+            if jx != 0 or jy != 0:
+                m = (1 << (n - 1 - i)) | (1 << (n - 1 - j))
+                groups.setdefault(m >> tile_bits, []).append((m, jx + jy, jx - jy))
+    total = 0.0
+    for h, terms in groups.items():
+        if h == 0:
+            continue
+        low_free = all((m & ((1 << tile_bits) - 1)) == 0 for m, _, _ in terms)
+        parity_only = len(terms) == 1 and (terms[0][1] == 0 or terms[0][2] == 0)
+        total += 0.5 if (low_free and parity_only) else 1.0
+    return total
 
 
 def spmm_source_hash() -> str:

@@ -22,14 +22,19 @@ def bench():
 
 
 def test_partner_tiles(bench):
-    """Distinct high parts of the flip masks with 1024-state tiles: 12 single-site flips
-    for the 22-spin transverse-field model; C(12,2) + 12 = 78 and C(15,2) + 15 = 120
-    pair patterns for all-to-all XX+YY on 22 and 25 spins; none for a 10-spin chain."""
+    """Partner tiles per 1024-state tile: the 12 single-site flips above the tile bits of
+    the 22-spin transverse-field model, every tile; for all-to-all XX+YY (J^x = J^y) the
+    12 (15) groups of one high and one low spin, every tile, plus the C(12,2) = 66
+    (C(15,2) = 105) pairs of high spins, each copied only by the half of the tiles where
+    the two spins differ; none for a 10-spin chain (all flips inside the tile)."""
     import workloads as W
     assert bench._partner_tiles(W.config_c2(0)["spec"]) == 12
-    assert bench._partner_tiles(W.long_range_xxz(22, 1, 1.0, 1.0, 0.1)) == 78
-    assert bench._partner_tiles(W.config_c3()["spec"]) == 120
+    assert bench._partner_tiles(W.long_range_xxz(22, 1, 1.0, 1.0, 0.1)) == 12 + 66 / 2
+    assert bench._partner_tiles(W.config_c3()["spec"]) == 15 + 105 / 2
     assert bench._partner_tiles(W.config_c1()["spec"]) == 0
+    spec = W.long_range_xxz(22, 1, 1.0, 1.0, 0.1)
+    spec.jy[:] = 0.5 * spec.jx  # J^x != J^y: every pair hops, every tile copies it
+    assert bench._partner_tiles(spec) == 12 + 66
 
 
 def test_both_arms_describe_the_same_workload(bench):
