@@ -43,6 +43,10 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--oracle-cores", type=int, default=0,
+                   help="worker processes timing the oracle (0 = every host core the memory allows)")
+    p.add_argument("--ref-steps", type=int, default=2,
+                   help="reference arm: Lanczos steps per bath vector in one timed step")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 one-vector form")
     p.add_argument("--n-sites", type=int, default=22,
                    help="spins of the workload (22 = the benchmark; smaller only for profiling)")
@@ -71,46 +75,94 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# ---------------------------------------------------------------- oracle sample (CPU)
+# ---------------------------------------------------------------- oracle timing (CPU)
+#
+# The oracle (float64 NumPy, one recurrence per process) is timed on the host's cores:
+# a pool of worker processes (started with `spawn`, one thread each) runs Lanczos steps
+# of different bath vectors of the workload side by side. A solve of the workload is
+# n_v vectors x (k steps of the first pass + k steps of the Gram-form rerun), so a
+# sample of `steps` steps on C vectors at once, taking `wall` seconds, extrapolates to
+#     seconds per solve = t_setup + n_v * 2k * wall / (C * steps),
+# t_setup being the oracle's operator build for one Hamiltonian (one core).
 
-_ORACLE_SAMPLE = r"""
-import json, sys, time
-sys.path.insert(0, {root!r})
-import workloads as W
-from oracle import lanczos, spin_ops
-c = W.config_c2(0)
-t0 = time.perf_counter()
-ham = spin_ops.TensorHamiltonian(c["spec"])
-ham.diagonal()
-t_setup = time.perf_counter() - t0
-est = lanczos.Estimator(c["spec"], apply_h=ham, hnorm=ham.norm_bound())
-v = est.starting_block(0, c["seed"], c["dist"])
-steps = {steps}
-t0 = time.perf_counter()
-for j, q, a, b in lanczos.block_lanczos(ham, v, steps, est.hnorm):
-    pass
-t_steps = time.perf_counter() - t0
-print(json.dumps(dict(t_setup=t_setup, t_step=t_steps / steps, steps=steps)))
-"""
+_ORACLE = {}
 
 
-def oracle_sample(steps: int) -> dict:
-    """Runs `steps` Lanczos steps of one bath vector of the workload with the oracle,
-    single-threaded, in a fresh interpreter (no CUDA in it)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", _ORACLE_SAMPLE.format(root=ROOT, steps=steps)],
-                       capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def _oracle_init():
+    import workloads as W_
+    from oracle import lanczos, spin_ops
+    c = W_.config_c2(0)
+    t0 = time.perf_counter()
+    ham = spin_ops.TensorHamiltonian(c["spec"])
+    ham.diagonal()
+    _ORACLE.update(t_setup=time.perf_counter() - t0, c=c,
+                   est=lanczos.Estimator(c["spec"], apply_h=ham, hnorm=ham.norm_bound()))
 
 
-def oracle_solves_per_s(sample: dict) -> float:
-    """One solve = n_v vectors x (k steps of pass 1 + k steps of the Gram-form rerun)."""
-    c = W.config_c2(0)
-    per_solve = sample["t_setup"] + sample["t_step"] * c["n_v"] * 2 * c["k"]
-    return 1.0 / per_solve
+def _oracle_task(args):
+    l, steps = args
+    from oracle import lanczos
+    c, est = _ORACLE["c"], _ORACLE["est"]
+    v = est.starting_block(l, c["seed"], c["dist"])
+    t0 = time.perf_counter()
+    for _ in lanczos.block_lanczos(est.apply_h, v, steps, est.hnorm):
+        pass
+    return time.perf_counter() - t0, _ORACLE["t_setup"]
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _mem_available_gb() -> float:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 64.0
+
+
+class OraclePool:
+    """Worker processes running the oracle on bath vectors of the workload, one
+    vector per worker. Each worker holds about 1 GB (the N = 22 blocks in float64), so
+    the count is bounded by the free host memory as well as by the cores."""
+
+    GB_PER_WORKER = 2.5
+
+    def __init__(self, cores: int | None = None):
+        import multiprocessing as mp
+        avail = host_cores()
+        n = cores if cores else avail
+        n = max(1, min(n, avail, int(_mem_available_gb() / self.GB_PER_WORKER) or 1))
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.cores = n
+        self.pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init)
+        self.t_setup = None
+
+    def sample(self, steps: int) -> dict:
+        """`steps` Lanczos steps on each of `cores` bath vectors at once."""
+        n_v = W.config_c2(0)["n_v"]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_task, [(i % n_v, steps) for i in range(self.cores)], chunksize=1)
+        wall = time.perf_counter() - t0
+        self.t_setup = max(r[1] for r in res)
+        return {"wall": wall, "steps": steps, "vectors": self.cores, "t_setup": self.t_setup}
+
+    def solves_per_s(self, s: dict) -> float:
+        c = W.config_c2(0)
+        per_solve = s["t_setup"] + c["n_v"] * 2 * c["k"] * s["wall"] / (s["vectors"] * s["steps"])
+        return 1.0 / per_solve
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def _bench_case(a) -> bool:
@@ -129,26 +181,42 @@ def _config(a, world: int) -> dict:
 
 
 def run_reference(a):
+    """The oracle timed on the host cores (the reference arm: the paper has no code).
+    Each step is a bounded sample of the workload: `--ref-steps` Lanczos steps of the
+    first pass on one bath vector per core, all cores at once. `ms_per_step` is the wall
+    time of those samples as run; `value` is the solves/s they extrapolate to (labelled
+    in `value_kind`). Under torchrun only rank 0 works."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    for _ in range(a.warmup):
-        oracle_sample(1)
-    t0 = time.perf_counter()
-    samples = [oracle_sample(2) for _ in range(a.steps)]
-    wall = time.perf_counter() - t0
-    rates = [oracle_solves_per_s(s) for s in samples]
+    t_start = time.perf_counter()
+    pool = OraclePool(a.oracle_cores)
+    try:
+        pool.sample(1)  # starts the workers (operator build), not timed
+        for _ in range(a.warmup):
+            pool.sample(a.ref_steps)
+        samples = [pool.sample(a.ref_steps) for _ in range(a.steps)]
+    finally:
+        pool.close()
+    walls = [s["wall"] for s in samples]
+    rates = [pool.solves_per_s(s) for s in samples]
     value = statistics.median(rates)
+    c = W.config_c2(0)
+    sample = (f"per step: {a.ref_steps} Lanczos steps (first pass) on each of {pool.cores} bath vectors at "
+              f"once, one per worker process, at full size (D=2^22, 4 columns, float64 NumPy); "
+              f"extrapolated to {c['n_v']} vectors x 2 x {c['k']} steps per solve plus the operator build "
+              f"({pool.t_setup:.1f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / value,
+        "value_kind": "extrapolated from the timed samples (see cpu_baseline.sample)",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(a, int(os.environ.get("WORLD_SIZE", "1"))),
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step: 2 Lanczos steps of bath vector 0 at full size "
-                                   "(D=2^22, 4 columns, float64 NumPy), scaled to 32 vectors x "
-                                   "2 x 60 steps per solve", "wall_s": wall},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": sample, "host_cores": host_cores()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_start,
     }
     print(json.dumps(line))
     return 0
@@ -220,11 +288,19 @@ def run_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    torch.cuda.set_device(local)
 
-    cpu_sample = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu_sample = oracle_sample(5)  # before any CUDA work in this process
+    # The oracle's CPU baseline: worker processes started with spawn, before this
+    # process makes its first CUDA call; a bounded sample (one warm step, then 5 timed
+    # Lanczos steps on one bath vector per core).
+    cpu_sample = cpu_pool = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and _bench_case(a):
+        cpu_pool = OraclePool(a.oracle_cores)
+        try:
+            cpu_pool.sample(1)
+            cpu_sample = cpu_pool.sample(5)
+        finally:
+            cpu_pool.close()
+    torch.cuda.set_device(local)
 
     from paper_2204_08147_gb300 import rdm
     ctx = rdm.Context(local)
@@ -238,7 +314,6 @@ def run_ours(a):
             c["k"] = a.k
             c["n_v"] = a.n_v
     hams = [rdm.Hamiltonian(ctx, c["spec"]) for c in cfgs]
-    c0 = cfgs[0]
 
     def solve(i):
         c = cfgs[i % N_G]
@@ -253,8 +328,9 @@ def run_ours(a):
     props = torch.cuda.get_device_properties(local)
     uuid = str(getattr(props, "uuid", "")) or None
     clocks = Clocks(uuid)
-    # The context runs on torch's current stream, so these events bracket its work.
-    ctx.profile(True)
+    # The timed region runs the library's default path (graph replay of the first pass,
+    # no per-launch events). The context runs on torch's current stream, so these
+    # events bracket its work.
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -272,12 +348,20 @@ def run_ours(a):
     ctx.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    stats = ctx.profile_stats()
-    ctx.profile(False)
     if dist:
         t = torch.tensor([ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+
+    # Per-kernel split: the same solves again with per-launch CUDA events on the
+    # launching stream (rdm_profile; graphs are not replayed while it records).
+    n_prof = max(1, min(a.steps, 8))
+    ctx.profile(True)
+    for i in range(n_prof):
+        solve(base + a.warmup + i)
+    ctx.synchronize()
+    stats = ctx.profile_stats()
+    ctx.profile(False)
     total_solves = a.steps * world
     value = total_solves / (ms / 1000.0)
 
@@ -397,7 +481,9 @@ def run_ours(a):
                               "tiles_per_tile": units, "dram_to_smem_probe": dram_rate,
                               "peak_kind": "probe: rdm_probe_copy_rate, 32 MB L2-resident buffer, 32 KB "
                                            "bulk copies, 6 in flight per SM"}
-    launches = sum(s["launches"] for s in stats.values())
+    # launches of the library's kernels in the timed region: the profiled pass runs the
+    # same solves' launch sequence (graph replay launches the same kernel nodes)
+    launches = int(round(sum(s["launches"] for s in stats.values()) * a.steps / n_prof))
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -408,7 +494,9 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": launches,
-        "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["launches"]},
+        "kernel_ms_per_solve": {k: round(v["ms"] / n_prof, 3) for k, v in stats.items() if v["launches"]},
+        "kernel_split": f"per-launch CUDA events on the launching stream over {n_prof} profiled solves "
+                        f"run after the timed region (same workload)",
         "host_small_dense_ms_per_solve": (host_dense["ms"] / host_dense["launches"])
         if host_dense and host_dense["launches"] else None,
         "roofline": roof,
@@ -419,11 +507,13 @@ def run_ours(a):
         "sweep": sweep,
     }
     if cpu_sample is not None:
-        line["cpu_baseline"] = {"value": oracle_solves_per_s(cpu_sample), "unit": "solves/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": "5 Lanczos steps of bath vector 0 at full size (D=2^22, "
-                                          "float64 NumPy, 1 thread), scaled to 32 vectors x 2 x 60 "
-                                          "steps per solve"}
+        c = W.config_c2(0)
+        line["cpu_baseline"] = {
+            "value": cpu_pool.solves_per_s(cpu_sample), "unit": "solves/s", "cores": cpu_pool.cores,
+            "kind": "oracle", "host_cores": host_cores(), "wall_s": cpu_sample["wall"],
+            "sample": f"5 Lanczos steps (first pass) on each of {cpu_pool.cores} bath vectors at once, one "
+                      f"per worker process, at full size (D=2^22, float64 NumPy), extrapolated to "
+                      f"{c['n_v']} vectors x 2 x {c['k']} steps per solve plus the operator build"}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -531,6 +621,33 @@ def _partner_tiles(spec, tile_bits: int = 10) -> float:
     return total
 
 
+def sweep_bench(rdm, ctx) -> dict:
+    """A parameter sweep shaped like the paper's entropy phase plot (Sec. 5.3.1):
+    long-range XY chain N=16, J/|i-j|, N_s=2, field h over 8 values in [0, 2.2],
+    n_v=400 Gaussian bath vectors, k=60, 8 betas in [0.5, 4], float32; one solve per
+    h value, back to back (each solve's Krylov block is 2^16 x 1600 columns)."""
+    hs = np.linspace(0.0, 2.2, 8)
+    betas = W.beta_grid(8, 0.5, 4.0)
+    hams = [rdm.Hamiltonian(ctx, W.long_range_xxz(16, 2, alpha=1.0, delta=0.0, h=float(h), lam=1.0)) for h in hs]
+
+    def one(i):
+        return hams[i].estimate(betas, 400, 60, 20220421, precision="fp32", dist="gauss")
+    one(0)
+    ctx.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(len(hs)):
+        t1 = time.perf_counter()
+        one(i)
+        lat.append(time.perf_counter() - t1)
+    wall = time.perf_counter() - t0
+    for h in hams:
+        h.close()
+    return {"workload": "lr_xy_N16_Ns2_alpha1_h0-2.2x8_nv400_k60_8beta_fp32", "solves": len(hs),
+            "solves_per_s": len(hs) / wall, "ms_per_solve_p50": 1000 * float(np.percentile(lat, 50)),
+            "block_mb": (1 << 16) * 1600 * 4 / 1e6}
+
+
 def spmm_source_hash() -> str:
     """sha256 (16 hex) of the tiled SpMM's source: its region of kernels.cu plus the
     layout constants header. A committed DRAM-traffic figure is only reported while
@@ -593,8 +710,32 @@ def run_config(a):
     return 0
 
 
+def _launch_ranks(a) -> int | None:
+    """`--gpus N` outside torchrun: re-run this command under torch.distributed.run with
+    N ranks on this node (127.0.0.1 rendezvous) and return its exit code. Under torchrun
+    the world size must equal N."""
+    world = os.environ.get("WORLD_SIZE")
+    if world is not None:
+        if int(world) != a.gpus:
+            sys.stderr.write(f"bench.py: --gpus {a.gpus} but WORLD_SIZE={world}\n")
+            return 2
+        return None
+    if a.gpus <= 1:
+        return None
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={a.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     a = _args()
+    rc = _launch_ranks(a)
+    if rc is not None:
+        return rc
     if a.impl == "reference":
         return run_reference(a)
     if a.config != "c2":

@@ -174,7 +174,9 @@ rdm_status rdm_synchronize(rdm_ctx* ctx);
  * stays in L2 (the L2 -> shared-memory rate, the level that feeds the tiled SpMM's
  * partner tiles); a buffer larger than L2 gives the DRAM -> shared-memory rate.
  * Allocates and frees its buffer; synchronous. RDM_ENOMEM if the buffer does not fit,
- * RDM_ECUDA if a copy wait gave up. The paper has no counterpart: this is the
+ * RDM_ECUDA if a copy wait gave up (a copy may then still be in flight into shared
+ * memory: destroy the context rather than time anything further on it). The paper
+ * has no counterpart: this is the
  * denominator of the SpMM's on-chip roofline. */
 rdm_status rdm_probe_copy_rate(rdm_ctx* ctx, size_t buffer_bytes, int stages, double* gbs);
 
@@ -276,11 +278,14 @@ rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, uint64_t see
  * synchronise the device. Same arguments, layout and result as
  * rdm_starting_block; x is still caller-owned device memory.
  * Scratch: the Gaussian vectors' norms use a fixed device array of this library
- * (1024 * 65 float64 = 532,480 bytes), which every GPU that loads the library
- * holds until the process exits. n_v may be at most 1024: larger n_v returns
- * RDM_EINVAL. The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before any
- * stream capture. All calls share the one array: calls whose device work overlaps
+ * (32 * 65 float64 = 16,640 bytes), which every GPU that loads the library holds
+ * until the process exits. n_v may be at most 32 (the most the column rule allows:
+ * d_s * n_v <= 32 float32 columns with d_s = 1); larger n_v returns RDM_EINVAL, as
+ * does any n_v whose d_s * n_v columns break the column rule. The first call on a
+ * device looks up the array's device address (once per device, with that device
+ * current) and caches it for the life of the process; make that first call before
+ * any stream capture, and do not use this entry point after a cudaDeviceReset of
+ * that device (the array may move). All calls share the one array: calls whose device work overlaps
  * (different streams, or different contexts on the same device) race on it and
  * must be ordered by the caller. Each call writes every scratch entry it reads,
  * so no clearing is needed between calls. */

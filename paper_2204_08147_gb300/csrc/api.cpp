@@ -341,6 +341,10 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
 
 // Layout of a caller's single-slice block of n_cols columns (apply / starting block).
 static rdm_status plan_single(const HostModel& h, int n_cols, int precision, int ds, Layout* L) {
+  if (precision != RDM_FP32 && precision != RDM_FP64) {
+    set_error("bad precision %d (RDM_FP64 or RDM_FP32)", precision);
+    return RDM_EINVAL;
+  }
   Layout l{};
   l.n_bits = h.n;
   l.n_bath_bits = h.n - h.ns;

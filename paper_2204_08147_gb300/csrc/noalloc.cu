@@ -9,7 +9,10 @@
 // holds it (kNoAllocScratchBytes) until the process exits. In host code the name
 // g_noalloc_scratch is only a host-side stand-in for the symbol, not a device
 // address: its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached.
+// cudaGetSymbolAddress (with that device current) and cached for the life of the
+// process. A cudaDeviceReset (or any teardown of the device's primary context)
+// reloads the module, possibly at another address, so the cache is only valid
+// while the context that looked it up lives.
 #include <mutex>
 
 #include "rdm_api_internal.h"
@@ -18,8 +21,10 @@ namespace rdm {
 namespace {
 
 // Largest n_v the variant accepts, and the scratch it needs: n_v * 64 per-block
-// partial sums plus n_v inverse norms, float64.
-constexpr int kNoAllocMaxVectors = 1024;
+// partial sums plus n_v inverse norms, float64. The column rule of the starting block
+// (d_s * n_v columns, at most 32 float32 or 16 float64) already caps n_v at 32 (float32
+// with d_s = 1), so the array is sized for exactly that.
+constexpr int kNoAllocMaxVectors = 32;
 constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocMaxVectors * 65;
 constexpr size_t kNoAllocScratchBytes = kNoAllocScratchDoubles * sizeof(double);
 

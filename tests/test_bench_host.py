@@ -53,8 +53,8 @@ def test_reference_arm_prints_the_contract_line():
     contract's keys (one bounded sample: about ten seconds of CPU)."""
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env,
-                       timeout=900, cwd=ROOT)
+                        "--steps", "2", "--warmup", "0", "--oracle-cores", "2", "--ref-steps", "1"],
+                       capture_output=True, text=True, env=env, timeout=900, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -67,3 +67,17 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "lr_tfim_N22_Ns2_nv32_k60_beta1_fp32"
+    # the steps it reports were run: their time fits the run's own wall time
+    assert d["steps"] == 2 and d["ms_per_step"] * d["steps"] <= 1000.0 * d["wall_s"]
+    assert d["cpu_baseline"]["cores"] == 2
+
+
+def test_world_size_must_match_gpus(bench, monkeypatch):
+    """Under torchrun `--gpus N` must equal the world size; outside it N = 1 runs here."""
+    a = types.SimpleNamespace(gpus=2)
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    assert bench._launch_ranks(a) == 2
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench._launch_ranks(a) is None
+    monkeypatch.delenv("WORLD_SIZE")
+    assert bench._launch_ranks(types.SimpleNamespace(gpus=1)) is None

@@ -30,10 +30,16 @@ def test_noalloc_starting_block_matches_allocating_entry_point(lib, dist):
                 ham.starting_block_noalloc(got, n_v, seed, dist)
                 torch.cuda.synchronize()
                 np.testing.assert_allclose(got.cpu().numpy(), ref.cpu().numpy(), rtol=rtol, atol=0)
-        big = torch.empty((1 << 10, 4 * 2048), dtype=torch.float32, device="cuda")
+        # beyond the scratch's 32 vectors
+        big = torch.empty((1 << 10, 4 * 64), dtype=torch.float32, device="cuda")
         with pytest.raises(lib.RdmError) as e:
-            ham.starting_block_noalloc(big, 2048, 1, dist)
+            ham.starting_block_noalloc(big, 64, 1, dist)
         assert e.value.status == lib.EINVAL and "maximum" in str(e.value)
+        # within the scratch but beyond the column rule (float64, 4 * 8 = 32 > 16 columns)
+        wide = torch.empty((1 << 10, 4 * 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(lib.RdmError) as e:
+            ham.starting_block_noalloc(wide, 8, 1, dist)
+        assert e.value.status == lib.EINVAL and "columns" in str(e.value)
         ham.close()
     finally:
         ctx.close()
