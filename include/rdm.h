@@ -46,9 +46,12 @@ typedef enum {
 
 /* Arithmetic of the Lanczos vectors and the matrix-free SpMM. Recurrence
  * scalars, the eigendecomposition of T, exp(-beta T/2), the Gram and ln Z are
- * float64 in both modes; with RDM_FP32 the inner products behind the Gram are
- * summed in float32 within a thread and a warp (the vectors' own precision) and in
- * float64 across warps and blocks. */
+ * float64 in both modes. With RDM_FP32 the vectors, the SpMM and psi = Q c are
+ * float32 with float32 accumulation; the Gram psi^T psi (eq. rho_est) is accumulated
+ * in float64 from the first product on (a product of two float32 values is exact in
+ * float64); the inner products behind the recurrence scalars (A_j = Q_j^T Z and the
+ * QR Gram Z^T Z) are summed in float32 within a thread and a warp and in float64
+ * across warps and blocks, and everything after that is float64. */
 enum { RDM_FP64 = 0, RDM_FP32 = 1 };
 
 /* Distribution of the bath vectors |v_l> (Sec. 3.1, eq. trace_est), drawn from a
@@ -251,6 +254,41 @@ rdm_status rdm_hamiltonian_info(const rdm_ham* ham, int* n_sites, int* n_sys,
  * Blocking: returns when the results are in `out` (host). */
 rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta, int n_v, int k,
                         uint64_t seed, const rdm_opts* opts, rdm_result* out);
+
+/* One estimate of a batch (rdm_estimate_batch): the arguments of rdm_estimate, and the
+ * item's own status on return. */
+typedef struct {
+  rdm_ham* ham;          /* a Hamiltonian of the batch's context */
+  const double* betas;   /* n_beta values (host, caller-owned) */
+  int n_beta;
+  int n_v;
+  int k;
+  uint64_t seed;
+  rdm_opts opts;
+  rdm_result* out;       /* caller-owned results, as for rdm_estimate */
+  rdm_status status;     /* out: this item's status */
+} rdm_batch_item;
+
+/* Many estimates at once, of Hamiltonians of any sizes (the paper's independent
+ * recurrences of Sec. 3.1, over several models): every item that keeps its Krylov basis
+ * (k+1 blocks fit) and whose block is at most 64 MB runs its first pass (Algorithm 1's k
+ * steps) in ONE persistent cooperative launch with the other such items of its
+ * precision and d_s -- the SpMM, A_j, orthogonalisation and QR phases of every item,
+ * separated by grid barriers; larger items run as rdm_estimate does. Each work unit of
+ * that launch is one block of the plain kernels of its item, so an item's result does
+ * not depend on which other items share the batch (bit-identical alone or in any mix).
+ * Its launch shape (blocks per SM of the cooperative grid) is chosen by an autotuner:
+ * the first batch of each size class times the candidates (1, 2, 4, 8 blocks per SM, as
+ * many as fit) and the fastest is kept on the context; the shape changes no result.
+ * Items whose workspaces do not fit the device together run in consecutive
+ * sub-batches. Blocking. Returns RDM_OK when every item succeeded, else the first
+ * failure (each item's own status is in items[i].status); RDM_EINVAL for a NULL
+ * argument or an item of another context, RDM_ECUDA if a grid-barrier wait gave up. */
+rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, int n_items);
+
+/* The autotuner's state on a context: size classes tuned (*n_keys) and candidate
+ * launches timed so far (*tuning_runs). Either pointer may be NULL. */
+rdm_status rdm_packed_tuning(rdm_ctx* ctx, int* n_keys, uint64_t* tuning_runs);
 
 /* Y = H X for a caller-owned device block of n_cols columns stored state-major,
  * vector-minor (element (s, c) at s*n_cols + c), float64 (RDM_FP64) or float32

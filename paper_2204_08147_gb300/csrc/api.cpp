@@ -296,6 +296,15 @@ static int ilog2_exact(int64_t x) {
   return (int64_t(1) << r) == x ? r : -1;
 }
 
+// Blocks per slice of the plain (untiled) kernels: enough to cover the rows once with
+// kThreads / TPR rows per block, at most 1216 blocks over all slices.
+static int untiled_gridx(const Layout& L) {
+  const int rpb = kThreads / L.TPR;
+  const int64_t gx = (L.D + rpb - 1) / rpb;
+  const int64_t cap = std::max<int64_t>(1, 1216 / L.n_slices);
+  return (int)std::min(gx, cap);
+}
+
 // Chooses the slice geometry for n_v bath vectors of block size d_s.
 rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad, int rec_ds) {
   if (precision != RDM_FP32 && precision != RDM_FP64) {
@@ -329,10 +338,7 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
   l.B = bcols;
   l.n_slices = l.B / l.Bs;
   l.TPR = l.Bs / l.VW;
-  const int rpb = kThreads / l.TPR;
-  int64_t gx = (l.D + rpb - 1) / rpb;
-  const int64_t cap = std::max<int64_t>(1, 1216 / l.n_slices);
-  l.gridx = (int)std::min(gx, cap);
+  l.gridx = untiled_gridx(l);
   if (layout_tiled(l)) l.gridx = spmm_tiled_grid(l);  // the tiled SpMM's blocks per slice
   *L = l;
   *n_v_pad = l.B / l.DS;
@@ -402,7 +408,8 @@ static PlanSizes plan_sizes(const Plan& p) {
   const Layout& L = p.L;
   const Layout& G = p.Lg;
   const size_t rec = (size_t)L.n_groups() * L.DS * L.DS, view = (size_t)G.n_groups() * G.DS * G.DS;
-  const size_t prec = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * L.DS * L.DS;
+  // (the packed first pass runs the untiled grid on a tiled layout: room for both)
+  const size_t prec = (size_t)L.n_slices * std::max(L.gridx, untiled_gridx(L)) * L.groups_per_slice() * L.DS * L.DS;
   const size_t pview = (size_t)G.n_slices * G.gridx * G.groups_per_slice() * G.DS * G.DS;
   return PlanSizes{std::max(prec, pview) * 4, (size_t)p.k * p.nbc * std::max(rec, view),
                    (size_t)p.nbc * std::max(rec, view)};
@@ -995,20 +1002,102 @@ extern "C" rdm_status rdm_function_of_t_batch(int n_mat, int n, int p, const dou
   return RDM_OK;
 }
 
-rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
-                         const double* betas, int n_beta, int n_v, int k, uint64_t seed,
-                         const rdm_opts* o, rdm_result* out, Profiler* prof) {
-  const HostModel& hm = ham->model;
+// One rdm_estimate call in three stages: prepare() plans the workspace and issues the
+// per-estimate set-up (tables, bath vectors, starting block); pass1() runs Algorithm 1's
+// k steps (plain launches, or a graph replay), unless the caller runs them in a packed
+// launch with other estimates (packed_item()); finish() does the small dense step, the
+// Gram form and the normalisation, and fills `out`.
+class EstimateRun {
+ public:
+  EstimateRun(rdm_ham* ham_, cudaStream_t s_, const double* betas_, int n_beta_, int n_v_, int k_,
+              uint64_t seed_, const rdm_opts* o_, rdm_result* out_, Profiler* prof_)
+      : ham(ham_), hm(ham_->model), s(s_), betas(betas_), n_beta(n_beta_), n_v(n_v_), k(k_), seed(seed_),
+        o(o_), out(out_), prof(prof_) {}
+  rdm_status prepare(char* ws, size_t ws_bytes);
+  rdm_status pass1();
+  rdm_status finish();
+  // Whether the packed launch can take this estimate's first pass (stored basis, one
+  // recurrence of block size d_s per bath vector, a block of at most kPackedMaxBlock
+  // bytes), and its description for that launch.
+  bool packable() const;
+  PackedItem packed_item() const;
+  const Plan& plan() const { return p; }
+  bool packed_done = false;  // the first pass ran in a packed launch
+
+ private:
+  rdm_ham* ham;
+  const HostModel& hm;
+  cudaStream_t s;
+  const double* betas;
+  int n_beta, n_v, k;
+  uint64_t seed;
+  const rdm_opts* o;
+  rdm_result* out;
+  Profiler* prof;
+
   Plan p;
+  Layout L, Lg;
+  int ds = 0, nv = 0, ng = 0, dso = 0, nvo = 0, ngo = 0, sub = 1, n_rec = 0;
+  int64_t d_b = 0;
+  bool store = false;
+  int nblk = 0;
+  std::vector<char*> blk;
+  char* psi = nullptr;
+  PlanSizes psz{};
+  size_t pstride = 0, pstride_g = 0, cstride = 0;
+  double* partials = nullptr;
+  double* coef = nullptr;
+  double* d_ta = nullptr;
+  double* d_tb = nullptr;
+  double* d_e = nullptr;
+  double* d_gram = nullptr;
+  double* d_norm = nullptr;
+  uint32_t* d_flags = nullptr;
+  char* d_tk = nullptr;
+  char* d_vbuf = nullptr;
+  double* d_graw = nullptr;
+  double thr_abs_sq = 0, thr_rel_sq = 0;
+  SpmmArgs sa{};
+  double blk_b = 0;
+  uint64_t h2d = 0, d2h = 0;
+  int cur = 0, prv = -1, nxt = 1;
+
+  double* MZ(int j) const { return coef + (size_t)j * cstride; }  // j = 1..k+1
+  double* CP(int j) const { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; }
+  double* CW(int j) const { return coef + (size_t)2 * (k + 2) * cstride + (size_t)j * cstride; }
+  // Launch wrappers: count every launch; time the block-sized kernels with events.
+  template <typename F>
+  cudaError_t timed(int kind, double bytes, F&& launch) {
+    const int ev = prof ? prof->begin(kind, s, true) : -1;
+    const cudaError_t e = launch();
+    if (prof) prof->end(kind, ev, s, bytes);
+    return e;
+  }
+  template <typename F>
+  cudaError_t counted(F&& launch) {
+    if (prof) prof->begin(kKSmall, s, false);
+    return launch();
+  }
+  rdm_status init_block(char* w) {
+    CK(timed(kKInit, blk_b, [&] {
+      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s, sub);
+    }));
+    return RDM_OK;
+  }
+};
+
+constexpr size_t kPackedMaxBlock = size_t(64) << 20;
+
+rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
   rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p);
   if (st != RDM_OK) return st;
-  const Layout& L = p.L;    // the recurrences (block size ds)
-  const Layout& Lg = p.Lg;  // the Gram view (groups of dso columns)
-  const int ds = L.DS, nv = ds * ds, ng = L.n_groups();
-  const int dso = 1 << hm.ns, nvo = dso * dso, ngo = Lg.n_groups();
-  const int sub = p.single ? dso : 1;  // recurrences per bath vector
-  const int n_rec = n_v * sub;         // real recurrences
-  const int64_t d_b = int64_t(1) << L.n_bath_bits;
+  L = p.L;    // the recurrences (block size ds)
+  Lg = p.Lg;  // the Gram view (groups of dso columns)
+  ds = L.DS, nv = ds * ds, ng = L.n_groups();
+  dso = 1 << hm.ns, nvo = dso * dso, ngo = Lg.n_groups();
+  sub = p.single ? dso : 1;  // recurrences per bath vector
+  n_rec = n_v * sub;         // real recurrences
+  d_b = int64_t(1) << L.n_bath_bits;
   if (o->vec_dist == RDM_BASIS && o->first_vector + (int64_t)n_v > d_b) {
     set_error("RDM_BASIS needs first_vector + n_v <= d_b = %lld", (long long)d_b);
     return RDM_EINVAL;
@@ -1020,40 +1109,37 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   Arena ar;
   ar.base = ws;
   ar.cap = ws_bytes;
-  const bool store = p.store;
-  const int nblk = store ? k + 1 : 3;
-  std::vector<char*> blk(nblk);
+  store = p.store;
+  nblk = store ? k + 1 : 3;
+  blk.assign(nblk, nullptr);
   {
     char* base = ar.take<char>(L.block_bytes() * nblk);
     for (int i = 0; i < nblk; ++i) blk[i] = base + (size_t)i * L.block_bytes();
   }
-  char* psi = store ? nullptr : ar.take<char>(L.block_bytes() * p.nbc);
-  const PlanSizes psz = plan_sizes(p);
-  const size_t pstride = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv;
-  const size_t pstride_g = (size_t)Lg.n_slices * Lg.gridx * Lg.groups_per_slice() * nvo;
-  double* partials = ar.take<double>(psz.partials);
-  double* coef = ar.take<double>((size_t)(k + 2) * ng * nv * 3);
-  double* d_ta = ar.take<double>((size_t)k * ng * nv);
-  double* d_tb = ar.take<double>((size_t)k * ng * nv);
-  double* d_e = ar.take<double>(psz.e);
-  double* d_gram = ar.take<double>(psz.gram);
-  double* d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
-  uint32_t* d_flags = ar.take<uint32_t>(4);
-  char* d_tk = ar.take<char>(p.tk_bytes);
-  char* d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
-  double* d_graw = p.gauss ? ar.take<double>((size_t)n_v * (size_t)d_b) : nullptr;
-  const size_t cstride = (size_t)ng * nv;
-  auto MZ = [&](int j) { return coef + (size_t)j * cstride; };                   // j = 1..k+1
-  auto CP = [&](int j) { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; };
-  auto CW = [&](int j) { return coef + (size_t)2 * (k + 2) * cstride + (size_t)j * cstride; };
+  psi = store ? nullptr : ar.take<char>(L.block_bytes() * p.nbc);
+  psz = plan_sizes(p);
+  pstride = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv;
+  pstride_g = (size_t)Lg.n_slices * Lg.gridx * Lg.groups_per_slice() * nvo;
+  partials = ar.take<double>(psz.partials);
+  coef = ar.take<double>((size_t)(k + 2) * ng * nv * 3);
+  d_ta = ar.take<double>((size_t)k * ng * nv);
+  d_tb = ar.take<double>((size_t)k * ng * nv);
+  d_e = ar.take<double>(psz.e);
+  d_gram = ar.take<double>(psz.gram);
+  d_norm = ar.take<double>((size_t)p.n_v_pad * 65);
+  d_flags = ar.take<uint32_t>(4);
+  d_tk = ar.take<char>(p.tk_bytes);
+  d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
+  d_graw = p.gauss ? ar.take<double>((size_t)n_v * (size_t)d_b) : nullptr;
+  cstride = (size_t)ng * nv;
 
   CK(cudaMemsetAsync(d_flags, 0, 4 * sizeof(uint32_t), s));
   const double tau_abs = o->precision == RDM_FP64 ? 1e-12 : 1e-6;
   const double tau_rel = o->precision == RDM_FP64 ? 1e-7 : 1e-5;
-  const double thr_abs_sq = (tau_abs * hm.hnorm) * (tau_abs * hm.hnorm);
-  const double thr_rel_sq = tau_rel * tau_rel;
+  thr_abs_sq = (tau_abs * hm.hnorm) * (tau_abs * hm.hnorm);
+  thr_rel_sq = tau_rel * tau_rel;
 
-  SpmmArgs sa{};
+  sa = SpmmArgs{};
   sa.flips = ham->d_flips;
   sa.n_flip = (int)hm.flips.size();
   sa.diags = ham->d_diags;
@@ -1062,19 +1148,8 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   sa.tile_k = p.tk_bytes ? d_tk : nullptr;
   sa.err = d_flags + 1;
 
-  const double blk_b = (double)L.block_bytes();
-  // Launch wrappers: count every launch; time the block-sized kernels with events.
-  auto timed = [&](int kind, double bytes, auto&& launch) -> cudaError_t {
-    const int ev = prof ? prof->begin(kind, s, true) : -1;
-    const cudaError_t e = launch();
-    if (prof) prof->end(kind, ev, s, bytes);
-    return e;
-  };
-  auto counted = [&](auto&& launch) -> cudaError_t {
-    if (prof) prof->begin(kKSmall, s, false);
-    return launch();
-  };
-  uint64_t h2d = 0, d2h = 0;
+  blk_b = (double)L.block_bytes();
+  h2d = d2h = 0;
 
   // Once per estimate: the per-tile diagonal table and (Gaussian case) the bath vectors.
   if (p.tk_bytes) CK(counted([&] { return launch_tile_diag(L, ham->tiled.dg, d_tk, s); }));
@@ -1085,18 +1160,40 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     if (prof) prof->begin(kKSmall, s, false);  // the norm kernel is two launches
     CK(counted([&] { return launch_gauss_fill(L, n_v, seed, o->first_vector, d_norm, d_vbuf, s, d_graw); }));
   }
-  auto init_block = [&](char* w) -> rdm_status {
-    CK(timed(kKInit, blk_b, [&] {
-      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s, sub);
-    }));
-    return RDM_OK;
-  };
-
-  // ---- pass 1: Algorithm 1, keeping only A_j, B_j and the mixing coefficients.
+  // ---- pass 1 starts from the starting block and M_1 = I, Cp_1 = 0.
   st = init_block(blk[0]);
   if (st != RDM_OK) return st;
   CK(counted([&] { return launch_coef_init(L, StepCoefs{MZ(1), CP(1), nullptr}, s); }));
-  int cur = 0, prv = -1, nxt = 1;
+  cur = 0, prv = -1, nxt = 1;
+  return RDM_OK;
+}
+
+bool EstimateRun::packable() const {
+  return store && !p.single && L.block_bytes() <= kPackedMaxBlock && L.n_slices * L.gridx <= (1 << 20);
+}
+
+PackedItem EstimateRun::packed_item() const {
+  PackedItem it{};
+  it.L = L;
+  // the untiled grid of the plain kernels (the tiled SpMM's own grid is not used here);
+  // the partials buffer is sized for the larger of the two (plan_sizes)
+  it.L.gridx = untiled_gridx(L);
+  it.sa = sa;
+  it.sa.partials = partials;
+  it.blk = blk[0];
+  it.coef = coef;
+  it.ta = d_ta;
+  it.tb = d_tb;
+  it.flags = d_flags;
+  it.thr_abs_sq = thr_abs_sq;
+  it.thr_rel_sq = thr_rel_sq;
+  it.k = k;
+  it.n_rec = n_rec;
+  return it;
+}
+
+rdm_status EstimateRun::pass1() {
+  rdm_status st = RDM_OK;
   // k steps; `launch` false only walks the buffer rotation (the launches are replayed
   // from a graph).
   auto pass1 = [&](cudaStream_t ls, bool launch) -> rdm_status {
@@ -1176,7 +1273,11 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
     }
   }
   st = pass1(s, !replayed);
-  if (st != RDM_OK) return st;
+  return st;
+}
+
+rdm_status EstimateRun::finish() {
+  rdm_status st = RDM_OK;
   std::vector<double> ta((size_t)k * cstride), tb((size_t)k * cstride), mz((size_t)(k + 1) * cstride);
   uint32_t flags[4];
   CK(cudaMemcpyAsync(ta.data(), d_ta, ta.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1429,7 +1530,297 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
   return RDM_OK;
 }
 
+rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
+                         const double* betas, int n_beta, int n_v, int k, uint64_t seed,
+                         const rdm_opts* o, rdm_result* out, Profiler* prof) {
+  EstimateRun run(ham, s, betas, n_beta, n_v, k, seed, o, out, prof);
+  rdm_status st = run.prepare(ws, ws_bytes);
+  if (st == RDM_OK) st = run.pass1();
+  if (st == RDM_OK) st = run.finish();
+  return st;
+}
+
+// ---------------------------------------------------------------- batches
+
+// Bytes at the front of a batch workspace for one packed launch's descriptors (items,
+// step and prefix tables, barrier words).
+static size_t packed_meta_bytes(int n_items, int k_max) {
+  return ((sizeof(PackedItem) * (size_t)n_items + sizeof(int) * ((size_t)k_max + 2 + 2 * ((size_t)n_items + 1)) +
+           64 + 255) / 256) * 256;
+}
+
+// One packed launch for the items `idx` of `runs` (same precision and d_s), with the
+// grid chosen by the autotuner. meta: device scratch of packed_meta_bytes.
+static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateRun*>& runs, int precision,
+                             int ds, char* meta, Profiler* prof) {
+  std::stable_sort(runs.begin(), runs.end(),
+                   [](const EstimateRun* a, const EstimateRun* b) { return a->plan().k > b->plan().k; });
+  const int n = (int)runs.size();
+  const int k_max = runs[0]->plan().k;
+  std::vector<PackedItem> items(n);
+  std::vector<int> pre_rows(n + 1, 0), pre_groups(n + 1, 0), active(k_max + 1, 0);
+  size_t smem = 16;
+  double bytes = 0.0;
+  for (int i = 0; i < n; ++i) {
+    items[i] = runs[i]->packed_item();
+    const Layout& L = items[i].L;
+    pre_rows[i + 1] = pre_rows[i] + L.gridx * L.n_slices;
+    pre_groups[i + 1] = pre_groups[i] + L.n_groups();
+    smem = std::max(smem, spmm_terms_smem(precision, items[i].sa.n_flip, items[i].sa.n_diag));
+    bytes += 6.0 * (double)L.block_bytes() * items[i].k;  // SpMM 3 blocks + orth 3 blocks per step
+  }
+  for (int j = 1; j <= k_max; ++j) {
+    int na = 0;
+    while (na < n && items[na].k >= j) ++na;
+    active[j] = na;
+  }
+  // host image of the descriptors, one copy
+  const size_t o_items = 0, o_active = sizeof(PackedItem) * n;
+  const size_t o_rows = o_active + sizeof(int) * (k_max + 1), o_groups = o_rows + sizeof(int) * (n + 1);
+  const size_t o_bar = (o_groups + sizeof(int) * (n + 1) + 15) / 16 * 16;
+  std::vector<char> img(o_bar);
+  std::memcpy(img.data() + o_items, items.data(), sizeof(PackedItem) * n);
+  std::memcpy(img.data() + o_active, active.data(), sizeof(int) * (k_max + 1));
+  std::memcpy(img.data() + o_rows, pre_rows.data(), sizeof(int) * (n + 1));
+  std::memcpy(img.data() + o_groups, pre_groups.data(), sizeof(int) * (n + 1));
+  CK(cudaMemcpyAsync(meta, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+  PackedPlan pp{};
+  pp.items = reinterpret_cast<const PackedItem*>(meta + o_items);
+  pp.n_items = n;
+  pp.k_max = k_max;
+  pp.active = reinterpret_cast<const int*>(meta + o_active);
+  pp.pre_rows = reinterpret_cast<const int*>(meta + o_rows);
+  pp.pre_groups = reinterpret_cast<const int*>(meta + o_groups);
+  pp.bar = reinterpret_cast<uint32_t*>(meta + o_bar);
+  // the pageable host image must outlive its copy
+  CK(cudaStreamSynchronize(s));
+
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int max_bpsm = packed_max_blocks_per_sm(precision, ds, smem);
+  if (max_bpsm < 1) {
+    set_error("packed first pass: no block fits an SM (%zu bytes of term tables)", smem);
+    return RDM_EINVAL;
+  }
+  const int units = std::max(pre_rows[n], pre_groups[n]);
+  auto grid_for = [&](int bpsm) { return std::max(1, std::min(bpsm * sms, units)); };
+  auto launch = [&](int grid) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(pp.bar, 0, 3 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = launch_pass1_packed(precision, ds, pp, grid, smem, s);
+    return e;
+  };
+  // Autotuner: key = (precision, d_s, log2 of the block-sized units of the batch).
+  int lg = 0;
+  while ((1 << lg) < pre_rows[n]) ++lg;
+  const uint64_t key = (uint64_t)precision | ((uint64_t)ds << 4) | ((uint64_t)lg << 8);
+  int bpsm = 0;
+  {
+    std::lock_guard<std::mutex> lk(ctx->tuning.mu);
+    auto f = ctx->tuning.blocks_per_sm.find(key);
+    if (f != ctx->tuning.blocks_per_sm.end()) bpsm = std::min(f->second, max_bpsm);
+  }
+  if (bpsm == 0) {
+    // Time each candidate once on this batch (the first pass is idempotent: it only
+    // reads the starting block and M_1, Cp_1), keep the fastest for the key.
+    std::vector<int> cand;
+    for (int c : {1, 2, 4, 8})
+      if (c <= max_bpsm && (cand.empty() || grid_for(c) > grid_for(cand.back()))) cand.push_back(c);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.0f;
+    for (int c : cand) {
+      CK(cudaEventRecord(e0, s));
+      CK(launch(grid_for(c)));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (bpsm == 0 || ms < best) {
+        best = ms;
+        bpsm = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(ctx->tuning.mu);
+    ctx->tuning.blocks_per_sm[key] = bpsm;
+    ctx->tuning.tuning_runs += cand.size();
+  }
+  const int ev = prof ? prof->begin(kKPacked, s, true) : -1;
+  const cudaError_t le = launch(grid_for(bpsm));
+  if (prof) prof->end(kKPacked, ev, s, bytes);
+  CK(le);
+  uint32_t bar_err = 0;
+  CK(cudaMemcpyAsync(&bar_err, pp.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bar_err) {
+    set_error("packed first pass: a grid-barrier wait gave up (device error)");
+    return RDM_ECUDA;
+  }
+  return RDM_OK;
+}
+
+rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws_bytes,
+                               rdm_batch_item* items, int n, const size_t* need, Profiler* prof) {
+  std::vector<std::unique_ptr<EstimateRun>> runs(n);
+  size_t off = 0;
+  // descriptors of at most two packed launches (float32 / float64 times d_s) go first
+  int k_max = 1;
+  for (int i = 0; i < n; ++i) k_max = std::max(k_max, items[i].k);
+  const size_t meta_b = packed_meta_bytes(n, k_max);
+  char* meta = ws;
+  off = 6 * meta_b;
+  rdm_status first_bad = RDM_OK;
+  for (int i = 0; i < n; ++i) {
+    rdm_batch_item& it = items[i];
+    runs[i] = std::make_unique<EstimateRun>(it.ham, s, it.betas, it.n_beta, it.n_v, it.k, it.seed, &it.opts,
+                                            it.out, prof);
+    it.status = runs[i]->prepare(ws + off, need[i]);
+    off += need[i];
+    if (it.status != RDM_OK && first_bad == RDM_OK) first_bad = it.status;
+  }
+  // packed first passes, one launch per (precision, d_s)
+  int slot = 0;
+  for (int prec : {RDM_FP32, RDM_FP64})
+    for (int ds : {1, 2, 4}) {
+      std::vector<EstimateRun*> group;
+      std::vector<int> idx;
+      for (int i = 0; i < n; ++i)
+        if (items[i].status == RDM_OK && runs[i]->packable() && runs[i]->plan().L.precision == prec &&
+            runs[i]->plan().L.DS == ds) {
+          group.push_back(runs[i].get());
+          idx.push_back(i);
+        }
+      if (group.empty()) continue;
+      const rdm_status st = run_packed(ctx, s, group, prec, ds, meta + (size_t)slot++ * meta_b, prof);
+      if (st != RDM_OK)
+        for (int i : idx) {
+          items[i].status = st;
+          if (first_bad == RDM_OK) first_bad = st;
+        }
+      for (int i : idx) items[i].status = items[i].status == RDM_OK ? RDM_OK : items[i].status;
+      for (int i : idx) runs[i]->packed_done = true;
+    }
+  for (int i = 0; i < n; ++i) {
+    if (items[i].status != RDM_OK) continue;
+    rdm_status st = runs[i]->packed_done ? RDM_OK : runs[i]->pass1();
+    if (st == RDM_OK) st = runs[i]->finish();
+    items[i].status = st;
+    if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
+  }
+  return first_bad;
+}
+
+size_t batch_workspace_bytes(const rdm_batch_item* items, int n, size_t usable, size_t* need) {
+  int k_max = 1;
+  for (int i = 0; i < n; ++i) k_max = std::max(k_max, items[i].k);
+  size_t tot = 6 * packed_meta_bytes(n, k_max);
+  for (int i = 0; i < n; ++i) {
+    rdm_status st = RDM_OK;
+    need[i] = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k, &items[i].opts,
+                             usable, &st);
+    if (need[i] == 0) return 0;
+    need[i] = (need[i] + 255) / 256 * 256;
+    tot += need[i];
+  }
+  return tot;
+}
+
 }  // namespace rdm
+
+static bool valid_opts(const rdm_opts* o);
+
+extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, int n_items) {
+  if (!ctx || !items || n_items < 1) {
+    set_error("rdm_estimate_batch: NULL context or items, or n_items < 1");
+    return RDM_EINVAL;
+  }
+  for (int i = 0; i < n_items; ++i) {
+    items[i].status = RDM_EINVAL;
+    if (!items[i].ham || items[i].ham->ctx != ctx) {
+      set_error("rdm_estimate_batch: item %d has no Hamiltonian of this context", i);
+      return RDM_EINVAL;
+    }
+    rdm_status st = check_estimate_args(items[i].ham, items[i].betas, items[i].n_beta, &items[i].opts,
+                                        items[i].out);
+    if (st != RDM_OK) return st;
+  }
+  CK(cudaSetDevice(ctx->device));
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const size_t usable = ctx->ws ? ctx->ws_bytes : (size_t)(0.85 * (double)(free_b + ctx->own_bytes));
+  // Items run in consecutive sub-batches whose workspaces fit together; an item whose
+  // sizes are invalid or that does not fit on its own fails alone.
+  rdm_status first_bad = RDM_OK;
+  std::vector<rdm_batch_item*> ok_items;
+  for (int i = 0; i < n_items; ++i) {
+    rdm_status st = RDM_OK;
+    const size_t need = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k,
+                                       &items[i].opts, usable, &st);
+    if (need == 0) {
+      items[i].status = st != RDM_OK ? st : RDM_ENOMEM;
+      if (first_bad == RDM_OK) first_bad = items[i].status;
+      continue;
+    }
+    ok_items.push_back(&items[i]);
+  }
+  size_t i0 = 0;
+  while (i0 < ok_items.size()) {
+    // greedy: as many consecutive items as fit (at least one)
+    std::vector<rdm_batch_item> sub;
+    std::vector<size_t> need;
+    size_t tot = 0;
+    size_t i1 = i0;
+    while (i1 < ok_items.size()) {
+      sub.push_back(*ok_items[i1]);
+      need.assign(sub.size(), 0);
+      const size_t t2 = batch_workspace_bytes(sub.data(), (int)sub.size(), usable, need.data());
+      if (t2 == 0 || (t2 > usable && i1 > i0)) {
+        sub.pop_back();
+        break;
+      }
+      tot = t2;
+      ++i1;
+    }
+    need.assign(sub.size(), 0);
+    tot = batch_workspace_bytes(sub.data(), (int)sub.size(), usable, need.data());
+    char* ws = ctx->ws;
+    rdm_status st = RDM_OK;
+    if (tot > usable) {
+      set_error("rdm_estimate_batch: an item needs %zu bytes of device memory, %zu usable", tot, usable);
+      st = RDM_ENOMEM;
+    } else if (!ws) {
+      if (ctx->own_bytes < tot) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->own_ws) CK(cudaFree(ctx->own_ws));
+        ctx->own_ws = nullptr;
+        ctx->own_bytes = 0;
+        CK(cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), tot));
+        ctx->own_bytes = tot;
+      }
+      ws = ctx->own_ws;
+    }
+    if (st == RDM_OK)
+      st = estimate_batch_impl(ctx, ctx->stream, ws, tot, sub.data(), (int)sub.size(), need.data(), &ctx->prof);
+    for (size_t q = 0; q < sub.size(); ++q) ok_items[i0 + q]->status = st == RDM_ENOMEM && tot > usable ? st
+                                                                                                       : sub[q].status;
+    if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
+    i0 = i1;
+  }
+  return first_bad;
+}
+
+extern "C" rdm_status rdm_packed_tuning(rdm_ctx* ctx, int* n_keys, uint64_t* tuning_runs) {
+  if (!ctx) {
+    set_error("rdm_packed_tuning: NULL context");
+    return RDM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(ctx->tuning.mu);
+  if (n_keys) *n_keys = (int)ctx->tuning.blocks_per_sm.size();
+  if (tuning_runs) *tuning_runs = ctx->tuning.tuning_runs;
+  return RDM_OK;
+}
 
 static bool valid_opts(const rdm_opts* o) {
   return o && (o->precision == RDM_FP32 || o->precision == RDM_FP64) &&

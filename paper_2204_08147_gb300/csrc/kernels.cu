@@ -115,13 +115,14 @@ __device__ __forceinline__ unsigned group_mask(int tpr) {
 // Fixed-order block reduction of NV values per thread into per-block float64
 // partials: partials[((slice*gridx + bx)*G_s + lane*NG + g)*NVG + v] where
 // vals[g*NVG + v] belongs to group g of the thread and lane = threadIdx.x % tpr
-// (tpr <= 8, a power of two). A butterfly over the lanes of a warp with the same
+// (tpr <= 8, a power of two), slot = slice*gridx + bx the block's place in the grid
+// (blockIdx.y * gridDim.x + blockIdx.x for a plain launch). A butterfly over the lanes of a warp with the same
 // lane in the type R of vals, then the warps' sums added in float64 in warp order:
 // the same order on every run. The float32 path runs the butterfly in float32 (its
 // per-thread sums are float32 already): GB300's float64 pipe is narrow, and a float64
 // butterfly in every block made launches of many short blocks float64-bound.
 template <int NG, int NVG, typename R = double>
-__device__ void block_reduce_store(const R* vals, int tpr, double* partials, int gs) {
+__device__ void block_reduce_store(const R* vals, int tpr, double* partials, int gs, size_t slot) {
   constexpr int NV = NG * NVG;
   constexpr int kWarps = kThreads / 32;
   __shared__ double red[kWarps * 8 * NV];
@@ -142,7 +143,7 @@ __device__ void block_reduce_store(const R* vals, int tpr, double* partials, int
     const int lane = threadIdx.x / NV, e = threadIdx.x % NV;
     double sum = 0.0;
     for (int w = 0; w < kWarps; ++w) sum += red[(w * tpr + lane) * NV + e];
-    const size_t base = ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * gs + (size_t)lane * NG) * NVG;
+    const size_t base = (slot * gs + (size_t)lane * NG) * NVG;
     partials[base + e] = sum;
   }
 }
@@ -301,14 +302,28 @@ __device__ TermsSmem<T> load_terms(const FlipTerm* flips, int nf, const DiagTerm
   return t;
 }
 
-template <typename T, int DS, int VW, int MODE>
-__global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
+// The rows of block (bx, by) of a grid of gx x n_slices blocks of the untiled SpMM:
+// rows bx*rpb + rs + i*gx*rpb of slice by (the grid-stride walk of a plain launch), and,
+// in pass 1, its partial sums of W_j^T Z at slot by*gx + bx. `terms` are the term tables
+// in shared memory (load_terms).
+template <typename T, int VW, bool COH>
+__device__ __forceinline__ void ld_vec(T* r, const T* p) {
+  if constexpr (COH)
+    VecIO<T, VW>::ld_rw(r, p);
+  else
+    VecIO<T, VW>::ld(r, p);
+}
+
+// COH: coherent loads only (no read-only cache path), for blocks written earlier in the
+// same launch (the packed kernel).
+template <typename T, int DS, int VW, int MODE, bool COH = false>
+__device__ __forceinline__ void spmm_block(const Layout& L, const SpmmArgs& a, const TermsSmem<T>& terms,
+                                           int bx, int by, int gx) {
   constexpr int NG = VW / DS;
   constexpr int NVG = DS * DS;
-  const TermsSmem<T> terms = load_terms<T>(a.flips, a.n_flip, a.diags, a.n_diag);
   const int tpr = L.TPR, rpb = kThreads / tpr;
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
-  const int slice = blockIdx.y;
+  const int slice = by;
   const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
   const T* __restrict__ W = reinterpret_cast<const T*>(a.w) + soff;
   const T* __restrict__ Wp = a.w_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
@@ -337,10 +352,10 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
       for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
 
   const int nf = a.n_flip, nd = a.n_diag;
-  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+  for (int64_t s = (int64_t)bx * rpb + rs; s < L.D; s += (int64_t)gx * rpb) {
     const uint32_t su = (uint32_t)s;
     T x[VW];
-    VecIO<T, VW>::ld(x, W + (size_t)s * L.Bs);
+    ld_vec<T, VW, COH>(x, W + (size_t)s * L.Bs);
     // Diagonal: sum_t c_t (1 - 2 parity(s & m_t)), split over the row group.
     T dg = (T)0;
     for (int t = lane; t < nd; t += tpr) {
@@ -357,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
       const T c = (__popc(su & m) & 1) ? terms.fodd[t] : terms.feven[t];
       if (c != (T)0) {
         T xp[VW];
-        VecIO<T, VW>::ld(xp, W + (size_t)(su ^ m) * L.Bs);
+        ld_vec<T, VW, COH>(xp, W + (size_t)(su ^ m) * L.Bs);
 #pragma unroll
         for (int v = 0; v < VW; ++v) y[v] = fma(c, xp[v], y[v]);
       }
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
       }
     if (Wp) {
       T xp[VW];
-      VecIO<T, VW>::ld(xp, Wp + (size_t)s * L.Bs);
+      ld_vec<T, VW, COH>(xp, Wp + (size_t)s * L.Bs);
 #pragma unroll
       for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -407,8 +422,14 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
       for (int i = 0; i < DS; ++i)
 #pragma unroll
         for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
-    block_reduce_store<NG, NVG, T>(vals, tpr, a.partials, L.groups_per_slice());
+    block_reduce_store<NG, NVG, T>(vals, tpr, a.partials, L.groups_per_slice(), (size_t)by * gx + bx);
   }
+}
+
+template <typename T, int DS, int VW, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmm(Layout L, SpmmArgs a) {
+  const TermsSmem<T> terms = load_terms<T>(a.flips, a.n_flip, a.diags, a.n_diag);
+  spmm_block<T, DS, VW, MODE>(L, a, terms, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // ---------------------------------------------------------------- tiled SpMM
@@ -1143,16 +1164,17 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
 
 // ---------------------------------------------------------------- orthogonalisation
 
-template <typename T, int DS, int VW, bool PASS1>
-__global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict__ Wg,
-                                                   T* __restrict__ Zg, const double* cw,
-                                                   double* partials, T* psi, const double* e,
-                                                   int nb) {
+// Block (bx, by) of a gx x n_slices grid of the orthogonalisation (grid-stride rows as
+// in spmm_block).
+template <typename T, int DS, int VW, bool PASS1, bool COH = false>
+__device__ __forceinline__ void orth_block(const Layout& L, const T* __restrict__ Wg, T* __restrict__ Zg,
+                                           const double* cw, double* partials, T* psi, const double* e,
+                                           int nb, int bx, int by, int gx) {
   constexpr int NG = VW / DS;
   constexpr int NVG = DS * DS;
   const int tpr = L.TPR, rpb = kThreads / tpr;
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
-  const int slice = blockIdx.y;
+  const int slice = by;
   const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
   const T* W = Wg + soff;
   T* Z = Zg + soff;
@@ -1184,9 +1206,9 @@ __global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict
     }
     __syncthreads();
   }
-  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+  for (int64_t s = (int64_t)bx * rpb + rs; s < L.D; s += (int64_t)gx * rpb) {
     T x[VW], z[VW];
-    VecIO<T, VW>::ld(x, W + (size_t)s * L.Bs);
+    ld_vec<T, VW, COH>(x, W + (size_t)s * L.Bs);
     VecIO<T, VW>::ld_rw(z, Z + (size_t)s * L.Bs);
 #pragma unroll
     for (int g = 0; g < NG; ++g)
@@ -1232,8 +1254,16 @@ __global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict
       for (int i = 0; i < DS; ++i)
 #pragma unroll
         for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
-    block_reduce_store<NG, NVG, T>(vals, tpr, partials, L.groups_per_slice());
+    block_reduce_store<NG, NVG, T>(vals, tpr, partials, L.groups_per_slice(), (size_t)by * gx + bx);
   }
+}
+
+template <typename T, int DS, int VW, bool PASS1>
+__global__ void __launch_bounds__(kThreads) k_orth(Layout L, const T* __restrict__ Wg,
+                                                   T* __restrict__ Zg, const double* cw,
+                                                   double* partials, T* psi, const double* e,
+                                                   int nb) {
+  orth_block<T, DS, VW, PASS1>(L, Wg, Zg, cw, partials, psi, e, nb, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // psi_beta = W_1 E_{1,beta} (start of pass 2).
@@ -1269,7 +1299,10 @@ __global__ void __launch_bounds__(kThreads) k_psi_init(Layout L, const T* __rest
   }
 }
 
-// Gram partials of one psi block.
+// Gram partials of one psi block. The Gram is accumulated in float64 whatever the
+// vectors' precision (eq. rho_est): a product of two float32 values is exact in float64,
+// so each fma rounds only the sum. Only the upper triangle is summed; the lower one is
+// its mirror (the same products, so the same bits).
 template <typename T, int DS, int VW>
 __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __restrict__ P,
                                                          double* partials) {
@@ -1279,31 +1312,35 @@ __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __re
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
   const int slice = blockIdx.y;
   const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
-  T acc[NG][DS][DS];
+  double acc[NG][DS][DS];
 #pragma unroll
   for (int g = 0; g < NG; ++g)
 #pragma unroll
     for (int i = 0; i < DS; ++i)
 #pragma unroll
-      for (int j = 0; j < DS; ++j) acc[g][i][j] = (T)0;
+      for (int j = 0; j < DS; ++j) acc[g][i][j] = 0.0;
   for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
     T p[VW];
     VecIO<T, VW>::ld(p, P + soff + (size_t)s * L.Bs);
+    double pd[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) pd[v] = (double)p[v];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int i = 0; i < DS; ++i)
 #pragma unroll
-        for (int j = 0; j < DS; ++j) acc[g][i][j] = fma(p[g * DS + i], p[g * DS + j], acc[g][i][j]);
+        for (int j = i; j < DS; ++j) acc[g][i][j] = fma(pd[g * DS + i], pd[g * DS + j], acc[g][i][j]);
   }
-  T vals[NG * NVG];
+  double vals[NG * NVG];
 #pragma unroll
   for (int g = 0; g < NG; ++g)
 #pragma unroll
     for (int i = 0; i < DS; ++i)
 #pragma unroll
-      for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[g][i][j];
-  block_reduce_store<NG, NVG, T>(vals, tpr, partials, L.groups_per_slice());
+      for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = j >= i ? acc[g][i][j] : acc[g][j][i];
+  block_reduce_store<NG, NVG, double>(vals, tpr, partials, L.groups_per_slice(),
+                                       (size_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Stored-basis Gram: psi_beta = sum_{j=1..k} W_j E_{j,beta} row by row (the same
@@ -1375,7 +1412,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
     sE[i] = (T)e[(((size_t)j * nbs + b0 + bi) * ng) * NVG + (size_t)slice * gs * NVG + r2];
   }
   __syncthreads();
-  T acc[NBT][NG][DS][DS];
+  // the Gram in float64 (upper triangle; see k_final_gram)
+  double acc[NBT][NG][DS][DS];
 #pragma unroll
   for (int bi = 0; bi < NBT; ++bi)
 #pragma unroll
@@ -1383,7 +1421,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
 #pragma unroll
       for (int i = 0; i < DS; ++i)
 #pragma unroll
-        for (int j = 0; j < DS; ++j) acc[bi][g][i][j] = (T)0;
+        for (int j = 0; j < DS; ++j) acc[bi][g][i][j] = 0.0;
   // Rows s and s + stride form a pair; the accumulation order per row is the same
   // as for single rows (rows are visited in the same sequence per thread).
   const int64_t stride = (int64_t)gridDim.x * rpb;
@@ -1445,27 +1483,33 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
     for (int h = 0; h < 2; ++h) {
       if (h == 1 && !two) break;
 #pragma unroll
-      for (int bi = 0; bi < NBT; ++bi)
+      for (int bi = 0; bi < NBT; ++bi) {
+        double pd[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) pd[v] = (double)psi[h][bi][v];
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
           for (int i = 0; i < DS; ++i)
 #pragma unroll
-            for (int j = 0; j < DS; ++j)
-              acc[bi][g][i][j] = fma(psi[h][bi][g * DS + i], psi[h][bi][g * DS + j], acc[bi][g][i][j]);
+            for (int j = i; j < DS; ++j)
+              acc[bi][g][i][j] = fma(pd[g * DS + i], pd[g * DS + j], acc[bi][g][i][j]);
+      }
     }
   }
 #pragma unroll
   for (int bi = 0; bi < NBT; ++bi) {  // static indices keep acc in registers
     if (bi < nb) {
-      T vals[NG * NVG];
+      double vals[NG * NVG];
 #pragma unroll
       for (int g = 0; g < NG; ++g)
 #pragma unroll
         for (int i = 0; i < DS; ++i)
 #pragma unroll
-          for (int j = 0; j < DS; ++j) vals[g * NVG + i * DS + j] = acc[bi][g][i][j];
-      block_reduce_store<NG, NVG, T>(vals, tpr, partials + (size_t)bi * pstride, gs);
+          for (int j = 0; j < DS; ++j)
+            vals[g * NVG + i * DS + j] = j >= i ? acc[bi][g][i][j] : acc[bi][g][j][i];
+      block_reduce_store<NG, NVG, double>(vals, tpr, partials + (size_t)bi * pstride, gs,
+                                           (size_t)blockIdx.y * gridDim.x + blockIdx.x);
       __syncthreads();
     }
   }
@@ -1475,18 +1519,22 @@ __global__ void __launch_bounds__(kThreads) k_gram_stored(Layout L, const T* __r
 
 constexpr int kSmallThreads = 128;
 
-// Sums the NV partials of group blockIdx.x over the gridx blocks (fixed order).
+// Sums the NV partials of group l over the gridx blocks (fixed order: thread t < 128
+// takes bx = t, t + 128, ..., then a tree over the 128 sums). Every thread of the block
+// must call it; threads beyond the first kSmallThreads only pass the barriers.
 template <int NV>
-__device__ void reduce_group(const Layout& L, const double* partials, double* out) {
+__device__ void reduce_group(const Layout& L, const double* partials, double* out, int l) {
   __shared__ double sh[kSmallThreads];
-  const int l = blockIdx.x;
   const int gs = L.groups_per_slice();
   const int slice = l / gs, gis = l % gs;
+  const bool part = threadIdx.x < kSmallThreads;
   for (int v = 0; v < NV; ++v) {
-    double s = 0.0;
-    for (int bx = threadIdx.x; bx < L.gridx; bx += kSmallThreads)
-      s += partials[((size_t)(slice * L.gridx + bx) * gs + gis) * NV + v];
-    sh[threadIdx.x] = s;
+    if (part) {
+      double s = 0.0;
+      for (int bx = threadIdx.x; bx < L.gridx; bx += kSmallThreads)
+        s += partials[((size_t)(slice * L.gridx + bx) * gs + gis) * NV + v];
+      sh[threadIdx.x] = s;
+    }
     __syncthreads();
     for (int w = kSmallThreads / 2; w > 0; w >>= 1) {
       if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -1508,14 +1556,14 @@ __global__ void k_coef_init(int n_groups, double* mz, double* cp) {
     }
 }
 
+// After the SpMM, for group l (every thread of the block calls it): A_j and Cw_j.
 template <int DS>
-__global__ void k_small_a(Layout L, const double* partials, const double* mz, double* a_out,
-                          double* cw_out, uint32_t* flags) {
+__device__ void small_a_group(const Layout& L, const double* partials, const double* mz, double* a_out,
+                              double* cw_out, uint32_t* flags, int l) {
   constexpr int NV = DS * DS;
   __shared__ double tot[NV];
-  reduce_group<NV>(L, partials, tot);
+  reduce_group<NV>(L, partials, tot, l);
   if (threadIdx.x != 0) return;
-  const int l = blockIdx.x;
   const double* M = mz + (size_t)l * NV;
   double p1[DS][DS], A[DS][DS];
   // P1 = M^T (W^T Z) = Q_j^T Z
@@ -1542,14 +1590,21 @@ __global__ void k_small_a(Layout L, const double* partials, const double* mz, do
 }
 
 template <int DS>
-__global__ void k_small_b(Layout L, const double* partials, const double* mz_j, double* b_out,
-                          double* mz_next, double* cp_next, double thr_abs_sq, double thr_rel_sq,
-                          int n_real, uint32_t* flags) {
+__global__ void k_small_a(Layout L, const double* partials, const double* mz, double* a_out,
+                          double* cw_out, uint32_t* flags) {
+  small_a_group<DS>(L, partials, mz, a_out, cw_out, flags, blockIdx.x);
+}
+
+// After the orthogonalisation, for group l (every thread of the block calls it): the
+// Cholesky QR with deflation -> B_j, M_{j+1}, Cp_{j+1}.
+template <int DS>
+__device__ void small_b_group(const Layout& L, const double* partials, const double* mz_j, double* b_out,
+                              double* mz_next, double* cp_next, double thr_abs_sq, double thr_rel_sq,
+                              int n_real, uint32_t* flags, int l) {
   constexpr int NV = DS * DS;
   __shared__ double tot[NV];
-  reduce_group<NV>(L, partials, tot);
+  reduce_group<NV>(L, partials, tot, l);
   if (threadIdx.x != 0) return;
-  const int l = blockIdx.x;
   double G[DS][DS], R[DS][DS], Ri[DS][DS];
   bool kept[DS];
   for (int i = 0; i < DS; ++i)
@@ -1608,12 +1663,145 @@ __global__ void k_small_b(Layout L, const double* partials, const double* mz_j, 
 }
 
 template <int DS>
+__global__ void k_small_b(Layout L, const double* partials, const double* mz_j, double* b_out,
+                          double* mz_next, double* cp_next, double thr_abs_sq, double thr_rel_sq,
+                          int n_real, uint32_t* flags) {
+  small_b_group<DS>(L, partials, mz_j, b_out, mz_next, cp_next, thr_abs_sq, thr_rel_sq, n_real, flags,
+                    blockIdx.x);
+}
+
+template <int DS>
 __global__ void k_reduce_gram(Layout L, const double* partials, double* gram) {
   constexpr int NV = DS * DS;
   __shared__ double tot[NV];
-  reduce_group<NV>(L, partials, tot);
+  reduce_group<NV>(L, partials, tot, blockIdx.x);
   if (threadIdx.x != 0) return;
   for (int v = 0; v < NV; ++v) gram[(size_t)blockIdx.x * NV + v] = tot[v];
+}
+
+// ---------------------------------------------------------------- packed first pass
+//
+// The first pass (Algorithm 1's k steps) of several estimates in ONE cooperative
+// launch: every block of a persistent grid walks the work units of a phase, and a grid
+// barrier separates the phases of a step: SpMM (+ W_j^T Z partials), A_j per bath
+// vector, orthogonalisation (+ Gram partials), Cholesky QR per bath vector. A unit is
+// exactly one block of the corresponding plain launch of that estimate (block (bx, by)
+// of its gridx x n_slices grid, or group l), so each estimate's arithmetic and
+// reduction order depend on its own layout only: results are the same whichever
+// estimates share the launch and however the units are spread over the grid. Items are
+// sorted by k, largest first, so the items still running at step j are a prefix.
+
+// Grid barrier: arrival counter, generation word, error word (zero before the launch).
+// The last block to arrive resets the counter and advances the generation; the others
+// wait for that with a bounded spin. A wait that gives up sets the error word, and a
+// block that sees the error word set leaves at its next barrier.
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ bool grid_barrier(uint32_t* bar, uint32_t& gen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    if (ld_acquire_gpu(bar + 2) != 0u) {
+      ok = 0;
+    } else if (atomicAdd(bar, 1u) == gridDim.x - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicExch(bar + 1, gen + 1u);
+    } else {
+      uint32_t it = 0;
+      while (ld_acquire_gpu(bar + 1) == gen) {
+        if (++it > (1u << 24) || ld_acquire_gpu(bar + 2) != 0u) {
+          atomicOr(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+        if (it > 64) __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  ++gen;
+  return ok_s != 0;
+}
+
+// Unit u of a phase -> its item (largest i with pre[i] <= u among the first n).
+__device__ __forceinline__ int packed_item_of(const int* pre, int n, int u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_pass1_packed(PackedPlan pp) {
+  constexpr int NVG = DS * DS;
+  uint32_t gen = 0;
+  for (int j = 1; j <= pp.k_max; ++j) {
+    const int na = pp.active[j];
+    // phase A: Z = (H W_j) M_j + W_{j-1} Cp_j and the partial sums of W_j^T Z
+    for (int u = blockIdx.x; u < pp.pre_rows[na]; u += gridDim.x) {
+      const int i = packed_item_of(pp.pre_rows, na, u);
+      const PackedItem& it = pp.items[i];
+      const int r = u - pp.pre_rows[i];
+      const size_t bb = it.L.block_bytes(), cs = (size_t)it.L.n_groups() * NVG;
+      SpmmArgs a = it.sa;
+      a.w = it.blk + (size_t)(j - 1) * bb;
+      a.w_prev = j > 1 ? it.blk + (size_t)(j - 2) * bb : nullptr;
+      a.z = it.blk + (size_t)j * bb;
+      a.mz = it.coef + (size_t)j * cs;
+      a.cp = it.coef + (size_t)(it.k + 2) * cs + (size_t)j * cs;
+      const TermsSmem<T> terms = load_terms<T>(a.flips, a.n_flip, a.diags, a.n_diag);
+      spmm_block<T, DS, VW, kModePass1, true>(it.L, a, terms, r % it.L.gridx, r / it.L.gridx, it.L.gridx);
+      __syncthreads();  // the next unit rewrites the term tables
+    }
+    if (!grid_barrier(pp.bar, gen)) return;
+    // phase B: A_j and Cw_j per bath vector
+    for (int u = blockIdx.x; u < pp.pre_groups[na]; u += gridDim.x) {
+      const int i = packed_item_of(pp.pre_groups, na, u);
+      const PackedItem& it = pp.items[i];
+      const size_t cs = (size_t)it.L.n_groups() * NVG;
+      small_a_group<DS>(it.L, it.sa.partials, it.coef + (size_t)j * cs, it.ta + (size_t)(j - 1) * cs,
+                        it.coef + (size_t)2 * (it.k + 2) * cs + (size_t)j * cs, it.flags, u - pp.pre_groups[i]);
+      __syncthreads();
+    }
+    if (!grid_barrier(pp.bar, gen)) return;
+    // phase C: W_{j+1} = Z + W_j Cw_j in place, partial sums of W_{j+1}^T W_{j+1}
+    for (int u = blockIdx.x; u < pp.pre_rows[na]; u += gridDim.x) {
+      const int i = packed_item_of(pp.pre_rows, na, u);
+      const PackedItem& it = pp.items[i];
+      const int r = u - pp.pre_rows[i];
+      const size_t bb = it.L.block_bytes(), cs = (size_t)it.L.n_groups() * NVG;
+      orth_block<T, DS, VW, true, true>(it.L, reinterpret_cast<const T*>(it.blk + (size_t)(j - 1) * bb),
+                                        reinterpret_cast<T*>(it.blk + (size_t)j * bb),
+                                        it.coef + (size_t)2 * (it.k + 2) * cs + (size_t)j * cs, it.sa.partials,
+                                        nullptr, nullptr, 0, r % it.L.gridx, r / it.L.gridx, it.L.gridx);
+      __syncthreads();
+    }
+    if (!grid_barrier(pp.bar, gen)) return;
+    // phase D: Cholesky QR with deflation -> B_j, M_{j+1}, Cp_{j+1}
+    for (int u = blockIdx.x; u < pp.pre_groups[na]; u += gridDim.x) {
+      const int i = packed_item_of(pp.pre_groups, na, u);
+      const PackedItem& it = pp.items[i];
+      const size_t cs = (size_t)it.L.n_groups() * NVG;
+      small_b_group<DS>(it.L, it.sa.partials, it.coef + (size_t)j * cs, it.tb + (size_t)(j - 1) * cs,
+                        it.coef + (size_t)(j + 1) * cs, it.coef + (size_t)(it.k + 2) * cs + (size_t)(j + 1) * cs,
+                        it.thr_abs_sq, it.thr_rel_sq, it.n_rec, it.flags, u - pp.pre_groups[i]);
+      __syncthreads();
+    }
+    if (!grid_barrier(pp.bar, gen)) return;
+  }
 }
 
 inline dim3 grid_of(const Layout& L) { return dim3((unsigned)L.gridx, (unsigned)L.n_slices); }
@@ -1819,6 +2007,43 @@ cudaError_t launch_small_b(const Layout& L, const double* partials, const double
                            L, partials, mz_j, b_out, mz_next, cp_next, thr_abs_sq, thr_rel_sq,
                            n_groups_real, flags)));
   return cudaGetLastError();
+}
+
+template <typename T, int DS, int VW>
+static cudaError_t packed_kernel_info(const void** fn) {
+  *fn = reinterpret_cast<const void*>(k_pass1_packed<T, DS, VW>);
+  return opt_in_smem(*fn);
+}
+
+static cudaError_t packed_fn(int precision, int ds, const void** fn) {
+  Layout L{};
+  L.precision = precision;
+  L.DS = ds;
+  cudaError_t e = cudaErrorInvalidValue;
+  RDM_DISPATCH(L, e = (packed_kernel_info<T, DS, VW>(fn)));
+  return e;
+}
+
+size_t spmm_terms_smem(int precision, int n_flip, int n_diag) {
+  return precision == RDM_FP32 ? terms_smem<float>(n_flip, n_diag) : terms_smem<double>(n_flip, n_diag);
+}
+
+int packed_max_blocks_per_sm(int precision, int ds, size_t smem) {
+  const void* fn = nullptr;
+  if (packed_fn(precision, ds, &fn) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,
+                                cudaStream_t st) {
+  const void* fn = nullptr;
+  cudaError_t e = packed_fn(precision, ds, &fn);
+  if (e != cudaSuccess) return e;
+  PackedPlan arg = pp;
+  void* args[] = {&arg};
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, smem, st);
 }
 
 cudaError_t launch_final_gram(const Layout& L, const void* psi, double* partials,

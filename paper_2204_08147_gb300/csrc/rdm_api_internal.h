@@ -24,9 +24,20 @@ struct HostModel {
 
 struct ServeState;
 
+// Launch shape of the packed first pass chosen by measurement (the autotuner of
+// rdm_estimate_batch): per key (precision, d_s, size class of the batch), the blocks per
+// SM of the cooperative grid that ran fastest. The shape does not change any result
+// (every work unit is one block of a plain launch whatever block runs it).
+struct PackedTuning {
+  std::mutex mu;
+  std::map<uint64_t, int> blocks_per_sm;
+  uint64_t tuning_runs = 0;  // candidate launches timed so far
+};
+
 // Launch statistics with CUDA-event timing on the launching stream.
 enum KernelKind {
   kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply,
+  kKPacked,     // the packed first pass of a batch (one cooperative launch)
   kKHostDense,  // not a kernel: host wall time of the small dense step (eigen + coefficients)
   kKNumKinds
 };
@@ -61,6 +72,7 @@ struct rdm_ctx {
   std::unique_ptr<rdm::ServeState> serve;
   rdm::Profiler prof;
   bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
+  rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete
 };
@@ -127,6 +139,13 @@ struct TermImage {
 void make_term_image(const HostModel& h, TermImage* img);
 // Points ham's device term pointers into `dev`, a device copy of img.bytes.
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
+
+// Runs the items of a batch on stream s with workspace ws (need[i] bytes per item after
+// the packed launches' descriptors); see rdm_estimate_batch.
+rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws_bytes,
+                               rdm_batch_item* items, int n, const size_t* need, Profiler* prof);
+// Workspace of a batch (0 if an item's sizes are invalid); need[i] per item.
+size_t batch_workspace_bytes(const rdm_batch_item* items, int n, size_t usable, size_t* need);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 // Bytes the estimator would use given `avail` bytes (0 if the sizes are invalid).

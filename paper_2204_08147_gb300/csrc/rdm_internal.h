@@ -243,6 +243,42 @@ int gram_stored_max_betas(const Layout& L, int k);
 cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,
                                cudaStream_t st);
 
+// One estimate's first pass inside the packed launch (k_pass1_packed). The layout is
+// the untiled one (blocks of kThreads threads, gridx x n_slices per block-sized
+// phase); blocks blk + j * block_bytes hold W_{j+1} (stored basis); coef holds
+// M_j | Cp_j | Cw_j, each (k + 2) * n_groups * d_s^2 float64.
+struct PackedItem {
+  Layout L;
+  SpmmArgs sa;  // term tables and the partials buffer; the block pointers are set per step
+  char* blk;
+  double* coef;
+  double* ta;
+  double* tb;
+  uint32_t* flags;
+  double thr_abs_sq, thr_rel_sq;
+  int k, n_rec;
+};
+// A packed launch: items sorted by k (largest first); active[j] = items with k >= j;
+// pre_rows / pre_groups: prefix sums over the items of their block-sized units
+// (gridx * n_slices) and of their groups; bar: three zeroed words for the grid barrier
+// (arrivals, generation, error).
+struct PackedPlan {
+  const PackedItem* items;
+  int n_items;
+  int k_max;
+  const int* active;
+  const int* pre_rows;
+  const int* pre_groups;
+  uint32_t* bar;
+};
+// Blocks of the packed kernel that fit one SM with `smem` dynamic bytes (0: unsupported).
+int packed_max_blocks_per_sm(int precision, int ds, size_t smem);
+// Cooperative launch of the packed first pass on `grid` blocks (all co-resident).
+cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,
+                                cudaStream_t st);
+// Dynamic shared memory of the untiled SpMM's term tables.
+size_t spmm_terms_smem(int precision, int n_flip, int n_diag);
+
 constexpr uint32_t kFlagNonFinite = 0x100u;
 
 }  // namespace rdm

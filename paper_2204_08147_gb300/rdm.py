@@ -51,6 +51,11 @@ class Result(C.Structure):
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("ham", C.c_void_p), ("betas", _dp), ("n_beta", C.c_int), ("n_v", C.c_int), ("k", C.c_int),
+                ("seed", C.c_uint64), ("opts", Opts), ("out", C.POINTER(Result)), ("status", C.c_int)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("ms", C.c_double),
                 ("bytes", C.c_double)]
@@ -100,6 +105,8 @@ _sig("rdm_profile", C.c_int, _vp, C.c_int)
 _sig("rdm_set_graphs", C.c_int, _vp, C.c_int)
 _sig("rdm_probe_copy_rate", C.c_int, _vp, C.c_size_t, C.c_int, C.POINTER(C.c_double))
 _sig("rdm_profile_stats", C.c_int, _vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int))
+_sig("rdm_estimate_batch", C.c_int, _vp, C.POINTER(BatchItem), C.c_int)
+_sig("rdm_packed_tuning", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64))
 
 
 class RdmError(RuntimeError):
@@ -241,6 +248,44 @@ class Context:
         _check(_lib.rdm_profile_stats(self.h, arr, 32, C.byref(n)), "rdm_profile_stats")
         return {arr[i].name.decode(): dict(launches=int(arr[i].launches), ms=arr[i].ms, bytes=arr[i].bytes)
                 for i in range(min(n.value, 32))}
+
+    def estimate_batch(self, jobs, full: bool = False) -> list:
+        """Runs several estimates at once (rdm_estimate_batch): `jobs` is a list of dicts
+        with keys ham (a Hamiltonian of this context), betas, n_v, k, seed and optional
+        precision, dist, form, passes, first_vector. Returns one result dict per job (as
+        Hamiltonian.estimate) plus its "status"; raises RdmError if any job failed."""
+        n = len(jobs)
+        items = (BatchItem * n)()
+        keep = []
+        for i, jb in enumerate(jobs):
+            ham = jb["ham"]
+            b = np.ascontiguousarray(np.atleast_1d(jb["betas"]), dtype=np.float64)
+            res = _ResultArrays(len(b), int(jb["n_v"]), int(jb["k"]), ham.d_s, full)
+            o = _opts(jb.get("precision", "fp32"), jb.get("dist", "rademacher"), jb.get("form", "gram"),
+                      jb.get("passes", "auto"), jb.get("first_vector", 0), jb.get("recurrence", "block"))
+            items[i].ham = ham.h
+            items[i].betas = _ptr(b)
+            items[i].n_beta = len(b)
+            items[i].n_v = int(jb["n_v"])
+            items[i].k = int(jb["k"])
+            items[i].seed = int(jb["seed"]) & (2 ** 64 - 1)
+            items[i].opts = o
+            items[i].out = C.pointer(res.struct)
+            keep.append((b, res, o))
+        st = _lib.rdm_estimate_batch(self.h, items, n)
+        outs = []
+        for i, (_, res, o) in enumerate(keep):
+            d = res.as_dict(o.form)
+            d["status"] = int(items[i].status)
+            outs.append(d)
+        _check(st, "rdm_estimate_batch")
+        return outs
+
+    def packed_tuning(self) -> tuple:
+        """(size classes tuned, candidate launches timed) of the batch autotuner."""
+        n, r = C.c_int(), C.c_uint64()
+        _check(_lib.rdm_packed_tuning(self.h, C.byref(n), C.byref(r)), "rdm_packed_tuning")
+        return int(n.value), int(r.value)
 
     def close(self):
         if getattr(self, "h", None):
