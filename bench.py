@@ -56,6 +56,11 @@ def _args():
     p.add_argument("--no-serving", action="store_true", help="skip the serving sub-benchmark")
     p.add_argument("--serving-requests", type=int, default=32)
     p.add_argument("--no-small", action="store_true", help="skip the small-chain latency sub-benchmark")
+    p.add_argument("--serving-stream", action="store_true",
+                   help="only the serving stream: --serving-requests requests with N in --serving-n "
+                        "(default 12..22), at saturation and 0.5x/0.8x/1.0x Poisson load; one JSON line")
+    p.add_argument("--serving-n", default="12,22")
+    p.add_argument("--serving-budget-gib", type=int, default=160)
     p.add_argument("--config", default="c2", choices=["c2", "c3", "c5"],
                    help="c2 = the benchmark line; c3 / c5 = one full-size solve of the long-range "
                         "XXZ configurations (25 spins, 64 vectors, 32 betas; 30 spins, 4 vectors) "
@@ -419,13 +424,15 @@ def run_ours(a):
         l2_rate = ctx.probe_copy_rate(32 << 20)
         dram_rate = ctx.probe_copy_rate(4 << 30)
 
-    serving = None
+    serving = batch = None
     if rank == 0 and not a.no_serving:
         serving = serving_bench(rdm, ctx, a.serving_requests)
-    small = sweep = None
+        batch = batch_bench(rdm, ctx)
+    small = sweep = ladder = None
     if rank == 0 and not a.no_small:
         small = small_chain_bench(rdm, ctx)
         sweep = sweep_bench(rdm, ctx)
+        ladder = ladder_bench(rdm, ctx)
 
     if rank != 0:
         if dist:
@@ -503,8 +510,10 @@ def run_ours(a):
         "plain_fp64": plain,
         "precision_fp32_vs_fp64": precision,
         "serving": serving,
+        "batch": batch,
         "small_chain": small,
         "sweep": sweep,
+        "ladder": ladder,
     }
     if cpu_sample is not None:
         c = W.config_c2(0)
@@ -520,12 +529,13 @@ def run_ours(a):
     return 0
 
 
-def serving_bench(rdm, ctx, n_req: int) -> dict:
-    """Mixed request stream (XXZ or LR-TFIM, N in 12..18, mixed beta grids, n_v, k)
+def serving_bench(rdm, ctx, n_req: int, n_min: int = 12, n_max: int = 18, budget_gib: int = 64) -> dict:
+    """Mixed request stream (XXZ or LR-TFIM, N in n_min..n_max, mixed beta grids, n_v, k)
     through the library's request loop: first all requests at once (saturated
-    throughput), then Poisson arrivals at 0.8x that rate (latency percentiles)."""
-    reqs = W.serving_requests(n_req, seed=20220419, n_min=12, n_max=18)
-    budget = 64 << 30
+    throughput), then Poisson arrivals at 0.5x, 0.8x and 1.0x that rate (latency
+    percentiles from submission to completion)."""
+    reqs = W.serving_requests(n_req, seed=20220419, n_min=n_min, n_max=n_max)
+    budget = budget_gib << 30
 
     def run(gaps):
         ctx.serve_start(budget, max_inflight=4)
@@ -548,13 +558,92 @@ def serving_bench(rdm, ctx, n_req: int) -> dict:
     wall, _ = run([0.0] * n_req)
     rate = n_req / wall
     rng = np.random.default_rng(7)
-    wall2, lat = run(list(rng.exponential(1.0 / (0.8 * rate), size=n_req)))
-    return {"requests": n_req, "saturated_solves_per_s": rate,
-            "poisson_rate_per_s": 0.8 * rate, "poisson_solves_per_s": n_req / wall2,
-            "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)),
-                           "p99": 1000 * float(np.percentile(lat, 99))},
-            "stream": "XXZ/LR-TFIM mix, N 12..18, N_s 1-2, 8-64 betas, n_v 8-64, k 30-100, float32",
+    loads = {}
+    for frac in (0.5, 0.8, 1.0):
+        wall2, lat = run(list(rng.exponential(1.0 / (frac * rate), size=n_req)))
+        loads[f"{frac}x"] = {"rate_per_s": frac * rate, "solves_per_s": n_req / wall2,
+                             "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)),
+                                            "p99": 1000 * float(np.percentile(lat, 99))}}
+    return {"requests": n_req, "saturated_solves_per_s": rate, "poisson": loads,
+            "stream": f"XXZ/LR-TFIM mix, N {n_min}..{n_max}, N_s 1-2, 8-64 betas, n_v 8-64, k 30-100, float32; "
+                      "small requests share packed launches",
             "max_inflight": 4, "budget_gib": budget >> 30}
+
+
+def batch_bench(rdm, ctx, n_req: int = 48) -> dict:
+    """Uneven small instances (the serving stream's XXZ / LR-TFIM mix with N 8..14, N_s 1-2,
+    8-64 betas, n_v 8-64, k 30-100, float32) estimated one at a time through rdm_estimate
+    and all at once through rdm_estimate_batch (their first passes in one persistent
+    cooperative launch), after one warm-up of each (the batch's warm-up runs the
+    autotuner). Host-timed around the blocking calls; the device time of the packed
+    launch and of the per-item launches comes from a profiled repeat."""
+    reqs = W.serving_requests(n_req, seed=20220422, n_min=8, n_max=14)
+    hams = [rdm.Hamiltonian(ctx, r["spec"]) for r in reqs]
+    jobs = [dict(ham=h, betas=r["betas"], n_v=r["n_v"], k=r["k"], seed=r["seed"], precision="fp32")
+            for h, r in zip(hams, reqs)]
+
+    def singles():
+        for jb in jobs:
+            jb["ham"].estimate(jb["betas"], jb["n_v"], jb["k"], jb["seed"], precision="fp32")
+    singles()
+    ctx.estimate_batch(jobs)
+    ctx.synchronize()
+    t0 = time.perf_counter()
+    singles()
+    t_single = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.estimate_batch(jobs)
+    t_batch = time.perf_counter() - t0
+    ctx.profile(True)
+    singles()
+    st_single = ctx.profile_stats()
+    ctx.profile(True)
+    ctx.estimate_batch(jobs)
+    st_batch = ctx.profile_stats()
+    ctx.profile(False)
+    for h in hams:
+        h.close()
+    keys, runs = ctx.packed_tuning()
+
+    def dev(st):
+        return {"launches": sum(v["launches"] for k, v in st.items() if k != "host_small_dense"),
+                "host_small_dense_ms": st.get("host_small_dense", {}).get("ms")}
+    return {"requests": n_req, "stream": "XXZ/LR-TFIM mix, N 8..14, N_s 1-2, 8-64 betas, n_v 8-64, k 30-100, "
+                                         "float32",
+            "one_by_one_solves_per_s": n_req / t_single, "batched_solves_per_s": n_req / t_batch,
+            "speedup": t_single / t_batch, "one_by_one": dev(st_single), "batched": dev(st_batch),
+            "packed_pass1_ms": st_batch.get("packed_pass1", {}).get("ms"),
+            "autotuner": {"size_classes": keys, "candidate_launches": runs}}
+
+
+def ladder_bench(rdm, ctx) -> dict:
+    """The ladder of Sec. 5.2 (10 rungs, J_leg = 1, J_rung = -0.45, h = 1, system = rung 2,
+    k = 30, n_v = 50, 16 betas in [0.1, 10], float32), its sites numbered leg by leg:
+    solves with the library's bath-bit order (chosen from the coupling graph) and with
+    the caller's order, SpMM time per launch from per-launch events."""
+    spec = W.spin_ladder(10, 2, numbering="leg")
+    order, before, after = rdm.bath_order(spec)
+    betas = W.beta_grid(16, 0.1, 10.0)
+    out = {"workload": "xy_ladder_L10_sys_rung2_leg_numbered_nv50_k30_16beta_fp32",
+           "partner_tiles_caller_order": before, "partner_tiles_chosen_order": after}
+    for name, on in (("chosen_order", True), ("caller_order", False)):
+        ctx.set_bath_order(on)
+        ham = rdm.Hamiltonian(ctx, spec)
+        ham.estimate(betas, 50, 30, 20220423, precision="fp32", dist="gauss")
+        ctx.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ham.estimate(betas, 50, 30, 20220423, precision="fp32", dist="gauss")
+        dt = (time.perf_counter() - t0) / 3
+        ctx.profile(True)
+        ham.estimate(betas, 50, 30, 20220423, precision="fp32", dist="gauss")
+        st = ctx.profile_stats()
+        ctx.profile(False)
+        ham.close()
+        sp = st["spmm_pass1"]
+        out[name] = {"ms_per_solve": 1000 * dt, "spmm_ms_per_launch": sp["ms"] / max(1, sp["launches"])}
+    ctx.set_bath_order(True)
+    return out
 
 
 def small_chain_bench(rdm, ctx, n_solves: int = 50) -> dict:
@@ -740,6 +829,14 @@ def main():
         return run_reference(a)
     if a.config != "c2":
         return run_config(a)
+    if a.serving_stream:
+        from paper_2204_08147_gb300 import rdm
+        lo, hi = (int(x) for x in a.serving_n.split(","))
+        ctx = rdm.Context(0)
+        line = serving_bench(rdm, ctx, a.serving_requests, lo, hi, a.serving_budget_gib)
+        print(json.dumps({"serving_stream": line}))
+        ctx.close()
+        return 0
     return run_ours(a)
 
 

@@ -238,6 +238,24 @@ rdm_status rdm_build_bath_hamiltonian(rdm_ctx* ctx, const rdm_model* model, rdm_
  * the system; the basis order of rho). RDM_EINVAL as rdm_build_hamiltonian. */
 rdm_status rdm_system_hamiltonian(const rdm_model* model, double* hs_out);
 
+/* Bath-bit order. rdm_build_hamiltonian may store a Hamiltonian with its bath sites in
+ * another order than the caller's: the order that minimises the partner tiles the
+ * tiled SpMM copies per tile (flip masks are grouped by their bits above the tile's
+ * 10 in-tile bits; sites coupled to many others belong in the tile), found by a
+ * deterministic local search over transpositions of bath sites from the coupling graph
+ * (the ladder of Sec. 5.2 goes from 15 to 11-12 partner tiles). Only the device layout
+ * changes: rdm_estimate draws the bath vectors in the caller's bath order, so results
+ * equal those of the caller's order up to rounding, and rdm_apply_hamiltonian /
+ * rdm_starting_block keep the caller's state order. The paper has no counterpart.
+ * rdm_set_bath_order(ctx, 0) keeps the caller's order for Hamiltonians built afterwards
+ * on ctx (default 1). rdm_bath_order (host only, no device) reports the order chosen for
+ * a model: order_out[q] = caller site at internal site q (n_sites entries; system sites
+ * unchanged), and the average partner tiles per tile in the caller's order and in the
+ * chosen one. Any output pointer may be NULL; RDM_EINVAL as rdm_build_hamiltonian. */
+rdm_status rdm_set_bath_order(rdm_ctx* ctx, int enable);
+rdm_status rdm_bath_order(const rdm_model* model, int* order_out, double* tiles_caller,
+                          double* tiles_chosen);
+
 /* Sizes and the bound ||H||_2 <= sum of |term coefficients| used to scale the
  * Lanczos breakdown tolerance. Any output pointer may be NULL. */
 rdm_status rdm_hamiltonian_info(const rdm_ham* ham, int* n_sites, int* n_sys,

@@ -106,6 +106,115 @@ rdm_status compile_model(const rdm_model* m, HostModel* out) {
   return RDM_OK;
 }
 
+double partner_tiles(const HostModel& h) {
+  struct G {
+    int n = 0;
+    bool low_free = true;
+    bool parity_only = false;
+  };
+  std::map<uint32_t, G> groups;
+  const uint32_t low = (1u << kTileBits) - 1u;
+  for (const FlipTerm& f : h.flips) {
+    const uint32_t hi = f.mask >> kTileBits;
+    if (!hi) continue;
+    G& g = groups[hi];
+    g.n++;
+    g.low_free = g.low_free && (f.mask & low) == 0;
+    g.parity_only = (f.c_odd == 0.0) != (f.c_even == 0.0);
+  }
+  double t = 0.0;
+  for (const auto& kv : groups) t += (kv.second.low_free && kv.second.n == 1 && kv.second.parity_only) ? 0.5 : 1.0;
+  return t;
+}
+
+// Masks of h with the bath bits moved: internal bath bit i takes old bit src[i].
+static HostModel permute_bath(const HostModel& h, const std::vector<uint8_t>& src) {
+  const int nb = h.n - h.ns;
+  HostModel o = h;
+  auto map = [&](uint32_t m) {
+    uint32_t r = m & ~((1u << nb) - 1u);  // system bits stay
+    for (int i = 0; i < nb; ++i) r |= ((m >> src[i]) & 1u) << i;
+    return r;
+  };
+  for (FlipTerm& f : o.flips) f.mask = map(f.mask);
+  for (DiagTerm& d : o.diags) d.mask = map(d.mask);
+  o.bath_src = src;
+  return o;
+}
+
+// Partner-tile count of flip masks `m` (parity-only flags `po`) after moving bath bit
+// src[i] to bit i: the same count as partner_tiles, on bare masks (the search's inner
+// loop).
+static double partner_tiles_of(const std::vector<uint32_t>& m, const std::vector<char>& po,
+                               const std::vector<uint8_t>& src, int nb, std::vector<std::pair<uint32_t, uint32_t>>& w) {
+  w.clear();
+  const uint32_t low = (1u << kTileBits) - 1u, sys = ~((1u << nb) - 1u);
+  for (size_t t = 0; t < m.size(); ++t) {
+    uint32_t r = m[t] & sys;
+    for (int i = 0; i < nb; ++i) r |= ((m[t] >> src[i]) & 1u) << i;
+    if (r >> kTileBits) w.emplace_back(r >> kTileBits, (r & low) ? 2u : (po[t] ? 0u : 1u));
+  }
+  std::sort(w.begin(), w.end());
+  double c = 0.0;
+  for (size_t i = 0; i < w.size();) {
+    size_t j = i;
+    while (j < w.size() && w[j].first == w[i].first) ++j;
+    c += (j - i == 1 && w[i].second == 0u) ? 0.5 : 1.0;
+    i = j;
+  }
+  return c;
+}
+
+// Local search over transpositions of bath bits, restarted from shuffled orders (a
+// fixed pseudo-random sequence, so a model always gets the same order); kept only if it
+// lowers the partner-tile count.
+void order_bath_bits(HostModel* h) {
+  const int nb = h->n - h->ns;
+  if (h->n <= kTileBits || nb < 2 || nb > 30) return;
+  std::vector<uint32_t> m;
+  std::vector<char> po;
+  for (const FlipTerm& f : h->flips) {
+    m.push_back(f.mask);
+    po.push_back((f.c_odd == 0.0) != (f.c_even == 0.0));
+  }
+  std::vector<uint8_t> cur(nb);
+  for (int i = 0; i < nb; ++i) cur[i] = (uint8_t)i;
+  std::vector<std::pair<uint32_t, uint32_t>> w;
+  const double c0 = partner_tiles_of(m, po, cur, nb, w);
+  if (c0 == 0.0 || m.empty()) return;
+  double best = c0;
+  uint64_t x = 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    return x;
+  };
+  // 8 descents (from the caller's order, then from shuffled orders), the best kept
+  const int iters = (int)std::min<size_t>(20000, 4000000 / (m.size() * (size_t)nb + 1) + 200);
+  std::vector<uint8_t> best_order = cur;
+  for (int start = 0; start < 8; ++start) {
+    if (start > 0)
+      for (int i = nb - 1; i > 0; --i) std::swap(cur[i], cur[(int)(next() % (uint64_t)(i + 1))]);
+    double c_run = partner_tiles_of(m, po, cur, nb, w);
+    for (int it = 0; it < iters; ++it) {
+      const int a = (int)(next() % (uint64_t)nb), b = (int)(next() % (uint64_t)nb);
+      if (a == b) continue;
+      std::swap(cur[a], cur[b]);
+      const double c = partner_tiles_of(m, po, cur, nb, w);
+      if (c <= c_run)
+        c_run = c;
+      else
+        std::swap(cur[a], cur[b]);
+    }
+    if (c_run < best) {
+      best = c_run;
+      best_order = cur;
+    }
+  }
+  if (best < c0) *h = permute_bath(*h, best_order);
+}
+
 // Sorted distinct m_lo of the diagonal terms with both a high and a low part (TileDiag).
 static std::vector<uint32_t> tile_diag_mlo(const HostModel& h) {
   std::vector<uint32_t> lo;
@@ -321,9 +430,9 @@ rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, in
   l.VW = precision == RDM_FP32 ? 4 : (l.DS == 4 ? 4 : 2);
   int cols = (1 << h.ns) * n_v;
   int bcols;
-  if (l.VW * l.elem == 16 && h.n >= kTileBits) {
-    // tiled layout: narrow slices of kTiledLanes vectors per row
-    const int sc = l.VW * kTiledLanes;
+  if ((16 * kTiledLanes / l.elem) % l.DS == 0 && h.n >= kTileBits) {
+    // tiled layout: narrow slices of kTiledLanes 16-byte vectors per row (32 bytes)
+    const int sc = 16 * kTiledLanes / l.elem;
     bcols = (cols + sc - 1) / sc * sc;
     l.Bs = sc;
   } else if (cols >= 128 / l.elem) {
@@ -599,19 +708,66 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   HostModel hm;
   rdm_status st = compile_model(model, &hm);
   if (st != RDM_OK) return st;
-  std::unique_ptr<rdm_ham> h(new rdm_ham());
-  h->ctx = ctx;
-  h->device = ctx->device;
-  h->model = std::move(hm);
+  HostModel caller_order;
+  if (ctx->bath_order) {
+    caller_order = hm;
+    order_bath_bits(&hm);
+  }
   CK(cudaSetDevice(ctx->device));
-  TermImage img;
-  make_term_image(h->model, &img);
-  CK(cudaMalloc(&h->d_terms, img.bytes.size()));
-  bind_terms(img, reinterpret_cast<char*>(h->d_terms), h.get());
-  CK(cudaMemcpyAsync(h->d_terms, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  *out = h.release();
+  auto upload = [&](HostModel&& m, rdm_ham** o) -> rdm_status {
+    std::unique_ptr<rdm_ham> h(new rdm_ham());
+    h->ctx = ctx;
+    h->device = ctx->device;
+    h->model = std::move(m);
+    TermImage img;
+    make_term_image(h->model, &img);
+    CK(cudaMalloc(&h->d_terms, img.bytes.size()));
+    bind_terms(img, reinterpret_cast<char*>(h->d_terms), h.get());
+    CK(cudaMemcpyAsync(h->d_terms, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *o = h.release();
+    return RDM_OK;
+  };
+  const bool reordered = !hm.bath_src.empty();
+  rdm_ham* h = nullptr;
+  st = upload(std::move(hm), &h);
+  if (st != RDM_OK) return st;
+  if (reordered) {
+    st = upload(std::move(caller_order), &h->caller);
+    if (st != RDM_OK) {
+      rdm_destroy_hamiltonian(h);
+      return st;
+    }
+  }
+  *out = h;
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_set_bath_order(rdm_ctx* ctx, int enable) {
+  if (!ctx) {
+    set_error("rdm_set_bath_order: NULL context");
+    return RDM_EINVAL;
+  }
+  ctx->bath_order = enable != 0;
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_bath_order(const rdm_model* model, int* order_out, double* tiles_caller,
+                                     double* tiles_chosen) {
+  HostModel hm;
+  rdm_status st = compile_model(model, &hm);
+  if (st != RDM_OK) return st;
+  const double c0 = partner_tiles(hm);
+  order_bath_bits(&hm);
+  if (tiles_caller) *tiles_caller = c0;
+  if (tiles_chosen) *tiles_chosen = partner_tiles(hm);
+  if (order_out) {
+    const int n = hm.n;
+    for (int q = 0; q < n; ++q) order_out[q] = q;
+    // internal site q is bit n-1-q; a bath bit i carries the caller's bit bath_src[i]
+    for (int i = 0; i < (int)hm.bath_src.size(); ++i) order_out[n - 1 - i] = n - 1 - hm.bath_src[i];
+  }
   return RDM_OK;
 }
 
@@ -694,6 +850,7 @@ void rdm::Pass1Graph::reset() {
 // is still running when it is destroyed.
 extern "C" void rdm_destroy_hamiltonian(rdm_ham* ham) {
   if (!ham) return;
+  if (ham->caller) rdm_destroy_hamiltonian(ham->caller);
   cudaSetDevice(ham->device);
   if (ham->d_terms) cudaFree(ham->d_terms);
   for (void* p : ham->d_apply_aux)
@@ -730,6 +887,7 @@ extern "C" rdm_status rdm_apply_hamiltonian(rdm_ham* ham, int precision, const v
     set_error("rdm_apply_hamiltonian: bad precision %d", precision);
     return RDM_EINVAL;
   }
+  ham = ham->caller_view();  // x and y are in the caller's state order
   Layout L;
   rdm_status st = plan_single(ham->model, n_cols, precision, 1, &L);
   if (st != RDM_OK) return st;
@@ -799,6 +957,7 @@ extern "C" rdm_status rdm_starting_block(rdm_ham* ham, int precision, int n_v, u
     set_error("rdm_starting_block: bad distribution %d", dist);
     return RDM_EINVAL;
   }
+  ham = ham->caller_view();  // x is in the caller's state order
   const int ds = 1 << ham->model.ns;
   if (dist == RDM_BASIS && (int64_t)n_v > (int64_t(1) << (ham->model.n - ham->model.ns))) {
     set_error("rdm_starting_block: RDM_BASIS needs n_v <= d_b");
@@ -1015,7 +1174,15 @@ class EstimateRun {
         o(o_), out(out_), prof(prof_) {}
   rdm_status prepare(char* ws, size_t ws_bytes);
   rdm_status pass1();
-  rdm_status finish();
+  rdm_status finish();  // fetch_t, every dense_task, finish_rest
+  // finish() in stages, so a batch can run the dense steps of all its items in one
+  // parallel pass: fetch_t copies T back; dense_task(r) is recurrence r's small dense step
+  // (thread-safe across r); finish_rest does the Gram form and the normalisation.
+  rdm_status fetch_t();
+  int n_dense_tasks() const { return n_rec; }
+  void dense_task(int r);
+  rdm_status finish_rest();
+  double host_ms_dense = 0.0;
   // Whether the packed launch can take this estimate's first pass (stored basis, one
   // recurrence of block size d_s per bath vector, a block of at most kPackedMaxBlock
   // bytes), and its description for that launch.
@@ -1061,6 +1228,8 @@ class EstimateRun {
   double blk_b = 0;
   uint64_t h2d = 0, d2h = 0;
   int cur = 0, prv = -1, nxt = 1;
+  std::vector<double> ta, tb, mz, cstore, tmin;
+  std::vector<char> okv;
 
   double* MZ(int j) const { return coef + (size_t)j * cstride; }  // j = 1..k+1
   double* CP(int j) const { return coef + (size_t)(k + 2) * cstride + (size_t)j * cstride; }
@@ -1079,14 +1248,25 @@ class EstimateRun {
     return launch();
   }
   rdm_status init_block(char* w) {
+    const BathPerm bp = hm.perm();  // bath vectors drawn in the caller's bath order
     CK(timed(kKInit, blk_b, [&] {
-      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s, sub);
+      return launch_init_block(L, o->vec_dist, seed, o->first_vector, n_v, nullptr, d_vbuf, w, s, sub, &bp);
     }));
     return RDM_OK;
   }
 };
 
 constexpr size_t kPackedMaxBlock = size_t(64) << 20;
+
+size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o) {
+  if (o->recurrence != RDM_BLOCK) return 0;
+  rdm_opts q = *o;
+  q.passes = RDM_PASSES_STORE;
+  Plan p;
+  if (make_plan(h, n_beta, n_v, k, &q, SIZE_MAX, &p) != RDM_OK) return 0;
+  if (!p.store || p.single || p.L.block_bytes() > kPackedMaxBlock) return 0;
+  return (plan_bytes(p) + 255) / 256 * 256;
+}
 
 rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
   rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p);
@@ -1276,9 +1456,10 @@ rdm_status EstimateRun::pass1() {
   return st;
 }
 
-rdm_status EstimateRun::finish() {
-  rdm_status st = RDM_OK;
-  std::vector<double> ta((size_t)k * cstride), tb((size_t)k * cstride), mz((size_t)(k + 1) * cstride);
+rdm_status EstimateRun::fetch_t() {
+  ta.assign((size_t)k * cstride, 0.0);
+  tb.assign((size_t)k * cstride, 0.0);
+  mz.assign((size_t)(k + 1) * cstride, 0.0);
   uint32_t flags[4];
   CK(cudaMemcpyAsync(ta.data(), d_ta, ta.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(tb.data(), d_tb, tb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1294,25 +1475,42 @@ rdm_status EstimateRun::finish() {
     set_error("non-finite Lanczos coefficient (overflow or invalid model)");
     return RDM_ENUMERIC;
   }
-
   // ---- small dense step (host float64): f(T_r) E1 for every beta (eq. fT) with the
   // per-recurrence shift t_min(r); E0 = min_r t_min(r) (Sec. 3.2), then rescaling. A
   // recurrence r is bath vector r (block) or column r = l dso + i (single).
   const int n = k * ds;
-  std::vector<double> cstore((size_t)n_rec * n_beta * n * ds);
-  std::vector<double> tmin(n_rec, 0.0);
-  std::vector<char> okv(n_rec, 1);
+  cstore.assign((size_t)n_rec * n_beta * n * ds, 0.0);
+  tmin.assign(n_rec, 0.0);
+  okv.assign(n_rec, 1);
+  return RDM_OK;
+}
+
+void EstimateRun::dense_task(int r) {
+  const int n = k * ds;
+  std::vector<double> t;
+  build_t(ds, k, ng, r, ta, tb, t);
+  okv[r] = tdense_fT(n, ds, t.data(), n_beta, betas, &tmin[r], &cstore[(size_t)r * n_beta * n * ds]);
+}
+
+rdm_status EstimateRun::finish() {
+  rdm_status st = fetch_t();
+  if (st != RDM_OK) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  parallel_for(n_rec, [&](int r) { dense_task(r); });
+  host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return finish_rest();
+}
+
+rdm_status EstimateRun::finish_rest() {
+  rdm_status st = RDM_OK;
+  const int n = k * ds;
+  uint32_t flags[4];
+  double host_ms = host_ms_dense;
   const auto host_t0 = std::chrono::steady_clock::now();
-  double host_ms = 0.0;
   auto host_lap = [&]() {
     const auto t1 = std::chrono::steady_clock::now();
     return std::chrono::duration<double, std::milli>(t1 - host_t0).count();
   };
-  parallel_for(n_rec, [&](int r) {
-    std::vector<double> t;
-    build_t(ds, k, ng, r, ta, tb, t);
-    okv[r] = tdense_fT(n, ds, t.data(), n_beta, betas, &tmin[r], &cstore[(size_t)r * n_beta * n * ds]);
-  });
   double e0 = INFINITY;
   for (int r = 0; r < n_rec; ++r) {
     if (!okv[r]) {
@@ -1609,9 +1807,11 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
     if (e == cudaSuccess) e = launch_pass1_packed(precision, ds, pp, grid, smem, s);
     return e;
   };
-  // Autotuner: key = (precision, d_s, log2 of the block-sized units of the batch).
+  // Autotuner: key = (precision, d_s, size class = log2 of the block-sized units of the
+  // batch, in steps of 3 (a factor 8)).
   int lg = 0;
   while ((1 << lg) < pre_rows[n]) ++lg;
+  lg /= 3;
   const uint64_t key = (uint64_t)precision | ((uint64_t)ds << 4) | ((uint64_t)lg << 8);
   int bpsm = 0;
   {
@@ -1702,24 +1902,41 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
       for (int i : idx) items[i].status = items[i].status == RDM_OK ? RDM_OK : items[i].status;
       for (int i : idx) runs[i]->packed_done = true;
     }
+  // first passes of the other items, then every item's T back to the host
   for (int i = 0; i < n; ++i) {
     if (items[i].status != RDM_OK) continue;
     rdm_status st = runs[i]->packed_done ? RDM_OK : runs[i]->pass1();
-    if (st == RDM_OK) st = runs[i]->finish();
+    if (st == RDM_OK) st = runs[i]->fetch_t();
+    items[i].status = st;
+    if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
+  }
+  // the small dense steps of all items in one pass over the host worker pool
+  std::vector<std::pair<int, int>> tasks;
+  for (int i = 0; i < n; ++i)
+    if (items[i].status == RDM_OK)
+      for (int r = 0; r < runs[i]->n_dense_tasks(); ++r) tasks.emplace_back(i, r);
+  const auto t0 = std::chrono::steady_clock::now();
+  parallel_for((int)tasks.size(), [&](int t) { runs[tasks[t].first]->dense_task(tasks[t].second); });
+  const double dense_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < n; ++i) {
+    if (items[i].status != RDM_OK) continue;
+    // the pass's wall time, shared out by the items' task counts
+    runs[i]->host_ms_dense = tasks.empty() ? 0.0 : dense_ms * runs[i]->n_dense_tasks() / (double)tasks.size();
+    const rdm_status st = runs[i]->finish_rest();
     items[i].status = st;
     if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
   }
   return first_bad;
 }
 
-size_t batch_workspace_bytes(const rdm_batch_item* items, int n, size_t usable, size_t* need) {
+size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* avail, size_t* need) {
   int k_max = 1;
   for (int i = 0; i < n; ++i) k_max = std::max(k_max, items[i].k);
   size_t tot = 6 * packed_meta_bytes(n, k_max);
   for (int i = 0; i < n; ++i) {
     rdm_status st = RDM_OK;
     need[i] = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k, &items[i].opts,
-                             usable, &st);
+                             avail[i], &st);
     if (need[i] == 0) return 0;
     need[i] = (need[i] + 255) / 256 * 256;
     tot += need[i];
@@ -1772,10 +1989,12 @@ extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, in
     std::vector<size_t> need;
     size_t tot = 0;
     size_t i1 = i0;
+    std::vector<size_t> avail;
     while (i1 < ok_items.size()) {
       sub.push_back(*ok_items[i1]);
       need.assign(sub.size(), 0);
-      const size_t t2 = batch_workspace_bytes(sub.data(), (int)sub.size(), usable, need.data());
+      avail.assign(sub.size(), usable);
+      const size_t t2 = batch_workspace_bytes(sub.data(), (int)sub.size(), avail.data(), need.data());
       if (t2 == 0 || (t2 > usable && i1 > i0)) {
         sub.pop_back();
         break;
@@ -1784,7 +2003,8 @@ extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, in
       ++i1;
     }
     need.assign(sub.size(), 0);
-    tot = batch_workspace_bytes(sub.data(), (int)sub.size(), usable, need.data());
+    avail.assign(sub.size(), usable);
+    tot = batch_workspace_bytes(sub.data(), (int)sub.size(), avail.data(), need.data());
     char* ws = ctx->ws;
     rdm_status st = RDM_OK;
     if (tot > usable) {

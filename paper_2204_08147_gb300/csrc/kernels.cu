@@ -182,7 +182,7 @@ __global__ void k_gauss_finish(int n_v, int gx, const double* part, double* inv_
 template <typename T, int DS, int VW>
 __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uint64_t seed,
                                                          int64_t l0, int nvr, const double* inv_norm,
-                                                         const T* vbuf, T* W, int sub) {
+                                                         const T* vbuf, T* W, int sub, BathPerm bp) {
   constexpr int NG = VW / DS;
   const int tpr = L.TPR, rpb = kThreads / tpr;
   const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
@@ -193,7 +193,12 @@ __global__ void __launch_bounds__(kThreads) k_init_block(Layout L, int dist, uin
   const double rad = 1.0 / sqrt((double)(1ull << L.n_bath_bits));
   for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
     const int i = (int)(s >> L.n_bath_bits);
-    const uint64_t b = (uint64_t)s & bmask;
+    uint64_t b = (uint64_t)s & bmask;
+    if (bp.n) {  // the caller's bath index of internal bath index b
+      uint64_t bc = 0;
+      for (int q = 0; q < bp.n; ++q) bc |= ((b >> q) & 1ull) << bp.src[q];
+      b = bc;
+    }
     T v[VW];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
@@ -719,9 +724,15 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr int LPR = kTiledLanes;          // 16-byte vectors per row
   constexpr int BS = VW * LPR;              // elements per row of a slice
-  constexpr int NG = VW / DS;
+  // HG: a bath-vector group is wider than one lane's 16-byte vector (float64 with
+  // d_s = 4: the group is the whole 32-byte row, half in each of the row's two lanes).
+  // Its mixing and partial sums then take the other lane's half by a shuffle.
+  constexpr bool HG = DS > VW;
+  static_assert(!HG || DS == VW * LPR, "a wide group spans exactly the lanes of a row");
+  constexpr int NG = HG ? 1 : VW / DS;
   constexpr int NVG = DS * DS;
-  constexpr int NV = NG * NVG;
+  constexpr int NV = HG ? DS * VW : NG * NVG;  // partial sums per thread
+  constexpr int NVC = HG ? NVG : NV;           // mixing coefficients per lane
   constexpr int RG = kConsumerWarps * 32 / LPR;  // row groups
   constexpr int RGL = (RG >= 256) ? 8 : (RG >= 128) ? 7 : (RG >= 64) ? 6 : 5;  // log2(RG)
   constexpr int RPT = kTileRows / RG;            // rows per consumer thread
@@ -901,7 +912,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   // of); every (slice, block) entry is written once.
   const int gs = BS / DS;
   auto partial_base = [&](int slice) -> size_t {
-    return ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (size_t)threadIdx.x * NG) * NVG;
+    return ((size_t)(slice * gridDim.x + blockIdx.x) * gs + (HG ? 0 : (size_t)threadIdx.x * NG)) * NVG;
+  };
+  // Entry e of a lane's partial sums in its group's DS x DS block: (i, j) = (e / VW,
+  // lane * VW + e % VW) for wide groups (lane = threadIdx.x here, < LPR).
+  auto partial_entry = [&](int e) -> int {
+    return HG ? (e / VW) * DS + (int)threadIdx.x * VW + e % VW : e;
   };
 
   T acc[NV];  // W_j^T Z sums of this lane's bath-vector groups
@@ -940,22 +956,22 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
             for (int e = 0; e < NV; ++e) {
               double sum = 0.0;
               for (int w = 0; w < kConsumerWarps; ++w) sum += red[(w * LPR + threadIdx.x) * 16 + e];
-              a.partials[base + e] = sum;
+              a.partials[base + partial_entry(e)] = sum;
             }
           }
           unwritten = cur + 1;
         }
         if (threadIdx.x < LPR)
           for (int c = unwritten; c < slice; ++c)
-            for (int e = 0; e < NV; ++e) a.partials[partial_base(c) + e] = 0.0;
+            for (int e = 0; e < NV; ++e) a.partials[partial_base(c) + partial_entry(e)] = 0.0;
         unwritten = slice;
       }
       if (slice >= L.n_slices) break;
       cur = slice;
       Z = reinterpret_cast<T*>(a.z) + (size_t)slice * L.D * BS;
       consumers_sync_or(false);  // the previous slice's coefficients have been read
-      if (MODE != kModeApply && threadIdx.x < LPR * NV) {
-        const int ln = threadIdx.x / NV, e = threadIdx.x % NV;
+      if (MODE != kModeApply && threadIdx.x < LPR * NVC) {
+        const int ln = threadIdx.x / NVC, e = threadIdx.x % NVC;
         const size_t gidx = (size_t)((slice * BS + ln * VW) / DS) * NVG + e;
         s_mz[ln * 16 + e] = (T)a.mz[gidx];
         s_cp[ln * 16 + e] = has_prev ? (T)a.cp[gidx] : (T)0;
@@ -1114,12 +1130,63 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       // so they hold no registers while the partner tiles are consumed. M_j is upper
       // triangular (the inverse Cholesky factor, exact zeros below the diagonal), so
       // z = y M_j skips the zero products: the same fma chain, ended early.
-      T mz[NV], cp[NV];
+      T mz[NVC], cp[NVC];
 #pragma unroll
-      for (int e = 0; e < NV; ++e) {
+      for (int e = 0; e < NVC; ++e) {
         mz[e] = s_mz[lane * 16 + e];
         cp[e] = s_cp[lane * 16 + e];
       }
+      if constexpr (HG) {
+        // the row's DS columns: this lane holds columns lane*VW .. lane*VW+VW-1; the whole
+        // row of Z is formed (static register indices) and the lane keeps its half
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          T yf[DS], xf[DS], zf[DS];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            const T yo = __shfl_xor_sync(0xffffffffu, y[m][v], 1);
+            const T xx = __shfl_xor_sync(0xffffffffu, xo[m][v], 1);
+            yf[v] = lane == 0 ? y[m][v] : yo;
+            yf[VW + v] = lane == 0 ? yo : y[m][v];
+            xf[v] = lane == 0 ? xo[m][v] : xx;
+            xf[VW + v] = lane == 0 ? xx : xo[m][v];
+          }
+#pragma unroll
+          for (int j = 0; j < DS; ++j) {
+            T t = (T)0;
+#pragma unroll
+            for (int i = 0; i <= j; ++i) t = fma(yf[i], mz[i * DS + j], t);
+            zf[j] = t;
+          }
+          if (has_prev) {
+            T xp[VW], pf[DS];
+            VecIO<T, VW>::ld_rw(xp, Pp + rgoff + m * kStep);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+              const T po = __shfl_xor_sync(0xffffffffu, xp[v], 1);
+              pf[v] = lane == 0 ? xp[v] : po;
+              pf[VW + v] = lane == 0 ? po : xp[v];
+            }
+#pragma unroll
+            for (int j = 0; j < DS; ++j) {
+              T t = zf[j];
+#pragma unroll
+              for (int i = 0; i < DS; ++i) t = fma(pf[i], cp[i * DS + j], t);
+              zf[j] = t;
+            }
+          }
+          T z[VW];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) z[v] = lane == 0 ? zf[v] : zf[VW + v];
+          VecIO<T, VW>::st_cs(zrow + m * kStep, z);
+          if (MODE == kModePass1) {
+#pragma unroll
+            for (int i = 0; i < DS; ++i)
+#pragma unroll
+              for (int jj = 0; jj < VW; ++jj) acc[i * VW + jj] = fma(xf[i], z[jj], acc[i * VW + jj]);
+          }
+        }
+      } else
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
         T z[VW];
@@ -1871,10 +1938,15 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, 
 
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
                               const double* inv_norm, const void* vbuf, void* W, cudaStream_t st,
-                              int sub) {
+                              int sub, const BathPerm* bp) {
+  BathPerm id{};
+  const BathPerm perm = bp ? *bp : id;
+  if (perm.n < 0 || perm.n > L.n_bath_bits) return cudaErrorInvalidValue;
+  for (int q = 0; q < perm.n; ++q)
+    if (perm.src[q] >= perm.n) return cudaErrorInvalidValue;
   RDM_DISPATCH(L, (k_init_block<T, DS, VW><<<grid_of(L), kThreads, 0, st>>>(
                       L, dist, seed, l0, n_v_real, inv_norm, reinterpret_cast<const T*>(vbuf),
-                      reinterpret_cast<T*>(W), sub)));
+                      reinterpret_cast<T*>(W), sub, perm)));
   return cudaGetLastError();
 }
 
@@ -1944,7 +2016,8 @@ cudaError_t launch_spmm(const Layout& L, int mode, const SpmmArgs& a, cudaStream
       return p1 ? launch_tiled<float, 4, kModePass1>(L, a, st) : launch_tiled<float, 4, kModePass2>(L, a, st);
     }
     if (L.DS == 1) return p1 ? launch_tiled<double, 1, kModePass1>(L, a, st) : launch_tiled<double, 1, kModePass2>(L, a, st);
-    return p1 ? launch_tiled<double, 2, kModePass1>(L, a, st) : launch_tiled<double, 2, kModePass2>(L, a, st);
+    if (L.DS == 2) return p1 ? launch_tiled<double, 2, kModePass1>(L, a, st) : launch_tiled<double, 2, kModePass2>(L, a, st);
+    return p1 ? launch_tiled<double, 4, kModePass1>(L, a, st) : launch_tiled<double, 4, kModePass2>(L, a, st);
   }
   RDM_DISPATCH(L, {
     const size_t sm = terms_smem<T>(a.n_flip, a.n_diag);

@@ -78,6 +78,7 @@ extern "C" rdm_status rdm_starting_block_noalloc(rdm_ham* ham, int precision, in
     set_error("rdm_starting_block_noalloc: bad precision %d", precision);
     return RDM_EINVAL;
   }
+  ham = ham->caller_view();  // x is in the caller's state order
   const HostModel& h = ham->model;
   const int ds = 1 << h.ns;
   if (dist == RDM_BASIS && (int64_t)n_v > (int64_t(1) << (h.n - h.ns))) {

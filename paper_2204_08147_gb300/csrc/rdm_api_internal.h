@@ -20,6 +20,14 @@ struct HostModel {
   double hnorm = 0.0;  // sum of |coefficients|, an upper bound on ||H||_2
   std::vector<FlipTerm> flips;
   std::vector<DiagTerm> diags;
+  // internal bath bit i carries the caller's bath bit bath_src[i] (empty: caller's order)
+  std::vector<uint8_t> bath_src;
+  BathPerm perm() const {
+    BathPerm p{};
+    p.n = (int)bath_src.size();
+    for (int i = 0; i < p.n; ++i) p.src[i] = bath_src[i];
+    return p;
+  }
 };
 
 struct ServeState;
@@ -72,6 +80,7 @@ struct rdm_ctx {
   std::unique_ptr<rdm::ServeState> serve;
   rdm::Profiler prof;
   bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
+  bool bath_order = true;  // rdm_build_hamiltonian reorders bath bits for the tiled SpMM
   rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete
@@ -109,12 +118,24 @@ struct rdm_ham {
   rdm::TiledTerms tiled{};
   void* d_apply_aux[2] = {};  // tiled apply: error word + K table (float64, float32)
   rdm::Pass1Graph graph;
+  // With reordered bath bits: the same model in the caller's order, for the entry points
+  // whose device blocks are in the caller's state order (apply, starting block).
+  rdm_ham* caller = nullptr;
+  rdm_ham* caller_view() { return caller ? caller : this; }
 };
 
 namespace rdm {
 
 void set_error(const char* fmt, ...);
 rdm_status compile_model(const rdm_model* m, HostModel* out);
+// Partner tiles a 2^kTileBits-state tile of the tiled SpMM copies, on average, for this
+// term list: one per distinct high part of the flip masks, half for a group that only
+// hops a pair of high spins with a parity-only coefficient (the tiles where that pair is
+// antiparallel).
+double partner_tiles(const HostModel& h);
+// Reorders the bath bits of h (deterministic local search) when that lowers
+// partner_tiles; records the order in h->bath_src.
+void order_bath_bits(HostModel* h);
 // rec_ds: block size of one recurrence (-1: d_s; 1: one recurrence per column)
 rdm_status plan_layout(const HostModel& h, int n_v, int precision, Layout* L, int* n_v_pad,
                        int rec_ds = -1);
@@ -144,8 +165,12 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);
 // the packed launches' descriptors); see rdm_estimate_batch.
 rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws_bytes,
                                rdm_batch_item* items, int n, const size_t* need, Profiler* prof);
-// Workspace of a batch (0 if an item's sizes are invalid); need[i] per item.
-size_t batch_workspace_bytes(const rdm_batch_item* items, int n, size_t usable, size_t* need);
+// Workspace of a batch (0 if an item's sizes are invalid); need[i] per item, planned
+// with at most avail[i] bytes.
+size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* avail, size_t* need);
+// Bytes of a request's workspace with its Krylov basis stored when the packed first
+// pass can take it (block recurrences, block of at most 64 MB), else 0.
+size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 // Bytes the estimator would use given `avail` bytes (0 if the sizes are invalid).

@@ -74,6 +74,15 @@ struct StepCoefs {
   double* cw;
 };
 
+// Bath-bit order of a Hamiltonian's internal state index: internal bath bit i carries
+// the caller's bath bit src[i] (n = 0: the caller's order). The starting block maps an
+// internal bath index back to the caller's before drawing v_l[b], so the same bath
+// vectors enter whatever order the library chose.
+struct BathPerm {
+  int n;
+  uint8_t src[32];
+};
+
 // ---- launchers (kernels.cu) ------------------------------------------------
 
 // Zero vector blocks etc. are plain cudaMemsetAsync on the host side.
@@ -91,7 +100,7 @@ cudaError_t launch_gauss_norms(int64_t d_b, int n_v, uint64_t seed, int64_t l0, 
 // e_i (x) v_l (the per-column recurrences).
 cudaError_t launch_init_block(const Layout& L, int dist, uint64_t seed, int64_t l0, int n_v_real,
                               const double* inv_norm, const void* vbuf, void* W, cudaStream_t st,
-                              int sub = 1);
+                              int sub = 1, const BathPerm* bp = nullptr);
 // vbuf[l][b] = normalised Gaussian bath vector l0 + l (T = the layout's precision),
 // from graw (the norm pass's raw values) when given, else regenerated.
 cudaError_t launch_gauss_fill(const Layout& L, int n_v, uint64_t seed, int64_t l0,
@@ -190,10 +199,12 @@ struct SpmmArgs {
   int stages;          // tiled SpMM: copy-ring depth (set by the launcher)
 };
 
-// True if the tiled SpMM applies to this layout (16-byte vectors, kTiledLanes of
-// them per row, at least one full tile per slice).
+// True if the tiled SpMM applies to this layout: rows of kTiledLanes 16-byte vectors
+// (32 bytes: 8 float32 or 4 float64 columns) holding whole bath-vector groups, at least
+// one full tile per slice. (The tiled kernel reads a row as kTiledLanes 16-byte lanes
+// whatever L.VW the plain kernels use on the same memory.)
 inline bool layout_tiled(const Layout& L) {
-  return L.VW * L.elem == 16 && L.Bs == L.VW * kTiledLanes && L.n_bits >= kTileBits;
+  return L.Bs * L.elem == 16 * kTiledLanes && L.Bs % L.DS == 0 && L.n_bits >= kTileBits;
 }
 // Blocks of the tiled SpMM (one persistent block per SM; the blocks walk the
 // (slice, tile) pairs of the whole block with one stride).

@@ -1,6 +1,7 @@
 // Request loop of the C ABI: continuous admission of estimator requests by device
 // footprint, each admitted request running on its own CUDA stream so that requests
 // arriving while others run overlap with them on the GPU.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -19,6 +20,7 @@ struct Request {
   rdm_opts opts{};
   rdm_result* out = nullptr;
   size_t footprint = 0;
+  bool packable = false;  // runs its first pass in a packed launch with other requests
   rdm_status status = RDM_OK;
   bool done = false;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -26,9 +28,11 @@ struct Request {
 };
 
 struct ServeState {
+  rdm_ctx* ctx = nullptr;  // the owning context (its autotuner serves the packed launches)
   int device = 0;
   size_t budget = 0, used = 0;
   int max_inflight = 1, inflight = 0;
+  int busy_workers = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
@@ -86,12 +90,63 @@ static rdm_status run_request(ServeState& S, Request& r, cudaStream_t st) {
   return s;
 }
 
+// A batch of packable requests: their first passes share one packed launch
+// (estimate_batch_impl); each request's result is the same as when it runs alone.
+static rdm_status run_batch(ServeState& S, std::vector<std::shared_ptr<Request>>& rs, cudaStream_t st,
+                            std::vector<rdm_status>& status) {
+  if (cudaSetDevice(S.device) != cudaSuccess) {
+    set_error("cudaSetDevice failed");
+    return RDM_ECUDA;
+  }
+  const int n = (int)rs.size();
+  std::vector<rdm_ham> hams(n);
+  std::vector<TermImage> imgs(n);
+  std::vector<rdm_batch_item> items(n);
+  std::vector<size_t> avail(n), need(n);
+  size_t terms = 0;
+  for (int i = 0; i < n; ++i) {
+    hams[i].ctx = nullptr;
+    hams[i].model = rs[i]->hm;
+    make_term_image(rs[i]->hm, &imgs[i]);
+    terms += (imgs[i].bytes.size() + 255) / 256 * 256;
+    items[i] = rdm_batch_item{&hams[i], rs[i]->betas.data(), (int)rs[i]->betas.size(), rs[i]->n_v, rs[i]->k,
+                              rs[i]->seed, rs[i]->opts, rs[i]->out, RDM_OK};
+    avail[i] = rs[i]->footprint;
+  }
+  const size_t ws = batch_workspace_bytes(items.data(), n, avail.data(), need.data());
+  if (ws == 0) return RDM_EINVAL;
+  char* mem = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&mem), terms + ws, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("batch of %d requests: device allocation of %zu bytes failed", n, terms + ws);
+    return RDM_ENOMEM;
+  }
+  size_t off = 0;
+  rdm_status s = RDM_OK;
+  for (int i = 0; i < n && s == RDM_OK; ++i) {
+    bind_terms(imgs[i], mem + off, &hams[i]);
+    if (cudaMemcpyAsync(mem + off, imgs[i].bytes.data(), imgs[i].bytes.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      set_error("batch: term upload failed");
+      s = RDM_ECUDA;
+    }
+    off += (imgs[i].bytes.size() + 255) / 256 * 256;
+  }
+  if (s == RDM_OK) s = estimate_batch_impl(S.ctx, st, mem + terms, ws, items.data(), n, need.data(), nullptr);
+  for (int i = 0; i < n; ++i) status[i] = s == RDM_OK || items[i].status != RDM_OK ? items[i].status : s;
+  cudaFreeAsync(mem, st);
+  cudaStreamSynchronize(st);  // the term images are pageable host memory
+  return s;
+}
+
+constexpr int kServeMaxBatch = 64;
+
 static void worker_loop(ServeState* S) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
-    std::shared_ptr<Request> r;
+    std::vector<std::shared_ptr<Request>> batch;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] {
@@ -101,21 +156,52 @@ static void worker_loop(ServeState* S) {
         return false;
       });
       if (S->stop) break;
-      r = take_admissible(*S);
+      std::shared_ptr<Request> r = take_admissible(*S);
       if (!r) continue;
+      // A packable request takes along every other queued packable request that fits
+      // the budget now (continuous batching: whatever arrived while others ran).
+      batch.push_back(r);
       S->used += r->footprint;
-      S->inflight++;
-      r->t_admit = now_s();
+      // share what is queued with the other idle workers: at most a 1/(idle workers)
+      // part of the queued packable requests per batch
+      int queued = 0;
+      for (auto& q : S->queue) queued += q->packable ? 1 : 0;
+      const int idle = std::max(1, S->max_inflight - S->busy_workers);
+      const int cap = std::min(kServeMaxBatch, 1 + (queued + idle - 1) / idle);
+      if (r->packable)
+        for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < cap;) {
+          if ((*it)->packable && S->used + (*it)->footprint <= S->budget) {
+            S->used += (*it)->footprint;
+            batch.push_back(*it);
+            it = S->queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      const double t = now_s();
+      for (auto& q : batch) q->t_admit = t;
+      S->inflight += (int)batch.size();
+      S->busy_workers++;
     }
-    const rdm_status s = run_request(*S, *r, st);
+    std::vector<rdm_status> status(batch.size(), RDM_OK);
+    if (batch[0]->packable) {
+      run_batch(*S, batch, st, status);
+    } else {
+      status[0] = run_request(*S, *batch[0], st);
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      r->status = s;
-      if (s != RDM_OK) r->error = rdm_last_error();
-      r->t_done = now_s();
-      r->done = true;
-      S->used -= r->footprint;
-      S->inflight--;
+      const double t = now_s();
+      for (size_t i = 0; i < batch.size(); ++i) {
+        Request& r = *batch[i];
+        r.status = status[i];
+        if (status[i] != RDM_OK) r.error = rdm_last_error();
+        r.t_done = t;
+        r.done = true;
+        S->used -= r.footprint;
+        S->inflight--;
+      }
+      S->busy_workers--;
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -150,6 +236,7 @@ extern "C" rdm_status rdm_serve_start(rdm_ctx* ctx, size_t budget, int max_infli
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   auto S = std::make_unique<ServeState>();
+  S->ctx = ctx;
   S->device = ctx->device;
   S->budget = budget;
   S->max_inflight = max_inflight;
@@ -204,6 +291,7 @@ extern "C" rdm_status rdm_submit(rdm_ctx* ctx, const rdm_model* model, const dou
   r->model.gx = copy(model->gx, r->gx, n);
   rdm_status st = compile_model(&r->model, &r->hm);
   if (st != RDM_OK) return st;
+  if (ctx->bath_order) order_bath_bits(&r->hm);  // the same bath order rdm_build_hamiltonian picks
   rdm_ham probe;
   probe.model = r->hm;
   if (n_beta < 1 || !betas) {
@@ -228,6 +316,15 @@ extern "C" rdm_status rdm_submit(rdm_ctx* ctx, const rdm_model* model, const dou
     fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc, opts->recurrence);
   }
   if (fp == 0) return RDM_EINVAL;  // make_plan set the error
+  // Small requests keep their Krylov basis and join packed launches (rdm_estimate_batch)
+  // when that takes at most a quarter of the budget.
+  if (opts->passes != RDM_PASSES_RECOMPUTE) {
+    const size_t fs = packed_store_footprint(r->hm, n_beta, n_v, k, opts);
+    if (fs > 0 && fs <= S->budget / 4) {
+      fp = fs;
+      r->packable = true;
+    }
+  }
   if (fp > S->budget) {
     set_error("rdm_submit: request needs %zu bytes, serving budget is %zu", fp, S->budget);
     return RDM_ENOMEM;

@@ -106,6 +106,9 @@ _sig("rdm_set_graphs", C.c_int, _vp, C.c_int)
 _sig("rdm_probe_copy_rate", C.c_int, _vp, C.c_size_t, C.c_int, C.POINTER(C.c_double))
 _sig("rdm_profile_stats", C.c_int, _vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int))
 _sig("rdm_estimate_batch", C.c_int, _vp, C.POINTER(BatchItem), C.c_int)
+_sig("rdm_set_bath_order", C.c_int, _vp, C.c_int)
+_sig("rdm_bath_order", C.c_int, C.POINTER(Model), C.POINTER(C.c_int), C.POINTER(C.c_double),
+     C.POINTER(C.c_double))
 _sig("rdm_packed_tuning", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64))
 
 
@@ -232,6 +235,10 @@ class Context:
         _check(_lib.rdm_probe_copy_rate(self.h, int(buffer_bytes), int(stages), C.byref(g)),
                "rdm_probe_copy_rate")
         return g.value
+
+    def set_bath_order(self, enable: bool = True):
+        """Let rdm_build_hamiltonian reorder bath bits for the tiled SpMM (default on)."""
+        _check(_lib.rdm_set_bath_order(self.h, 1 if enable else 0), "rdm_set_bath_order")
 
     def set_graphs(self, enable: bool = True):
         """Replay repeated first-pass launch sequences from CUDA graphs (default on)."""
@@ -430,6 +437,17 @@ class Hamiltonian:
 
 
 # ---------------------------------------------------------------- host post-processing
+
+def bath_order(spec) -> tuple:
+    """The bath-site order rdm_build_hamiltonian stores for `spec` (host only):
+    (order, partner tiles per tile in the caller's order, in the chosen order), where
+    order[q] is the caller's site at internal site q."""
+    m = _ModelArrays(spec)
+    order = (C.c_int * int(spec.n_sites))()
+    t0, t1 = C.c_double(), C.c_double()
+    _check(_lib.rdm_bath_order(C.byref(m.struct), order, C.byref(t0), C.byref(t1)), "rdm_bath_order")
+    return list(order), float(t0.value), float(t1.value)
+
 
 def mean_force(rho: np.ndarray, beta: float) -> np.ndarray:
     r = np.ascontiguousarray(rho, dtype=np.float64)

@@ -260,10 +260,11 @@ def test_post_processing_of_gpu_rho(ctx, lib):
 
 # ---------------------------------------------------------------- c2-shaped, FP32 vs FP64 oracle
 
-@pytest.mark.parametrize("n,n_sys,n_v", [(12, 1, 6), (13, 0, 3)])
+@pytest.mark.parametrize("n,n_sys,n_v", [(12, 1, 6), (13, 0, 3), (12, 2, 5), (11, 2, 1)])
 def test_tiled_fp64_estimate_vs_oracle(ctx, lib, n, n_sys, n_v):
-    """float64 with d_s <= 2 runs the tiled SpMM (32-byte slice rows); every term kind of
-    a random model against the oracle at the float64 tolerance."""
+    """float64 runs the tiled SpMM (32-byte slice rows); with d_s = 4 a bath vector's
+    group of four columns is the whole row, split over the row's two 16-byte lanes.
+    Every term kind of a random model against the oracle at the float64 tolerance."""
     spec = W.random_model(n, n_sys, 70 + n)
     betas = [0.2, 1.0, 3.0]
     ham = lib.Hamiltonian(ctx, spec)
@@ -311,18 +312,21 @@ def test_c2_full_size_sampled_vector(ctx, lib):
 # ---------------------------------------------------------------- serving
 
 def test_serving_alone_equals_in_mix(ctx, lib):
+    """Each request's result is the same whether it is served alone (submitted after the
+    previous one finished) or in a mix that arrives at once (small requests then share
+    packed launches), bit for bit; and it matches rdm_estimate run on its own within the
+    float32 contract."""
     reqs = W.serving_requests(12, seed=5, n_min=8, n_max=14)
     for r in reqs:  # keep the host eigen-step of the test small
         r["n_v"] = min(r["n_v"], 16)
         r["k"] = min(r["k"], 40)
         r["betas"] = r["betas"][:12]
-    alone = []
-    for r in reqs:
-        ham = lib.Hamiltonian(ctx, r["spec"])
-        alone.append(ham.estimate(r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32"))
-        ham.close()
     ctx.serve_start(8 << 30, max_inflight=4)
     try:
+        alone = []
+        for r in reqs:
+            t = ctx.submit(r["spec"], r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32")
+            alone.append(ctx.wait(t))
         tickets = [ctx.submit(r["spec"], r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32") for r in reqs]
         for t, a in zip(tickets, alone):
             res = ctx.wait(t)
@@ -332,6 +336,11 @@ def test_serving_alone_equals_in_mix(ctx, lib):
             assert lat >= q >= 0
     finally:
         ctx.serve_stop()
+    for r, a in zip(reqs, alone):
+        ham = lib.Hamiltonian(ctx, r["spec"])
+        single = ham.estimate(r["betas"], r["n_v"], r["k"], r["seed"], precision="fp32")
+        ham.close()
+        np.testing.assert_allclose(a["rho"], single["rho"], atol=TOL32, rtol=0)
 
 
 # ---------------------------------------------------------------- copy-rate probe
@@ -620,3 +629,55 @@ def test_block_recurrence_more_accurate_than_single(ctx, lib):
         b = ham.estimate([2.0], 6, k, 3, precision="fp32", dist="gauss")
         s = ham.estimate([2.0], 6, k, 3, precision="fp32", dist="gauss", recurrence="single")
         assert np.abs(b["rho"] - rho2).max() < np.abs(s["rho"] - rho2).max()
+
+
+# ---------------------------------------------------------------- bath order (ladder)
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_reordered_bath_bits_match_oracle(lib, prec, tol):
+    """The ladder of Sec. 5.2 numbered leg by leg (14 spins, system = rung 2): the
+    library stores it with its bath bits reordered (fewer partner tiles), draws the bath
+    vectors in the caller's order, and matches the oracle run on the caller's numbering;
+    with the reordering switched off the result agrees to rounding."""
+    spec = W.spin_ladder(7, 2, numbering="leg")
+    order, before, after = lib.bath_order(spec)
+    assert after < before and order != list(range(14))
+    betas = [0.5, 2.0]
+    ctx = lib.Context(0)
+    try:
+        ham = lib.Hamiltonian(ctx, spec)
+        out = ham.estimate(betas, 6, 24, 77, precision=prec, dist="gauss", full=True)
+        ctx.set_bath_order(False)
+        plain = lib.Hamiltonian(ctx, spec).estimate(betas, 6, 24, 77, precision=prec, dist="gauss", full=True)
+    finally:
+        ctx.close()
+    ref = lanczos.Estimator(spec).run(betas, 6, 24, 77, "gauss")
+    np.testing.assert_allclose(out["rho"], ref["rho"], atol=tol, rtol=0)
+    np.testing.assert_allclose(out["rho"], plain["rho"], atol=1e-13 if prec == "fp64" else 1e-5, rtol=0)
+    np.testing.assert_allclose(out["t_a"][:, :6], plain["t_a"][:, :6], atol=1e-12 if prec == "fp64" else 1e-4)
+
+
+def test_reordered_ham_keeps_caller_order_for_apply_and_starting_block(lib):
+    """rdm_apply_hamiltonian and rdm_starting_block of a reordered Hamiltonian act in the
+    caller's state order: bit-exact against the oracle's tensor-leg H on an
+    integer-valued ladder, and the starting block against the generator."""
+    import torch
+    spec = W.spin_ladder(7, 2, j_leg=2.0, j_rung=-1.0, h=2.0, numbering="leg")
+    assert lib.bath_order(spec)[0] != list(range(14))
+    ctx = lib.Context(0)
+    try:
+        ham = lib.Hamiltonian(ctx, spec)
+        rng = np.random.default_rng(3)
+        x = rng.integers(-3, 4, size=(1 << 14, 4)).astype(np.float64)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        ham.apply(xd, yd)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(yd.cpu().numpy(), spin_ops.TensorHamiltonian(spec)(x))
+        blk = torch.empty((1 << 14, 4 * 2), dtype=torch.float64, device="cuda")
+        ham.starting_block(blk, 2, 11, "rademacher")
+        torch.cuda.synchronize()
+        want = np.hstack([orng.starting_block(4, orng.bath_vector(1 << 12, l, 11, "rademacher")) for l in range(2)])
+        np.testing.assert_array_equal(blk.cpu().numpy(), want)
+    finally:
+        ctx.close()

@@ -226,3 +226,33 @@ def test_header_enums_match_binding(rdm):
         assert re.search(rf"{name}\s*=\s*{val}\b", txt), name
     assert re.search(r"RDM_FP64\s*=\s*0", txt) and re.search(r"RDM_FP32\s*=\s*1", txt)
     assert "RDM_RADEMACHER = 0, RDM_GAUSS = 1, RDM_BASIS = 2" in txt
+
+
+def test_bath_order_from_the_coupling_graph(rdm):
+    """The ladder of Sec. 5.2 (10 rungs, system = one rung) numbered leg by leg: the
+    library's bath order copies fewer partner tiles per tile than the caller's (13.5
+    there, 8.5 for the rung-by-rung numbering, which it keeps: 5 rung and 8 leg bonds
+    among the sites above the tile bits at 1/2 each -- only the antiparallel half of the
+    tiles hops such a pair -- plus the two legs that leave the tile's rungs). The order
+    is a permutation of the bath sites that leaves the system sites in place, and
+    repeated calls give the same order."""
+    import workloads as W
+    for sr in (0, 2, 4):
+        order, before, after = rdm.bath_order(W.spin_ladder(10, sr))
+        assert before == after == 8.5 and order == list(range(20))
+        spec = W.spin_ladder(10, sr, numbering="leg")
+        order, before, after = rdm.bath_order(spec)
+        assert before > 12.0 and after <= 9.0
+        assert order[:2] == [0, 1] and sorted(order) == list(range(20))
+        assert rdm.bath_order(spec) == (order, before, after)
+
+
+def test_bath_order_keeps_a_model_with_no_gain(rdm):
+    """Single-site flips (the transverse-field model) give one partner tile per high bit
+    in any order: the caller's order is kept; below 11 sites there is nothing to move."""
+    import workloads as W
+    spec = W.config_c2(0)["spec"]
+    order, before, after = rdm.bath_order(spec)
+    assert order == list(range(22)) and before == after == 12.0
+    order, before, after = rdm.bath_order(W.xxz_chain(10, 1))
+    assert order == list(range(10)) and before == after == 0.0

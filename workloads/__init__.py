@@ -29,6 +29,7 @@ __all__ = [
     "long_range_xxz",
     "long_range_tfim",
     "random_model",
+    "spin_ladder",
     "bath_spec",
     "beta_grid",
     "config_c1",
@@ -134,6 +135,35 @@ def bath_spec(spec: ModelSpec) -> ModelSpec:
     return ModelSpec(spec.n_sites - s, 0, spec.jx[s:, s:].copy(), spec.jy[s:, s:].copy(),
                      spec.jz[s:, s:].copy(), spec.hz[s:].copy(), spec.gx[s:].copy(), 1.0,
                      (spec.name + "_bath") if spec.name else "bath")
+
+
+def spin_ladder(n_rungs: int, system_rung: int, j_leg: float = 1.0, j_rung: float = -0.45,
+                h: float = 1.0, lam: float = 1.0, numbering: str = "rung") -> ModelSpec:
+    """Isotropic XY spin ladder of Sec. 5.2: two legs of n_rungs spins, coupling j_leg
+    along the legs and j_rung on the rungs (J^x = J^y, J^z = 0), field (h/2) sum Z.
+    The system is the rung `system_rung` (its two spins are sites 0 and 1); the bath
+    sites follow rung by rung, leg 0 before leg 1 on each rung (numbering="rung"), or
+    all of leg 0, then all of leg 1 (numbering="leg")."""
+    n = 2 * n_rungs
+    order = [(0, system_rung), (1, system_rung)]
+    if numbering == "rung":
+        order += [(leg, r) for r in range(n_rungs) if r != system_rung for leg in (0, 1)]
+    else:
+        order += [(leg, r) for leg in (0, 1) for r in range(n_rungs) if r != system_rung]
+    site = {ls: q for q, ls in enumerate(order)}
+    jx, jy, jz, hz, gx = _empty(n)
+
+    def bond(a, b, c):
+        i, k = sorted((site[a], site[b]))
+        jx[i, k] += c
+        jy[i, k] += c
+    for r in range(n_rungs):
+        bond((0, r), (1, r), j_rung)
+        if r + 1 < n_rungs:
+            bond((0, r), (0, r + 1), j_leg)
+            bond((1, r), (1, r + 1), j_leg)
+    hz[:] = h / 2.0
+    return ModelSpec(n, 2, jx, jy, jz, hz, gx, lam, f"ladder_L{n_rungs}_sys{system_rung}")
 
 
 def random_model(n: int, n_sys: int, seed: int, lam: float = 0.7, density: float = 0.6,
