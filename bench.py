@@ -739,15 +739,19 @@ def sweep_bench(rdm, ctx) -> dict:
 
 def spmm_source_hash() -> str:
     """sha256 (16 hex) of the tiled SpMM's source: its region of kernels.cu plus the
-    layout constants header. A committed DRAM-traffic figure is only reported while
-    this matches the hash it was measured with."""
+    layout and tile definitions it compiles against (rdm_internal.h). A committed
+    DRAM-traffic figure is only reported while this matches the hash it was measured
+    with."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2204_08147_gb300", "csrc")
     src = open(os.path.join(csrc, "kernels.cu")).read()
+    hdr = open(os.path.join(csrc, "rdm_internal.h")).read()
     a = src.index("// ---------------------------------------------------------------- tiled SpMM")
     b = src.index("// ---------------------------------------------------------------- orthogonalisation")
     h = hashlib.sha256(src[a:b].encode())
-    h.update(open(os.path.join(csrc, "rdm_internal.h"), "rb").read())
+    for s0, s1 in (("// Geometry of a Krylov block", "// Bath-bit order of a Hamiltonian"),
+                   ("constexpr int kTiledLanesLog", "// A table of the tiled diagonal (TileDiag), out[tile]")):
+        h.update(hdr[hdr.index(s0):hdr.index(s1)].encode())
     return h.hexdigest()[:16]
 
 

@@ -505,6 +505,8 @@ struct Plan {
   bool gauss;                         // Gaussian bath vectors are generated once into a buffer
   bool store;                         // keep all k+1 Krylov blocks (no second pass)
   size_t tk_bytes;                    // K table of the tiled diagonal (0 if untiled)
+  bool dev_dense;                     // the small dense step can run on the device
+  int vstride;                        // its Chebyshev degree bound + 1
 };
 
 // Float64 counts of the arrays whose size depends on the grouping: reduction partials
@@ -541,11 +543,20 @@ static size_t plan_bytes(const Plan& p) {
   a.take<char>(p.tk_bytes);
   if (p.gauss) a.take<char>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits) * L.elem);
   if (p.gauss) a.take<double>((size_t)p.n_v * ((size_t)1 << L.n_bath_bits));  // raw Gaussians
+  if (p.dev_dense) {  // device small dense step: bounds, Chebyshev vectors, results, betas
+    const size_t ne = (size_t)p.k * L.DS * L.DS;
+    a.take<double>(2 * ng);
+    a.take<double>(ng * (size_t)p.vstride * ne);
+    a.take<double>(ng * (size_t)p.n_beta * ne);
+    a.take<double>((size_t)p.n_beta);
+  }
   return a.off + 256;
 }
 
-static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, const rdm_opts* o,
-                            size_t avail, Plan* out) {
+// beta_max: the largest beta of the grid (< 0: unknown, plan for the largest degree).
+// dense: plan room for the device small dense step if it fits the recurrences.
+static rdm_status make_plan_impl(const HostModel& hm, int n_beta, int n_v, int k, const rdm_opts* o,
+                                 size_t avail, Plan* out, double beta_max, bool dense) {
   if (n_beta < 1 || n_v < 1 || n_v > 4096 || k < 1 || k > 512) {
     set_error("need n_beta >= 1, 1 <= n_v <= 4096, 1 <= k <= 512 (got %d, %d, %d)", n_beta, n_v, k);
     return RDM_EINVAL;
@@ -573,6 +584,8 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   p.nbc = 1;
   p.gauss = o->vec_dist == RDM_GAUSS;
   p.store = false;
+  p.dev_dense = dense && dense_device_fits(k, p.L.DS);
+  p.vstride = (beta_max < 0 ? kChebMaxDegree : dense_device_max_degree(beta_max, hm.hnorm)) + 1;
   if (layout_tiled(p.L)) {
     uint32_t dep;
     int off[8];
@@ -610,21 +623,38 @@ static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, con
   return RDM_OK;
 }
 
+// The plan with the device small dense step when its arrays fit beside the rest, else
+// the plan without it (the host step needs no device memory).
+static rdm_status make_plan(const HostModel& hm, int n_beta, int n_v, int k, const rdm_opts* o,
+                            size_t avail, Plan* out, double beta_max = -1.0) {
+  rdm_status st = make_plan_impl(hm, n_beta, n_v, k, o, avail, out, beta_max, true);
+  if (st == RDM_ENOMEM || (st == RDM_OK && out->dev_dense && o->passes == RDM_PASSES_AUTO && !out->store)) {
+    Plan q;
+    const rdm_status s2 = make_plan_impl(hm, n_beta, n_v, k, o, avail, &q, beta_max, false);
+    // keep the stored basis (or any plan at all) rather than the device step
+    if (s2 == RDM_OK && (st != RDM_OK || q.store)) {
+      *out = q;
+      return RDM_OK;
+    }
+  }
+  return st;
+}
+
 size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail,
-                      rdm_status* status) {
+                      rdm_status* status, double beta_max) {
   Plan p;
-  const rdm_status st = make_plan(h, n_beta, n_v, k, o, avail, &p);
+  const rdm_status st = make_plan(h, n_beta, n_v, k, o, avail, &p, beta_max);
   if (status) *status = st;
   if (st != RDM_OK) return 0;
   return plan_bytes(p);
 }
 
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int passes, int nbc, int recurrence) {
+                          int passes, int nbc, int recurrence, double beta_max) {
   rdm_opts o{precision, dist, RDM_GRAM,
              passes == RDM_PASSES_STORE ? RDM_PASSES_STORE : RDM_PASSES_RECOMPUTE, 0, recurrence};
   Plan p;
-  if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p) != RDM_OK) return 0;
+  if (make_plan(h, n_beta, n_v, k, &o, SIZE_MAX, &p, beta_max) != RDM_OK) return 0;
   if (!p.store) p.nbc = std::max(1, std::min(nbc, n_beta));
   return plan_bytes(p);
 }
@@ -741,6 +771,15 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
     }
   }
   *out = h;
+  return RDM_OK;
+}
+
+extern "C" rdm_status rdm_set_device_dense(rdm_ctx* ctx, int enable) {
+  if (!ctx) {
+    set_error("rdm_set_device_dense: NULL context");
+    return RDM_EINVAL;
+  }
+  ctx->device_dense = enable != 0;
   return RDM_OK;
 }
 
@@ -1179,7 +1218,7 @@ class EstimateRun {
   // parallel pass: fetch_t copies T back; dense_task(r) is recurrence r's small dense step
   // (thread-safe across r); finish_rest does the Gram form and the normalisation.
   rdm_status fetch_t();
-  int n_dense_tasks() const { return n_rec; }
+  int n_dense_tasks() const { return dense_on_device ? 0 : n_rec; }
   void dense_task(int r);
   rdm_status finish_rest();
   double host_ms_dense = 0.0;
@@ -1223,6 +1262,11 @@ class EstimateRun {
   char* d_tk = nullptr;
   char* d_vbuf = nullptr;
   double* d_graw = nullptr;
+  double* d_lohi = nullptr;  // device small dense step (dense.cu)
+  double* d_cheb = nullptr;
+  double* d_c = nullptr;
+  double* d_betas = nullptr;
+  bool dense_on_device = false;
   double thr_abs_sq = 0, thr_rel_sq = 0;
   SpmmArgs sa{};
   double blk_b = 0;
@@ -1258,18 +1302,24 @@ class EstimateRun {
 
 constexpr size_t kPackedMaxBlock = size_t(64) << 20;
 
-size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o) {
+size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, double beta_max) {
   if (o->recurrence != RDM_BLOCK) return 0;
   rdm_opts q = *o;
   q.passes = RDM_PASSES_STORE;
   Plan p;
-  if (make_plan(h, n_beta, n_v, k, &q, SIZE_MAX, &p) != RDM_OK) return 0;
+  if (make_plan(h, n_beta, n_v, k, &q, SIZE_MAX, &p, beta_max) != RDM_OK) return 0;
   if (!p.store || p.single || p.L.block_bytes() > kPackedMaxBlock) return 0;
   return (plan_bytes(p) + 255) / 256 * 256;
 }
 
+static double max_beta(const double* b, int n) {
+  double m = 0.0;
+  for (int i = 0; i < n; ++i) m = std::max(m, b[i]);
+  return m;
+}
+
 rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
-  rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p);
+  rdm_status st = make_plan(hm, n_beta, n_v, k, o, ws_bytes, &p, max_beta(betas, n_beta));
   if (st != RDM_OK) return st;
   L = p.L;    // the recurrences (block size ds)
   Lg = p.Lg;  // the Gram view (groups of dso columns)
@@ -1311,6 +1361,13 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
   d_tk = ar.take<char>(p.tk_bytes);
   d_vbuf = p.gauss ? ar.take<char>((size_t)n_v * (size_t)d_b * L.elem) : nullptr;
   d_graw = p.gauss ? ar.take<double>((size_t)n_v * (size_t)d_b) : nullptr;
+  if (p.dev_dense) {
+    const size_t ne = (size_t)k * ds * ds;
+    d_lohi = ar.take<double>(2 * (size_t)ng);
+    d_cheb = ar.take<double>((size_t)ng * p.vstride * ne);
+    d_c = ar.take<double>((size_t)ng * n_beta * ne);
+    d_betas = ar.take<double>((size_t)n_beta);
+  }
   cstride = (size_t)ng * nv;
 
   CK(cudaMemsetAsync(d_flags, 0, 4 * sizeof(uint32_t), s));
@@ -1482,6 +1539,36 @@ rdm_status EstimateRun::fetch_t() {
   cstore.assign((size_t)n_rec * n_beta * n * ds, 0.0);
   tmin.assign(n_rec, 0.0);
   okv.assign(n_rec, 1);
+  dense_on_device = false;
+  const bool want = p.dev_dense && (!ham->ctx || ham->ctx->device_dense);
+  if (want) {
+    // the same f(T_r) E1 on the device (Chebyshev expansion, dense.cu); results to the
+    // host arrays the rest of finish() reads
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(cudaMemcpyAsync(d_betas, betas, sizeof(double) * n_beta, cudaMemcpyHostToDevice, s));
+    const int ev = prof ? prof->begin(kKDense, s, true) : -1;
+    const cudaError_t e = launch_dense_fT(ds, k, ng, n_rec, d_ta, d_tb, hm.hnorm, d_betas, n_beta,
+                                          max_beta(betas, n_beta), p.vstride, d_lohi, d_cheb, d_c, s);
+    if (prof) prof->end(kKDense, ev, s, 0.0);
+    CK(e);
+    std::vector<double> lohi(2 * (size_t)n_rec);
+    CK(cudaMemcpyAsync(cstore.data(), d_c, cstore.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lohi.data(), d_lohi, lohi.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h2d += sizeof(double) * n_beta;
+    d2h += (cstore.size() + lohi.size()) * sizeof(double);
+    for (int r = 0; r < n_rec; ++r) {
+      tmin[r] = lohi[2 * (size_t)r];
+      okv[r] = std::isfinite(tmin[r]) ? 1 : 0;
+    }
+    for (double x : cstore)
+      if (!std::isfinite(x)) {
+        set_error("the device small dense step gave a non-finite coefficient");
+        return RDM_ENUMERIC;
+      }
+    dense_on_device = true;
+    host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
   return RDM_OK;
 }
 
@@ -1495,9 +1582,11 @@ void EstimateRun::dense_task(int r) {
 rdm_status EstimateRun::finish() {
   rdm_status st = fetch_t();
   if (st != RDM_OK) return st;
-  const auto t0 = std::chrono::steady_clock::now();
-  parallel_for(n_rec, [&](int r) { dense_task(r); });
-  host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!dense_on_device) {
+    const auto t0 = std::chrono::steady_clock::now();
+    parallel_for(n_rec, [&](int r) { dense_task(r); });
+    host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
   return finish_rest();
 }
 
@@ -1920,8 +2009,10 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
   const double dense_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < n; ++i) {
     if (items[i].status != RDM_OK) continue;
-    // the pass's wall time, shared out by the items' task counts
-    runs[i]->host_ms_dense = tasks.empty() ? 0.0 : dense_ms * runs[i]->n_dense_tasks() / (double)tasks.size();
+    // the pass's wall time, shared out by the items' task counts (items whose step ran on
+    // the device keep their own time)
+    if (runs[i]->n_dense_tasks() > 0)
+      runs[i]->host_ms_dense = dense_ms * runs[i]->n_dense_tasks() / (double)tasks.size();
     const rdm_status st = runs[i]->finish_rest();
     items[i].status = st;
     if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
@@ -1936,7 +2027,7 @@ size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* a
   for (int i = 0; i < n; ++i) {
     rdm_status st = RDM_OK;
     need[i] = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k, &items[i].opts,
-                             avail[i], &st);
+                             avail[i], &st, max_beta(items[i].betas, items[i].n_beta));
     if (need[i] == 0) return 0;
     need[i] = (need[i] + 255) / 256 * 256;
     tot += need[i];
@@ -1974,7 +2065,7 @@ extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, in
   for (int i = 0; i < n_items; ++i) {
     rdm_status st = RDM_OK;
     const size_t need = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k,
-                                       &items[i].opts, usable, &st);
+                                       &items[i].opts, usable, &st, max_beta(items[i].betas, items[i].n_beta));
     if (need == 0) {
       items[i].status = st != RDM_OK ? st : RDM_ENOMEM;
       if (first_bad == RDM_OK) first_bad = items[i].status;
@@ -2085,7 +2176,7 @@ extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta
   CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t usable = (size_t)(0.85 * (double)(free_b + ctx->own_bytes));
   rdm_status pst = RDM_OK;
-  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst);
+  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst, max_beta(betas, n_beta));
   if (need == 0) return pst != RDM_OK ? pst : RDM_ENOMEM;  // make_plan set the message
   if (ctx->own_bytes < need) {
     CK(cudaStreamSynchronize(ctx->stream));

@@ -46,6 +46,7 @@ struct PackedTuning {
 enum KernelKind {
   kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply,
   kKPacked,     // the packed first pass of a batch (one cooperative launch)
+  kKDense,      // the small dense step on the device (bounds, Chebyshev vectors, combination)
   kKHostDense,  // not a kernel: host wall time of the small dense step (eigen + coefficients)
   kKNumKinds
 };
@@ -81,6 +82,7 @@ struct rdm_ctx {
   rdm::Profiler prof;
   bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
   bool bath_order = true;  // rdm_build_hamiltonian reorders bath bits for the tiled SpMM
+  bool device_dense = true;  // run the small dense step on the device when it fits
   rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete
@@ -170,13 +172,16 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
 size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* avail, size_t* need);
 // Bytes of a request's workspace with its Krylov basis stored when the packed first
 // pass can take it (block recurrences, block of at most 64 MB), else 0.
-size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o);
+size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o,
+                              double beta_max = -1.0);
 
 // Device bytes estimate_impl needs with a pass-2 chunk of nbc betas.
 // Bytes the estimator would use given `avail` bytes (0 if the sizes are invalid).
+// beta_max: the largest beta of the grid (< 0: unknown; plans the device small dense
+// step for its largest Chebyshev degree).
 size_t estimate_bytes(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail,
-                      rdm_status* status = nullptr);
+                      rdm_status* status = nullptr, double beta_max = -1.0);
 size_t estimate_footprint(const HostModel& h, int n_beta, int n_v, int k, int precision, int dist,
-                          int passes, int nbc, int recurrence = 0);
+                          int passes, int nbc, int recurrence = 0, double beta_max = -1.0);
 
 }  // namespace rdm

@@ -290,6 +290,18 @@ cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int
 // Dynamic shared memory of the untiled SpMM's term tables.
 size_t spmm_terms_smem(int precision, int n_flip, int n_diag);
 
+// The small dense step on the device (dense.cu): c[r][beta] = exp(-beta (T_r - t_r)/2) E1
+// (n x d_s, row-major per beta) and lohi[2r] = t_r = lambda_min(T_r), lohi[2r+1] = the
+// top of the Chebyshev interval, for recurrences r < n_rec of the step arrays ta, tb
+// ([k][ng][d_s^2]); betas on the device. V: scratch of n_rec * vstride * k d_s * d_s
+// float64 (vstride = Chebyshev degree bound + 1, dense_device_max_degree + 1).
+constexpr int kChebMaxDegree = 400;
+bool dense_device_fits(int k, int ds);
+int dense_device_max_degree(double beta_max, double hnorm);
+cudaError_t launch_dense_fT(int ds, int k, int ng, int n_rec, const double* ta, const double* tb, double hnorm,
+                            const double* betas, int n_beta, double beta_max, int vstride, double* lohi,
+                            double* V, double* cout, cudaStream_t st);
+
 constexpr uint32_t kFlagNonFinite = 0x100u;
 
 }  // namespace rdm

@@ -310,16 +310,19 @@ extern "C" rdm_status rdm_submit(rdm_ctx* ctx, const rdm_model* model, const dou
   // Footprint: all betas in one pass-2 sweep if that takes at most a quarter of
   // the budget, else halve the sweep until it does (results do not depend on it).
   int nbc = n_beta;
-  size_t fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc, opts->recurrence);
+  const double bmax = *std::max_element(betas, betas + n_beta);
+  size_t fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc,
+                                 opts->recurrence, bmax);
   while (nbc > 1 && fp > S->budget / 4) {
     nbc = (nbc + 1) / 2;
-    fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc, opts->recurrence);
+    fp = estimate_footprint(r->hm, n_beta, n_v, k, opts->precision, opts->vec_dist, opts->passes, nbc,
+                            opts->recurrence, bmax);
   }
   if (fp == 0) return RDM_EINVAL;  // make_plan set the error
   // Small requests keep their Krylov basis and join packed launches (rdm_estimate_batch)
   // when that takes at most a quarter of the budget.
   if (opts->passes != RDM_PASSES_RECOMPUTE) {
-    const size_t fs = packed_store_footprint(r->hm, n_beta, n_v, k, opts);
+    const size_t fs = packed_store_footprint(r->hm, n_beta, n_v, k, opts, bmax);
     if (fs > 0 && fs <= S->budget / 4) {
       fp = fs;
       r->packable = true;

@@ -107,6 +107,7 @@ _sig("rdm_probe_copy_rate", C.c_int, _vp, C.c_size_t, C.c_int, C.POINTER(C.c_dou
 _sig("rdm_profile_stats", C.c_int, _vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int))
 _sig("rdm_estimate_batch", C.c_int, _vp, C.POINTER(BatchItem), C.c_int)
 _sig("rdm_set_bath_order", C.c_int, _vp, C.c_int)
+_sig("rdm_set_device_dense", C.c_int, _vp, C.c_int)
 _sig("rdm_bath_order", C.c_int, C.POINTER(Model), C.POINTER(C.c_int), C.POINTER(C.c_double),
      C.POINTER(C.c_double))
 _sig("rdm_packed_tuning", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64))
@@ -235,6 +236,10 @@ class Context:
         _check(_lib.rdm_probe_copy_rate(self.h, int(buffer_bytes), int(stages), C.byref(g)),
                "rdm_probe_copy_rate")
         return g.value
+
+    def set_device_dense(self, enable: bool = True):
+        """Run the small dense step (f(T) E1 per bath vector and beta) on the device."""
+        _check(_lib.rdm_set_device_dense(self.h, 1 if enable else 0), "rdm_set_device_dense")
 
     def set_bath_order(self, enable: bool = True):
         """Let rdm_build_hamiltonian reorder bath bits for the tiled SpMM (default on)."""
