@@ -29,12 +29,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "rdm_internal.h"
 
 namespace rdm {
 namespace {
 
 constexpr int kChebThreads = 256;
+constexpr int kDenseSmemMax = 200 * 1024;  // dynamic shared memory of the largest launch
 
 __device__ __forceinline__ double blk(const double* m, int ds, int a, int b) { return m[a * ds + b]; }
 
@@ -308,15 +311,22 @@ cudaError_t launch_dense(int k, int ng, int n_rec, const double* ta, const doubl
   k_dense_bounds<DS><<<n_rec, 32, 0, st>>>(k, ng, ta, tb, hnorm, lohi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // Both kernels' dynamic shared-memory limits are raised once, to the largest size any
+  // launch uses (kDenseSmemMax), so concurrent host threads cannot lower one under
+  // another's launch.
+  static std::once_flag once;
+  static cudaError_t set_err = cudaSuccess;
+  std::call_once(once, [] {
+    set_err = cudaFuncSetAttribute(k_cheb_vectors<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmemMax);
+    if (set_err == cudaSuccess)
+      set_err = cudaFuncSetAttribute(k_cheb_combine<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmemMax);
+  });
+  if (set_err != cudaSuccess) return set_err;
   const size_t smv = ((size_t)2 * k * DS * DS + (size_t)3 * ne) * sizeof(double);
-  e = cudaFuncSetAttribute(k_cheb_vectors<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
-  if (e != cudaSuccess) return e;
   k_cheb_vectors<DS><<<n_rec, kChebThreads, smv, st>>>(k, ng, ta, tb, lohi, beta_max, vstride, V);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smc = (size_t)kCombineBetas * vstride * sizeof(double);
-  e = cudaFuncSetAttribute(k_cheb_combine<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)n_rec, (unsigned)((n_beta + kCombineBetas - 1) / kCombineBetas));
   k_cheb_combine<DS><<<grid, kChebThreads, smc, st>>>(k, lohi, betas, n_beta, beta_max, vstride, V, cout);
   return cudaGetLastError();
@@ -326,8 +336,8 @@ cudaError_t launch_dense(int k, int ng, int n_rec, const double* ta, const doubl
 
 bool dense_device_fits(int k, int ds) {
   const size_t smv = ((size_t)2 * k * ds * ds + (size_t)3 * k * ds * ds) * sizeof(double);
-  return ds >= 1 && ds <= 4 && smv <= (size_t)200 * 1024 &&
-         (size_t)kCombineBetas * (kChebMaxDegree + 1) * sizeof(double) <= (size_t)200 * 1024;
+  return ds >= 1 && ds <= 4 && smv <= (size_t)kDenseSmemMax &&
+         (size_t)kCombineBetas * (kChebMaxDegree + 1) * sizeof(double) <= (size_t)kDenseSmemMax;
 }
 
 int dense_device_max_degree(double beta_max, double hnorm) {

@@ -519,8 +519,9 @@ struct alignas(16) PatS {
   uint32_t flags;  // bit0 uniform activity, bit1/bit2 some c_odd/c_even nonzero
   int start, end;  // its terms
   uint32_t low0;   // m_low of its first term
-  uint32_t single;
+  uint32_t single; // bit0: one term, c_odd = c_even; bit1: one term with m_low = 0
   T c0;            // c_odd of its first term
+  T c1;            // c_even of its first term
 };
 template <typename T>
 struct alignas(16) TermS {
@@ -609,6 +610,31 @@ __device__ __forceinline__ int partner_base(int rgoff, uint32_t ml) {
   return (rgoff ^ (int)((ml & (uint32_t)(RG - 1)) * BS)) | (int)((ml / RG) * (uint32_t)(RG * BS));
 }
 
+// Rows m and m ^ K (K a register-row bit of mh) of this thread for a parity-only term:
+// the pair's active row a (parity p0 ^ parity(a & mh) selects the nonzero coefficient)
+// loads its partner row once; y[a] += c * partner, y[other] += 0 * partner.
+template <int K, typename T, int VW, int RPT>
+__device__ __forceinline__ void pair_rows(T (&y)[RPT][VW], const T* P, int x, int kStep, uint32_t mh, uint32_t p0,
+                                          T co, T ce) {
+  if constexpr (K >= RPT) return;
+  const T c = co != (T)0 ? co : ce;
+  const uint32_t want = co != (T)0 ? 1u : 0u;  // the parity with the nonzero coefficient
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    if (m & K) continue;
+    const bool lo = ((p0 ^ (uint32_t)__popc((uint32_t)m & mh)) & 1u) == want;
+    const int a = lo ? m : (m ^ K);
+    T xp[VW];
+    VecIO<T, VW>::ld_rw(xp, P + (x ^ (a * kStep)));
+    const T cl = lo ? c : (T)0, ch = lo ? (T)0 : c;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      y[m][v] = fma(cl, xp[v], y[m][v]);
+      y[m ^ K][v] = fma(ch, xp[v], y[m ^ K][v]);
+    }
+  }
+}
+
 // y[m] += c * P[row m ^ ml] for one term whose coefficient depends on the parity of
 // (row0 + row) & mparity (c_odd / c_even), rows of this thread.
 // UNI: every term of the Hamiltonian has c_odd = c_even (a separate instantiation,
@@ -653,6 +679,16 @@ __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], int rgoff, int rg, c
 #pragma unroll
           for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
         }
+      }
+    } else if (co == (T)0 || ce == (T)0) {
+      // Parity-only coefficient (one of c_odd, c_even zero, e.g. XX + YY with J^x = J^y):
+      // rows m and m ^ hb (hb the lowest bit of mh) have opposite parities, so exactly one
+      // of each such pair is active. One load serves the pair: the active row's partner,
+      // added to the active row (the other row's product is with zero).
+      switch (mh & (0u - mh)) {
+        case 1u: pair_rows<1, T, VW, RPT>(y, P, x, kStep, mh, p0, co, ce); break;
+        case 2u: pair_rows<2, T, VW, RPT>(y, P, x, kStep, mh, p0, co, ce); break;
+        default: pair_rows<4, T, VW, RPT>(y, P, x, kStep, mh, p0, co, ce); break;
       }
     } else {
 #pragma unroll
@@ -766,7 +802,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     const bool any = r.start < r.end;
     r.low0 = any ? tt.term_low[r.start] : 0u;
     r.c0 = any ? (T)tt.term_odd[r.start] : (T)0;
-    r.single = (r.end - r.start == 1 && tt.term_odd[r.start] == tt.term_even[r.start]) ? 1u : 0u;
+    r.c1 = any ? (T)tt.term_even[r.start] : (T)0;
+    const bool one = r.end - r.start == 1;
+    r.single = ((one && tt.term_odd[r.start] == tt.term_even[r.start]) ? 1u : 0u) |
+               ((one && tt.term_low[r.start] == 0u) ? 2u : 0u);
     pat[i] = r;
   }
   for (int i = threadIdx.x; i < nterm; i += blockDim.x) {
@@ -1073,6 +1112,42 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     for (int p = all_active ? 1 : tiled_next(1, npat, ut, pat); p < npat;) {
       const int pn = all_active ? p + 1 : tiled_next(p + 1, npat, ut, pat);
       const PatS<T> A = pat[p];
+      if (A.single & 2u) {
+        // One term whose partner row is the same row (m_low = 0): its coefficient is
+        // the same for every row of this tile (the parity of its mask is that of the
+        // tile bits). Two such partner tiles are consumed together when they follow
+        // each other.
+        const T cA = (__popc(ut & A.high) & 1) ? A.c0 : A.c1;
+        if (pn < npat && (pat[pn].single & 2u)) {
+          const PatS<T> Bq = pat[pn];
+          const T cB = (__popc(ut & Bq.high) & 1) ? Bq.c0 : Bq.c1;
+          const unsigned char* sp2;
+          if (!acquire(sp, 0) || !acquire(sp2, 1)) {
+            aborted = true;
+            break;
+          }
+          apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, reinterpret_cast<const T*>(sp), 0u, cA,
+                                             reinterpret_cast<const T*>(sp2), 0u, cB);
+          release2();
+          p = all_active ? pn + 1 : tiled_next(pn + 1, npat, ut, pat);
+          continue;
+        }
+        if (!acquire(sp, 0)) {
+          aborted = true;
+          break;
+        }
+        const T* PA = reinterpret_cast<const T*>(sp) + rgoff;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          T u[VW];
+          VecIO<T, VW>::ld_rw(u, PA + m * kStep);
+#pragma unroll
+          for (int v = 0; v < VW; ++v) y[m][v] = fma(cA, u[v], y[m][v]);
+        }
+        release();
+        p = pn;
+        continue;
+      }
       if (pn < npat && A.single) {
         const PatS<T> Bq = pat[pn];
         if (Bq.single) {

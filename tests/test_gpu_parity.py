@@ -681,3 +681,55 @@ def test_reordered_ham_keeps_caller_order_for_apply_and_starting_block(lib):
         np.testing.assert_array_equal(blk.cpu().numpy(), want)
     finally:
         ctx.close()
+
+
+# ---------------------------------------------------------------- small dense step on the device
+
+@pytest.mark.parametrize("spec_fn,n_v,k,betas,dist", [
+    (lambda: W.long_range_tfim(12, 2, 1.5, 1.1), 6, 40, list(W.beta_grid(20, 0.05, 10.0)) + [0.0], "gauss"),
+    (lambda: W.long_range_xxz(11, 1, 1.0, 1.0, 0.1), 5, 60, [0.3, 3.0, 12.0], "rademacher"),
+    (lambda: W.random_model(9, 2, 31), 3, 25, [1.0, 4.0], "gauss"),
+    (lambda: W.xxz_chain(10, 1, 1.0, 0.5), 16, 40, [0.5, 1.0, 2.0], "rademacher"),
+])
+def test_device_dense_step_matches_host_and_oracle(lib, spec_fn, n_v, k, betas, dist):
+    """The device small dense step (multisection for lambda_min, Chebyshev expansion of
+    exp(-beta (T - E0)/2) E1) against the host eigendecomposition on the same T (float64
+    path: per-vector Gram and quadrature forms within 1e-12 of their trace, E0 within
+    1e-12 |E0|), and the estimate against the oracle at the float64 tolerance. Covers
+    more than one chunk of 16 betas, beta = 0 and beta up to 12."""
+    spec = spec_fn()
+    ctx = lib.Context(0)
+    try:
+        ham = lib.Hamiltonian(ctx, spec)
+        dev = ham.estimate(betas, n_v, k, 9, precision="fp64", dist=dist, full=True)
+        ctx.set_device_dense(False)
+        host = ham.estimate(betas, n_v, k, 9, precision="fp64", dist=dist, full=True)
+    finally:
+        ctx.close()
+    assert abs(dev["e0"] - host["e0"]) <= 1e-12 * max(1.0, abs(host["e0"]))
+    for key in ("gram_l", "quad_l"):
+        tr = np.trace(host[key], axis1=2, axis2=3)[..., None, None]
+        assert np.abs(dev[key] - host[key]).max() <= 1e-12 * tr.max()
+        assert np.all(np.abs(dev[key] - host[key]) <= 1e-12 * tr)
+    ref = lanczos.Estimator(spec).run(betas, n_v, k, 9, dist)
+    np.testing.assert_allclose(dev["rho"], ref["rho"], atol=TOL64, rtol=0)
+
+
+def test_device_dense_step_is_used_and_large_t_falls_back(lib):
+    """The profiler sees the device step (dense_fT) and no host eigen-solves beyond the
+    coefficient assembly; a T too large for its shared memory (k d_s^2 > 5120) takes the
+    host path and still matches the oracle."""
+    spec = W.random_model(8, 2, 5)
+    ctx = lib.Context(0)
+    try:
+        ham = lib.Hamiltonian(ctx, spec)
+        ctx.profile(True)
+        ham.estimate([1.0, 2.0], 2, 20, 3, precision="fp64", dist="gauss")
+        st = ctx.profile_stats()
+        ctx.profile(False)
+        assert st["dense_fT"]["launches"] == 1
+        big = ham.estimate([1.0], 1, 330, 3, precision="fp64", dist="gauss")  # k d_s^2 = 5280
+        ref = lanczos.Estimator(spec).run([1.0], 1, 330, 3, "gauss")
+        np.testing.assert_allclose(big["rho"], ref["rho"], atol=1e-8, rtol=0)
+    finally:
+        ctx.close()
