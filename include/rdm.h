@@ -195,14 +195,17 @@ rdm_status rdm_set_graphs(rdm_ctx* ctx, int enable);
 
 /* Where rdm_estimate's small dense step runs (Sec. 3.1-3.2, eq. fT:
  * exp(-beta (T_l - t_l)/2) E1 for every bath vector l and beta, t_l = lambda_min(T_l)).
- * With enable != 0 (the default) it runs on the device whenever T_l fits (k d_s^2 up to
- * 5120 for d_s = 4): t_l by multisection on the inertia of the block LDL^T factors of
- * T_l - sigma I, then a Chebyshev expansion of the exponential on [t_l, top of the
- * spectrum], its coefficients scaled Bessel values e^-w I_i(w) from Miller's backward
- * recurrence; float64 throughout, to within ~1e-14 of the host eigendecomposition. 0
- * keeps the host path (tridiagonal reduction, implicit QR, rotations applied back for
- * every beta on the host worker pool). The paper has no counterpart. */
-rdm_status rdm_set_device_dense(rdm_ctx* ctx, int enable);
+ * On the device: t_l by multisection on the inertia of the block LDL^T factors of
+ * T_l - sigma I (float32 rounds, then float64), then a Chebyshev expansion of the
+ * exponential on [t_l, top of the spectrum] whose coefficients are scaled Bessel values
+ * e^-w I_i(w) from Miller's backward recurrence; float64, within ~1e-13 of the host path
+ * on the Gram. On the host: tridiagonal reduction, implicit QR, rotations applied back
+ * for every beta, on the host worker pool. mode 0: always the host; 1 (the default):
+ * the device for beta grids of at least 8 points (where the host's per-beta
+ * back-transformation dominates) when T_l fits (k d_s^2 <= 5120); 2: the device
+ * whenever T_l fits. rdm_estimate_batch launches the device steps of all its items at
+ * once. RDM_EINVAL for another mode. The paper has no counterpart. */
+rdm_status rdm_set_device_dense(rdm_ctx* ctx, int mode);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* rdm_last_error(void);

@@ -549,6 +549,7 @@ static size_t plan_bytes(const Plan& p) {
     a.take<double>(ng * (size_t)p.vstride * ne);
     a.take<double>(ng * (size_t)p.n_beta * ne);
     a.take<double>((size_t)p.n_beta);
+    a.take<char>(dense_jobs_bytes(1));
   }
   return a.off + 256;
 }
@@ -779,7 +780,11 @@ extern "C" rdm_status rdm_set_device_dense(rdm_ctx* ctx, int enable) {
     set_error("rdm_set_device_dense: NULL context");
     return RDM_EINVAL;
   }
-  ctx->device_dense = enable != 0;
+  if (enable < 0 || enable > 2) {
+    set_error("rdm_set_device_dense: mode must be 0, 1 or 2");
+    return RDM_EINVAL;
+  }
+  ctx->device_dense = enable;
   return RDM_OK;
 }
 
@@ -1218,8 +1223,15 @@ class EstimateRun {
   // parallel pass: fetch_t copies T back; dense_task(r) is recurrence r's small dense step
   // (thread-safe across r); finish_rest does the Gram form and the normalisation.
   rdm_status fetch_t();
-  int n_dense_tasks() const { return dense_on_device ? 0 : n_rec; }
+  int n_dense_tasks() const { return dense_on_device || wants_device ? 0 : n_rec; }
   void dense_task(int r);
+  // The device path of the dense step (fetch_t decides wants_device): the job's
+  // descriptor for launch_dense_jobs, its betas on the device, and the results back.
+  bool wants_device = false;
+  DenseJob dense_job();
+  rdm_status upload_betas();
+  rdm_status fetch_dense();
+  int rec_ds() const { return ds; }
   rdm_status finish_rest();
   double host_ms_dense = 0.0;
   // Whether the packed launch can take this estimate's first pass (stored basis, one
@@ -1266,6 +1278,7 @@ class EstimateRun {
   double* d_cheb = nullptr;
   double* d_c = nullptr;
   double* d_betas = nullptr;
+  char* d_jobs = nullptr;
   bool dense_on_device = false;
   double thr_abs_sq = 0, thr_rel_sq = 0;
   SpmmArgs sa{};
@@ -1301,6 +1314,10 @@ class EstimateRun {
 };
 
 constexpr size_t kPackedMaxBlock = size_t(64) << 20;
+// Below this many betas the host's eigendecomposition path is faster than the device
+// small dense step for a single estimate (its per-beta rotations are what the device
+// step saves; its float64 multisection is latency-bound on few recurrences).
+constexpr int kDeviceDenseMinBetas = 8;
 
 size_t packed_store_footprint(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, double beta_max) {
   if (o->recurrence != RDM_BLOCK) return 0;
@@ -1367,6 +1384,7 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
     d_cheb = ar.take<double>((size_t)ng * p.vstride * ne);
     d_c = ar.take<double>((size_t)ng * n_beta * ne);
     d_betas = ar.take<double>((size_t)n_beta);
+    d_jobs = ar.take<char>(dense_jobs_bytes(1));
   }
   cstride = (size_t)ng * nv;
 
@@ -1540,35 +1558,51 @@ rdm_status EstimateRun::fetch_t() {
   tmin.assign(n_rec, 0.0);
   okv.assign(n_rec, 1);
   dense_on_device = false;
-  const bool want = p.dev_dense && (!ham->ctx || ham->ctx->device_dense);
-  if (want) {
-    // the same f(T_r) E1 on the device (Chebyshev expansion, dense.cu); results to the
-    // host arrays the rest of finish() reads
-    const auto t0 = std::chrono::steady_clock::now();
-    CK(cudaMemcpyAsync(d_betas, betas, sizeof(double) * n_beta, cudaMemcpyHostToDevice, s));
-    const int ev = prof ? prof->begin(kKDense, s, true) : -1;
-    const cudaError_t e = launch_dense_fT(ds, k, ng, n_rec, d_ta, d_tb, hm.hnorm, d_betas, n_beta,
-                                          max_beta(betas, n_beta), p.vstride, d_lohi, d_cheb, d_c, s);
-    if (prof) prof->end(kKDense, ev, s, 0.0);
-    CK(e);
-    std::vector<double> lohi(2 * (size_t)n_rec);
-    CK(cudaMemcpyAsync(cstore.data(), d_c, cstore.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(lohi.data(), d_lohi, lohi.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    h2d += sizeof(double) * n_beta;
-    d2h += (cstore.size() + lohi.size()) * sizeof(double);
-    for (int r = 0; r < n_rec; ++r) {
-      tmin[r] = lohi[2 * (size_t)r];
-      okv[r] = std::isfinite(tmin[r]) ? 1 : 0;
-    }
-    for (double x : cstore)
-      if (!std::isfinite(x)) {
-        set_error("the device small dense step gave a non-finite coefficient");
-        return RDM_ENUMERIC;
-      }
-    dense_on_device = true;
-    host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const int mode = ham->ctx ? ham->ctx->device_dense : 1;
+  wants_device = p.dev_dense && (mode == 2 || (mode == 1 && n_beta >= kDeviceDenseMinBetas));
+  return RDM_OK;
+}
+
+DenseJob EstimateRun::dense_job() {
+  DenseJob j{};
+  j.k = k;
+  j.ng = ng;
+  j.n_rec = n_rec;
+  j.n_beta = n_beta;
+  j.vstride = p.vstride;
+  j.hnorm = hm.hnorm;
+  j.beta_max = max_beta(betas, n_beta);
+  j.ta = d_ta;
+  j.tb = d_tb;
+  j.betas = d_betas;
+  j.lohi = d_lohi;
+  j.V = d_cheb;
+  j.cout = d_c;
+  return j;
+}
+
+rdm_status EstimateRun::upload_betas() {
+  CK(cudaMemcpyAsync(d_betas, betas, sizeof(double) * n_beta, cudaMemcpyHostToDevice, s));
+  h2d += sizeof(double) * n_beta;
+  return RDM_OK;
+}
+
+rdm_status EstimateRun::fetch_dense() {
+  std::vector<double> lohi(2 * (size_t)n_rec);
+  CK(cudaMemcpyAsync(cstore.data(), d_c, cstore.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(lohi.data(), d_lohi, lohi.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  d2h += (cstore.size() + lohi.size()) * sizeof(double);
+  for (int r = 0; r < n_rec; ++r) {
+    tmin[r] = lohi[2 * (size_t)r];
+    okv[r] = std::isfinite(tmin[r]) ? 1 : 0;
   }
+  for (double x : cstore)
+    if (!std::isfinite(x)) {
+      set_error("the device small dense step gave a non-finite coefficient");
+      return RDM_ENUMERIC;
+    }
+  dense_on_device = true;
   return RDM_OK;
 }
 
@@ -1582,7 +1616,19 @@ void EstimateRun::dense_task(int r) {
 rdm_status EstimateRun::finish() {
   rdm_status st = fetch_t();
   if (st != RDM_OK) return st;
-  if (!dense_on_device) {
+  if (wants_device) {
+    const auto t0 = std::chrono::steady_clock::now();
+    st = upload_betas();
+    if (st != RDM_OK) return st;
+    const DenseJob j = dense_job();
+    const int ev = prof ? prof->begin(kKDense, s, true) : -1;
+    const cudaError_t e = launch_dense_jobs(ds, &j, 1, d_jobs, s);
+    if (prof) prof->end(kKDense, ev, s, 0.0);
+    CK(e);
+    st = fetch_dense();
+    if (st != RDM_OK) return st;
+    host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  } else {
     const auto t0 = std::chrono::steady_clock::now();
     parallel_for(n_rec, [&](int r) { dense_task(r); });
     host_ms_dense = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1959,7 +2005,7 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
   for (int i = 0; i < n; ++i) k_max = std::max(k_max, items[i].k);
   const size_t meta_b = packed_meta_bytes(n, k_max);
   char* meta = ws;
-  off = 6 * meta_b;
+  off = 6 * meta_b + dense_jobs_bytes(n);
   rdm_status first_bad = RDM_OK;
   for (int i = 0; i < n; ++i) {
     rdm_batch_item& it = items[i];
@@ -1999,6 +2045,38 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
     items[i].status = st;
     if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
   }
+  // the device small dense steps of all items that take it: one launch per d_s over all
+  // their recurrences
+  char* dense_meta = ws + 6 * meta_b;
+  for (int ds : {1, 2, 4}) {
+    std::vector<DenseJob> jobs;
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i)
+      if (items[i].status == RDM_OK && runs[i]->wants_device && runs[i]->rec_ds() == ds) {
+        const rdm_status st = runs[i]->upload_betas();
+        if (st != RDM_OK) {
+          items[i].status = st;
+          continue;
+        }
+        jobs.push_back(runs[i]->dense_job());
+        idx.push_back(i);
+      }
+    if (jobs.empty()) continue;
+    const int ev = prof ? prof->begin(kKDense, s, true) : -1;
+    const cudaError_t e = launch_dense_jobs(ds, jobs.data(), (int)jobs.size(), dense_meta, s);
+    if (prof) prof->end(kKDense, ev, s, 0.0);
+    for (int i : idx) {
+      rdm_status st = RDM_OK;
+      if (e != cudaSuccess) {
+        set_error("device small dense step: %s", cudaGetErrorString(e));
+        st = RDM_ECUDA;
+      } else {
+        st = runs[i]->fetch_dense();
+      }
+      items[i].status = st;
+      if (st != RDM_OK && first_bad == RDM_OK) first_bad = st;
+    }
+  }
   // the small dense steps of all items in one pass over the host worker pool
   std::vector<std::pair<int, int>> tasks;
   for (int i = 0; i < n; ++i)
@@ -2023,7 +2101,7 @@ rdm_status estimate_batch_impl(rdm_ctx* ctx, cudaStream_t s, char* ws, size_t ws
 size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* avail, size_t* need) {
   int k_max = 1;
   for (int i = 0; i < n; ++i) k_max = std::max(k_max, items[i].k);
-  size_t tot = 6 * packed_meta_bytes(n, k_max);
+  size_t tot = 6 * packed_meta_bytes(n, k_max) + dense_jobs_bytes(n);
   for (int i = 0; i < n; ++i) {
     rdm_status st = RDM_OK;
     need[i] = estimate_bytes(items[i].ham->model, items[i].n_beta, items[i].n_v, items[i].k, &items[i].opts,

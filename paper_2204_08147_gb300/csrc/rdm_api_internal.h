@@ -82,7 +82,7 @@ struct rdm_ctx {
   rdm::Profiler prof;
   bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
   bool bath_order = true;  // rdm_build_hamiltonian reorders bath bits for the tiled SpMM
-  bool device_dense = true;  // run the small dense step on the device when it fits
+  int device_dense = 1;  // small dense step: 0 host, 1 device for grids of >= 8 betas, 2 device
   rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete

@@ -290,17 +290,29 @@ cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int
 // Dynamic shared memory of the untiled SpMM's term tables.
 size_t spmm_terms_smem(int precision, int n_flip, int n_diag);
 
-// The small dense step on the device (dense.cu): c[r][beta] = exp(-beta (T_r - t_r)/2) E1
-// (n x d_s, row-major per beta) and lohi[2r] = t_r = lambda_min(T_r), lohi[2r+1] = the
-// top of the Chebyshev interval, for recurrences r < n_rec of the step arrays ta, tb
-// ([k][ng][d_s^2]); betas on the device. V: scratch of n_rec * vstride * k d_s * d_s
-// float64 (vstride = Chebyshev degree bound + 1, dense_device_max_degree + 1).
+// The small dense step on the device (dense.cu), for the n_rec recurrences of one
+// estimate (a job): c[r][beta] = exp(-beta (T_r - t_r)/2) E1 (n x d_s, row-major per
+// beta) and lohi[2r] = t_r = lambda_min(T_r), lohi[2r+1] = the top of the Chebyshev
+// interval, from the step arrays ta, tb ([k][ng][d_s^2]); betas on the device; V
+// scratch of n_rec * vstride * k d_s * d_s float64 (vstride = the Chebyshev degree
+// bound + 1, dense_device_max_degree + 1).
+struct DenseJob {
+  int k, ng, n_rec, n_beta, vstride;
+  double hnorm, beta_max;
+  const double* ta;
+  const double* tb;
+  const double* betas;
+  double* lohi;
+  double* V;
+  double* cout;
+};
 constexpr int kChebMaxDegree = 400;
 bool dense_device_fits(int k, int ds);
 int dense_device_max_degree(double beta_max, double hnorm);
-cudaError_t launch_dense_fT(int ds, int k, int ng, int n_rec, const double* ta, const double* tb, double hnorm,
-                            const double* betas, int n_beta, double beta_max, int vstride, double* lohi,
-                            double* V, double* cout, cudaStream_t st);
+// Device bytes of the descriptors of n_jobs jobs (scratch of launch_dense_jobs).
+size_t dense_jobs_bytes(int n_jobs);
+// One launch of each dense kernel over all recurrences of all jobs (same d_s).
+cudaError_t launch_dense_jobs(int ds, const DenseJob* host_jobs, int n_jobs, void* scratch, cudaStream_t st);
 
 constexpr uint32_t kFlagNonFinite = 0x100u;
 

@@ -237,9 +237,10 @@ class Context:
                "rdm_probe_copy_rate")
         return g.value
 
-    def set_device_dense(self, enable: bool = True):
-        """Run the small dense step (f(T) E1 per bath vector and beta) on the device."""
-        _check(_lib.rdm_set_device_dense(self.h, 1 if enable else 0), "rdm_set_device_dense")
+    def set_device_dense(self, mode=1):
+        """Where the small dense step (f(T) E1 per bath vector and beta) runs: 0/False the
+        host, 1/True the device for grids of >= 8 betas (default), 2 always the device."""
+        _check(_lib.rdm_set_device_dense(self.h, int(mode)), "rdm_set_device_dense")
 
     def set_bath_order(self, enable: bool = True):
         """Let rdm_build_hamiltonian reorder bath bits for the tiled SpMM (default on)."""

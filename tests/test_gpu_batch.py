@@ -119,3 +119,28 @@ def test_batch_rejects_a_foreign_hamiltonian(lib):
     finally:
         a.close()
         b.close()
+
+
+def test_batch_device_dense_steps_in_one_launch(lib):
+    """Items with 10-point beta grids take the device small dense step; a batch runs all
+    their recurrences (both d_s groups) in one launch per d_s. Against each estimate on
+    its own with the host path: float64 items within 1e-12 in rho*, float32 within the
+    float32 contract."""
+    ctx = lib.Context(0)
+    try:
+        jobs = _jobs(lib, ctx)
+        for jb in jobs:
+            jb["betas"] = list(W.beta_grid(10, 0.2, 6.0))
+        ctx.profile(True)
+        outs = ctx.estimate_batch(jobs)
+        st = ctx.profile_stats()
+        ctx.profile(False)
+        assert st["dense_fT"]["launches"] == 2  # d_s = 2 and d_s = 4 groups
+        ctx.set_device_dense(0)
+        for jb, out in zip(jobs, outs):
+            single = jb["ham"].estimate(jb["betas"], jb["n_v"], jb["k"], jb["seed"], precision=jb["precision"],
+                                        dist=jb["dist"])
+            tol = 1e-12 if jb["precision"] == "fp64" else 1e-4
+            np.testing.assert_allclose(out["rho"], single["rho"], atol=tol, rtol=0)
+    finally:
+        ctx.close()

@@ -701,8 +701,9 @@ def test_device_dense_step_matches_host_and_oracle(lib, spec_fn, n_v, k, betas, 
     ctx = lib.Context(0)
     try:
         ham = lib.Hamiltonian(ctx, spec)
+        ctx.set_device_dense(2)
         dev = ham.estimate(betas, n_v, k, 9, precision="fp64", dist=dist, full=True)
-        ctx.set_device_dense(False)
+        ctx.set_device_dense(0)
         host = ham.estimate(betas, n_v, k, 9, precision="fp64", dist=dist, full=True)
     finally:
         ctx.close()
@@ -716,20 +717,48 @@ def test_device_dense_step_matches_host_and_oracle(lib, spec_fn, n_v, k, betas, 
 
 
 def test_device_dense_step_is_used_and_large_t_falls_back(lib):
-    """The profiler sees the device step (dense_fT) and no host eigen-solves beyond the
-    coefficient assembly; a T too large for its shared memory (k d_s^2 > 5120) takes the
-    host path and still matches the oracle."""
+    """By default the device step (dense_fT in the profile) runs for grids of 8 or more
+    betas and the host path for fewer; a T too large for the device step's shared memory
+    (k d_s^2 > 5120) takes the host path and still matches the oracle."""
     spec = W.random_model(8, 2, 5)
     ctx = lib.Context(0)
     try:
         ham = lib.Hamiltonian(ctx, spec)
         ctx.profile(True)
-        ham.estimate([1.0, 2.0], 2, 20, 3, precision="fp64", dist="gauss")
+        ham.estimate([1.0, 2.0], 2, 20, 3, precision="fp64", dist="gauss")  # 2 betas: host
+        ham.estimate(W.beta_grid(8, 0.5, 4.0), 2, 20, 3, precision="fp64", dist="gauss")  # 8: device
         st = ctx.profile_stats()
         ctx.profile(False)
         assert st["dense_fT"]["launches"] == 1
-        big = ham.estimate([1.0], 1, 330, 3, precision="fp64", dist="gauss")  # k d_s^2 = 5280
-        ref = lanczos.Estimator(spec).run([1.0], 1, 330, 3, "gauss")
+        big = ham.estimate(W.beta_grid(8, 0.5, 4.0), 1, 330, 3, precision="fp64", dist="gauss")  # 5280
+        ref = lanczos.Estimator(spec).run(W.beta_grid(8, 0.5, 4.0), 1, 330, 3, "gauss")
         np.testing.assert_allclose(big["rho"], ref["rho"], atol=1e-8, rtol=0)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n,n_sys", [(13, 1), (14, 0), (15, 2)])
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_apply_tiled_bit_exact_hopping_pairs(ctx, lib, n, n_sys, dtype):
+    """All-to-all XX + YY with J^x = J^y (the long-range XXZ shape: every pair hops only
+    antiparallel spins, a coefficient that depends on the parity of the flipped pair) on
+    integer couplings: the tiled SpMM's parity-only paths -- one load per pair of
+    register rows, and partner tiles of single high pairs with a tile-uniform
+    coefficient -- equal H x bit for bit."""
+    torch = _torch()
+    rng = np.random.default_rng(n)
+    spec = W.long_range_xxz(n, n_sys, 0.0, 1.0, 0.0)
+    c = rng.integers(1, 4, size=(n, n)).astype(np.float64)
+    spec.jx[:] = np.triu(c, 1)
+    spec.jy[:] = spec.jx
+    spec.jz[:] = np.triu(rng.integers(-2, 3, size=(n, n)).astype(np.float64), 1)
+    spec.hz[:] = rng.integers(-2, 3, size=n)
+    h = spin_ops.sparse_hamiltonian(spec)
+    ncols = 8 if dtype == "float32" else 4
+    x = rng.integers(-3, 4, size=(1 << n, ncols)).astype(np.float64)
+    ham = lib.Hamiltonian(ctx, spec)
+    xd = torch.from_numpy(x).to(getattr(torch, dtype)).cuda()
+    yd = torch.empty_like(xd)
+    ham.apply(xd, yd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(yd.double().cpu().numpy(), h @ x)
