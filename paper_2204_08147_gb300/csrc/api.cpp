@@ -586,7 +586,10 @@ static rdm_status make_plan_impl(const HostModel& hm, int n_beta, int n_v, int k
   p.gauss = o->vec_dist == RDM_GAUSS;
   p.store = false;
   p.dev_dense = dense && dense_device_fits(k, p.L.DS);
-  p.vstride = (beta_max < 0 ? kChebMaxDegree : dense_device_max_degree(beta_max, hm.hnorm)) + 1;
+  // (rounded up to a multiple of 32, so Hamiltonians with nearby norm bounds plan the
+  // same workspace)
+  p.vstride = std::min(kChebMaxDegree + 1,
+                       ((beta_max < 0 ? kChebMaxDegree : dense_device_max_degree(beta_max, hm.hnorm)) + 32) / 32 * 32);
   if (layout_tiled(p.L)) {
     uint32_t dep;
     int off[8];
@@ -2117,6 +2120,29 @@ size_t batch_workspace_bytes(const rdm_batch_item* items, int n, const size_t* a
 
 static bool valid_opts(const rdm_opts* o);
 
+// Grows the context-owned workspace to at least `need` bytes. A grown workspace gets
+// 1/8 of headroom (within `usable`), so calls whose plans differ slightly (another
+// Hamiltonian's Chebyshev bound, another k) reuse it instead of freeing and
+// reallocating it -- which would also invalidate the first-pass graphs keyed on its
+// addresses.
+static rdm_status grow_own_workspace(rdm_ctx* ctx, size_t need, size_t usable) {
+  if (ctx->own_bytes >= need) return RDM_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->own_ws) CK(cudaFree(ctx->own_ws));
+  ctx->own_ws = nullptr;
+  ctx->own_bytes = 0;
+  size_t want = need + need / 8;
+  want = (want + (size_t(1) << 21) - 1) / (size_t(1) << 21) * (size_t(1) << 21);
+  if (want > usable) want = need;
+  if (cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), want) != cudaSuccess) {
+    cudaGetLastError();
+    want = need;
+    CK(cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), want));
+  }
+  ctx->own_bytes = want;
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, int n_items) {
   if (!ctx || !items || n_items < 1) {
     set_error("rdm_estimate_batch: NULL context or items, or n_items < 1");
@@ -2180,14 +2206,7 @@ extern "C" rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, in
       set_error("rdm_estimate_batch: an item needs %zu bytes of device memory, %zu usable", tot, usable);
       st = RDM_ENOMEM;
     } else if (!ws) {
-      if (ctx->own_bytes < tot) {
-        CK(cudaStreamSynchronize(ctx->stream));
-        if (ctx->own_ws) CK(cudaFree(ctx->own_ws));
-        ctx->own_ws = nullptr;
-        ctx->own_bytes = 0;
-        CK(cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), tot));
-        ctx->own_bytes = tot;
-      }
+      st = grow_own_workspace(ctx, tot, usable);
       ws = ctx->own_ws;
     }
     if (st == RDM_OK)
@@ -2256,14 +2275,8 @@ extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta
   rdm_status pst = RDM_OK;
   const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst, max_beta(betas, n_beta));
   if (need == 0) return pst != RDM_OK ? pst : RDM_ENOMEM;  // make_plan set the message
-  if (ctx->own_bytes < need) {
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->own_ws) CK(cudaFree(ctx->own_ws));
-    ctx->own_ws = nullptr;
-    ctx->own_bytes = 0;
-    CK(cudaMalloc(reinterpret_cast<void**>(&ctx->own_ws), need));
-    ctx->own_bytes = need;
-  }
+  const rdm_status gst = grow_own_workspace(ctx, need, usable);
+  if (gst != RDM_OK) return gst;
   return estimate_impl(ham, ctx->stream, ctx->own_ws, ctx->own_bytes, betas, n_beta, n_v, k, seed,
                        opts, out, &ctx->prof);
 }
