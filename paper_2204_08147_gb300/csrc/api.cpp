@@ -182,6 +182,25 @@ void order_bath_bits(HostModel* h) {
   std::vector<std::pair<uint32_t, uint32_t>> w;
   const double c0 = partner_tiles_of(m, po, cur, nb, w);
   if (c0 == 0.0 || m.empty()) return;
+  // If every transposition of neighbouring bath bits maps the set of (mask, parity-only)
+  // pairs onto itself, so does every permutation (they generate the symmetric group),
+  // and every order has the same count: nothing to search (a field on every site, or
+  // all-to-all couplings).
+  {
+    std::vector<std::pair<uint32_t, char>> base(m.size()), sw(m.size());
+    for (size_t t = 0; t < m.size(); ++t) base[t] = {m[t], po[t]};
+    std::sort(base.begin(), base.end());
+    bool symmetric = true;
+    for (int i = 0; i + 1 < nb && symmetric; ++i) {
+      for (size_t t = 0; t < m.size(); ++t) {
+        const uint32_t x = m[t], bi = (x >> i) & 1u, bj = (x >> (i + 1)) & 1u;
+        sw[t] = {bi == bj ? x : x ^ ((1u << i) | (1u << (i + 1))), po[t]};
+      }
+      std::sort(sw.begin(), sw.end());
+      symmetric = sw == base;
+    }
+    if (symmetric) return;
+  }
   double best = c0;
   uint64_t x = 0x9E3779B97F4A7C15ull;
   auto next = [&]() {

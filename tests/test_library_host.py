@@ -256,3 +256,19 @@ def test_bath_order_keeps_a_model_with_no_gain(rdm):
     assert order == list(range(22)) and before == after == 12.0
     order, before, after = rdm.bath_order(W.xxz_chain(10, 1))
     assert order == list(range(10)) and before == after == 0.0
+
+
+def test_bath_order_search_skipped_for_permutation_symmetric_couplings(rdm):
+    """All-to-all couplings (the long-range XXZ models, where every pair of sites hops) and
+    single-site flips map onto themselves under any permutation of the bath bits, so every
+    order has the same partner count and the search is skipped: the call returns at once.
+    A chain is not symmetric and is searched."""
+    import time
+    import workloads as W
+    for spec in (W.config_c2(0)["spec"], W.config_c3()["spec"], W.config_c5()["spec"]):
+        t = time.perf_counter()
+        order, before, after = rdm.bath_order(spec)
+        assert time.perf_counter() - t < 0.02
+        assert order == list(range(spec.n_sites)) and before == after > 0.0
+    order, before, after = rdm.bath_order(W.xxz_chain(20, 1))
+    assert sorted(order) == list(range(20)) and after <= before
