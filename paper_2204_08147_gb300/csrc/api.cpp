@@ -262,6 +262,33 @@ static int tile_diag_layout(const std::vector<uint32_t>& mlo, uint32_t* dep, int
 }
 
 // Groups the flip terms by m_high = mask >> kTileBits for the tiled SpMM.
+// The order in which the tiled SpMM walks the 2^b tiles of a slice: by the number of
+// set tile bits, and within one count by the ascending list of set bits in
+// lexicographic order (the simplicial order of the b-cube, whose prefixes have the
+// smallest vertex boundary of all sets of their size; Harper 1966). A tile's partners
+// across single and paired high bits then lie in the same or a neighbouring count
+// class, so the W_j tiles a slice still needs stay few enough to be kept in L2; in
+// tile-index order the partner across the top bit comes half a slice later.
+std::vector<uint32_t> tile_walk_order(int b) {
+  std::vector<uint32_t> out;
+  out.reserve((size_t)1 << b);
+  for (int w = 0; w <= b; ++w) {
+    std::vector<int> c(w);  // the set bits, ascending; first subset {0, .., w-1}
+    for (int i = 0; i < w; ++i) c[i] = i;
+    while (true) {
+      uint32_t t = 0;
+      for (int i = 0; i < w; ++i) t |= 1u << c[i];
+      out.push_back(t);
+      int i = w - 1;  // the last position that can still move right
+      while (i >= 0 && c[i] == b - w + i) --i;
+      if (i < 0) break;
+      ++c[i];
+      for (int q = i + 1; q < w; ++q) c[q] = c[q - 1] + 1;
+    }
+  }
+  return out;
+}
+
 void make_term_image(const HostModel& h, TermImage* img) {
   std::map<uint32_t, std::vector<const FlipTerm*>> groups;
   groups[0];  // pattern 0 always exists
@@ -384,6 +411,8 @@ void make_term_image(const HostModel& h, TermImage* img) {
   img->off_dg_thi = put(dg_thi.data(), dg_thi.size() * 4);
   img->off_dg_tc = put(dg_tc.data(), dg_tc.size() * 8);
   img->off_dg_slot = put(dg_slot.data(), dg_slot.size() * 4);
+  const std::vector<uint32_t> walk = tile_walk_order(tiled ? h.n - kTileBits : 0);
+  img->off_tile_order = put(walk.data(), walk.size() * 4);
 }
 
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
@@ -402,6 +431,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   t.term_low = reinterpret_cast<const uint32_t*>(dev + img.off_term_low);
   t.term_odd = reinterpret_cast<const double*>(dev + img.off_term_odd);
   t.term_even = reinterpret_cast<const double*>(dev + img.off_term_even);
+  t.tile_order = reinterpret_cast<const uint32_t*>(dev + img.off_tile_order);
   TileDiag& d = t.dg;
   d.n_groups = img.n_dg_groups;
   d.n_terms = img.n_dg_terms;

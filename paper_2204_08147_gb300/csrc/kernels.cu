@@ -855,7 +855,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     bool stop = false;
     for (int64_t gt = blockIdx.x; gt < n_tiles && !stop; gt += gridDim.x) {
       const int slice = (int)(gt >> tile_log);
-      const uint32_t ut = (uint32_t)gt & tile_mask;
+      const uint32_t ut = tt.tile_order[(uint32_t)gt & tile_mask];
       const size_t soff = (size_t)slice * L.D * BS;
       const T* W = reinterpret_cast<const T*>(a.w) + soff;
       const T* Wp = has_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
     }
     if (aborted) continue;
 
-    const uint32_t ut = (uint32_t)gt & tile_mask;
+    const uint32_t ut = tt.tile_order[(uint32_t)gt & tile_mask];
     const uint32_t row0 = ut << kTileBits;
     const unsigned char* sp;
     // own tile: diagonal and in-tile terms

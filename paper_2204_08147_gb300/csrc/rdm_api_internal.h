@@ -153,12 +153,14 @@ struct TermImage {
   std::vector<unsigned char> bytes;
   size_t off_flips = 0, off_diags = 0, off_pat_high = 0, off_pat_start = 0, off_pat_flags = 0,
          off_term_low = 0, off_term_odd = 0, off_term_even = 0, off_dg_low = 0, off_dg_mlo = 0,
-         off_dg_hstart = 0, off_dg_thi = 0, off_dg_tc = 0, off_dg_slot = 0;
+         off_dg_hstart = 0, off_dg_thi = 0, off_dg_tc = 0, off_dg_slot = 0, off_tile_order = 0;
   int n_pat = 0, n_terms = 0, all_active = 1, partners_flat = 0, all_uniform = 1, n_reg0 = 0, n_dg_groups = 0,
       n_dg_terms = 0, dg_entries = 0;
   uint32_t dg_dep = 0;
   int dg_off[8] = {};
 };
+// Order of the tiled SpMM's walk over the 2^b tiles of a slice (a permutation).
+std::vector<uint32_t> tile_walk_order(int b);
 void make_term_image(const HostModel& h, TermImage* img);
 // Points ham's device term pointers into `dev`, a device copy of img.bytes.
 void bind_terms(const TermImage& img, char* dev, rdm_ham* ham);

@@ -174,6 +174,7 @@ struct TiledTerms {
   const uint32_t* term_low;   // [n_terms]
   const double* term_odd;     // [n_terms]
   const double* term_even;    // [n_terms]
+  const uint32_t* tile_order;  // [tiles per slice]: the walk's k-th tile of a slice
   TileDiag dg;
 };
 
