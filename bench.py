@@ -470,7 +470,10 @@ def run_ours(a):
     step_c = 3.0 * blk
     roof["step"] = {"compulsory_bytes": step_c, "ms_spmm_plus_orth": step_ms,
                     "gbs": step_c / (step_ms / 1000.0) / 1e9 if step_ms > 0 else None,
-                    "frac": (step_c / (step_ms / 1000.0) / 1e9) / peak if step_ms > 0 else None}
+                    "frac": (step_c / (step_ms / 1000.0) / 1e9) / peak if step_ms > 0 else None,
+                    # against the 6 blocks any streaming form moves when A_j = W_j^T Z must
+                    # be complete before W_{j+1} can be written
+                    "frac_two_pass": (2.0 * step_c / (step_ms / 1000.0) / 1e9) / peak if step_ms > 0 else None}
     sm_max = clk.get("sm_max_mhz") or 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     spmm_tflops = 2.0 * (1 << a.n_sites) * cols * (f_off + 1) / (sp_ms / sp_launch / 1000.0) / 1e12 \
