@@ -311,6 +311,48 @@ void make_term_image(const HostModel& h, TermImage* img) {
   std::vector<std::pair<const uint32_t, std::vector<const FlipTerm*>>*> order;
   for (auto& kv : groups) order.push_back(&kv);
   std::sort(order.begin() + 1, order.end(), [](auto* x, auto* y) { return x->first > y->first; });
+  // Pairable partner tiles: one high spin h, and terms that each hop it with one spin
+  // l inside the tile with a parity-only coefficient (c_even = 0: XX + YY with
+  // J^x = J^y), the same set of l in every such group. For a given tile, a group whose
+  // h is down acts on the rows with l up and a group whose h is up on the rows with l
+  // down, so the SpMM consumes one of each together and every row takes exactly one of
+  // the two loads (no idle lanes). They go first, their terms in ascending l.
+  auto low_list = [](const std::vector<const FlipTerm*>& ts, std::vector<uint32_t>* out) -> bool {
+    out->clear();
+    for (const FlipTerm* f : ts) {
+      const uint32_t low = f->mask & (uint32_t)(kTileRows - 1);
+      if (__builtin_popcount(low) != 1 || f->c_even != 0.0 || f->c_odd == 0.0) return false;
+      out->push_back(low);
+    }
+    std::sort(out->begin(), out->end());
+    return std::adjacent_find(out->begin(), out->end()) == out->end();
+  };
+  int n_pair = 0;
+  {
+    std::vector<uint32_t> first, cur;
+    std::vector<char> is_pair(order.size(), 0);
+    bool have = false;
+    for (size_t q = 1; q < order.size(); ++q) {
+      if (__builtin_popcount(order[q]->first) != 1 || !low_list(order[q]->second, &cur)) continue;
+      if (!have) {
+        first = cur;
+        have = true;
+      }
+      if (cur == first) is_pair[q] = 1;
+    }
+    for (size_t q = 1; q < order.size(); ++q) n_pair += is_pair[q];
+    if (n_pair >= 2) {
+      std::vector<std::pair<const uint32_t, std::vector<const FlipTerm*>>*> head{order[0]}, tail;
+      for (size_t q = 1; q < order.size(); ++q) (is_pair[q] ? head : tail).push_back(order[q]);
+      for (size_t q = 1; q < head.size(); ++q)
+        std::sort(head[q]->second.begin(), head[q]->second.end(),
+                  [](const FlipTerm* x, const FlipTerm* y) { return x->mask < y->mask; });
+      order = head;
+      order.insert(order.end(), tail.begin(), tail.end());
+    } else {
+      n_pair = 0;
+    }
+  }
   for (auto* kvp : order) {
     auto& kv = *kvp;
     pat_high.push_back(kv.first);
@@ -386,6 +428,7 @@ void make_term_image(const HostModel& h, TermImage* img) {
   for (size_t t = 0; t < term_odd.size(); ++t)
     if (term_odd[t] != term_even[t]) img->all_uniform = 0;
   img->n_pat = tiled ? (int)pat_high.size() : 0;
+  img->n_pair = tiled ? n_pair : 0;
   img->n_terms = tiled ? (int)term_low.size() : 0;
   auto& b = img->bytes;
   b.clear();
@@ -420,6 +463,7 @@ void bind_terms(const TermImage& img, char* dev, rdm_ham* ham) {
   ham->d_diags = reinterpret_cast<DiagTerm*>(dev + img.off_diags);
   TiledTerms& t = ham->tiled;
   t.n_pat = img.n_pat;
+  t.n_pair = img.n_pair;
   t.all_active = img.all_active;
   t.partners_flat = img.partners_flat;
   t.all_uniform = img.all_uniform;

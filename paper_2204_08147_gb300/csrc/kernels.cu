@@ -732,6 +732,69 @@ __device__ __forceinline__ void apply2_uniform(T (&y)[RPT][VW], int rgoff, const
   }
 }
 
+// Pairable partner tiles (TiledTerms::n_pair): for a tile, the groups of one high spin h
+// whose h is down (zm, bit q = pattern q + 1) and up (om). The i-th stage of the block:
+// down and up groups alternate (z_0, o_0, z_1, o_1, ..), then the rest of the longer list.
+__device__ __forceinline__ int pair_pattern(int i, uint32_t zm, uint32_t om) {
+  const int nz = __popc(zm), no = __popc(om), mn = nz < no ? nz : no;
+  uint32_t m;
+  int k;
+  if (i < 2 * mn) {
+    m = (i & 1) ? om : zm;
+    k = i >> 1;
+  } else {
+    m = nz > no ? zm : om;
+    k = i - mn;
+  }
+  for (; k > 0; --k) m &= m - 1u;
+  return __ffs((int)m);
+}
+
+// Term i of both groups hops the same in-tile spin l with h (parity-only coefficient,
+// active where l and h differ): with h down in PZ and up in PO, a row whose spin l is up
+// takes PZ's term and a row whose spin l is down PO's, so every row loads once per l.
+template <int K, typename T, int VW, int RPT>
+__device__ __forceinline__ void paired_reg(T (&y)[RPT][VW], const T* PZ, const T* PO, int x, int kStep, T cz,
+                                           T co) {
+  if constexpr (K >= RPT) return;
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    T xp[VW];
+    VecIO<T, VW>::ld_rw(xp, ((m & K) ? PZ : PO) + (x ^ (m * kStep)));
+    const T c = (m & K) ? cz : co;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+  }
+}
+template <typename T, int VW, int RPT, int RG, int BS>
+__device__ __forceinline__ void apply_paired(T (&y)[RPT][VW], int rgoff, int rg, const T* PZ, const T* PO,
+                                             const TermS<T>* tz, const TermS<T>* to, int nt) {
+  constexpr int kStep = RG * BS;
+  for (int i = 0; i < nt; ++i) {
+    const uint32_t ml = tz[i].low;
+    const T cz = tz[i].co, co = to[i].co;
+    const int x = partner_base<RG, BS>(rgoff, ml);
+    if (ml < (uint32_t)RG) {  // spin l is a bit of rg: the same for all of this thread's rows
+      const bool up = ((uint32_t)rg & ml) != 0u;
+      const T* P = up ? PZ : PO;
+      const T c = up ? cz : co;
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        T xp[VW];
+        VecIO<T, VW>::ld_rw(xp, P + x + m * kStep);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) y[m][v] = fma(c, xp[v], y[m][v]);
+      }
+    } else {
+      switch (ml / (uint32_t)RG) {
+        case 1u: paired_reg<1, T, VW, RPT>(y, PZ, PO, x, kStep, cz, co); break;
+        case 2u: paired_reg<2, T, VW, RPT>(y, PZ, PO, x, kStep, cz, co); break;
+        default: paired_reg<4, T, VW, RPT>(y, PZ, PO, x, kStep, cz, co); break;
+      }
+    }
+  }
+}
+
 // Diagonal of H on this thread's RPT rows rg + RG m of a tile, from the tile's A-table
 // row hk (TileDiag): low[r] + sum_q A_q (-1)^popc(q & m), one RPT-point Walsh-Hadamard
 // transform of the A_q.
@@ -777,7 +840,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
   static_assert((1 << RGL) == RG && RGL == kTileRegShift, "row groups are the low tile bits");
   extern __shared__ __align__(128) unsigned char smem[];
   const TiledTerms& tt = a.tiled;
-  const int npat = tt.n_pat, nterm = tt.n_terms;
+  const int npat = tt.n_pat, nterm = tt.n_terms, npair = tt.n_pair;
   const int hstride = tile_diag_stride(tt.dg.n_entries, (int)sizeof(T));
   const uint32_t kSlotBytes = tiled_slot_bytes(tt.dg.n_entries, (int)sizeof(T));
   unsigned char* const ring = smem;
@@ -859,8 +922,14 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       const size_t soff = (size_t)slice * L.D * BS;
       const T* W = reinterpret_cast<const T*>(a.w) + soff;
       const T* Wp = has_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
+      uint32_t zm = 0u, om = 0u;  // pairable groups with their high spin down / up here
+      for (int q = 0; q < npair; ++q) {
+        if (ut & pat[1 + q].high) om |= 1u << q;
+        else zm |= 1u << q;
+      }
       // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
       int kind = -1;
+      int pi = 0;  // pairable stages issued
       while (true) {
         if (seq % kProducerWarps == q) {
           if (round > 0 && !ring_wait(&empty[slot], (round - 1u) & 1u, abort_flag)) {
@@ -889,7 +958,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         }
         // next stage of this tile
         if (kind == -2) break;
-        const int p = all_active ? (kind == -1 ? 1 : kind + 1) : tiled_next(kind == -1 ? 1 : kind + 1, npat, ut, pat);
+        int p;
+        if (pi < npair) {
+          p = pair_pattern(pi++, zm, om);
+        } else {
+          const int from = kind <= npair ? npair + 1 : kind + 1;
+          p = all_active ? from : tiled_next(from, npat, ut, pat);
+        }
         if (p < npat) {
           kind = p;
         } else if (has_prev) {
@@ -1068,6 +1143,61 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       ++t;
     }
     release();
+    // the terms of one partner pattern A, copied to P (any coefficients)
+    auto pattern_terms = [&](const PatS<T>& A, const T* P) {
+      const uint32_t hi_bits = A.high << kTileBits;
+      for (int t = A.start; t < A.end;) {
+        const TermS<T> d = term[t];
+        if (d.co == d.ce && t + 1 < A.end) {
+          const TermS<T> d2 = term[t + 1];
+          if (d2.co == d2.ce) {
+            apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, P, d.low, d.co, P, d2.low, d2.co);
+            t += 2;
+            continue;
+          }
+        }
+        apply_term<T, VW, RPT, RG, BS, UNI>(y, rgoff, rg, P, d.low, d.low | hi_bits, d.co, d.ce, row0);
+        ++t;
+      }
+    };
+    if constexpr (!UNI) {
+      // pairable partner tiles: a group with its high spin down and one with it up
+      // together, then the rest of the longer list one by one
+      if (npair > 0) {
+        uint32_t zm = 0u, om = 0u;
+        for (int q = 0; q < npair; ++q) {
+          if (ut & pat[1 + q].high) om |= 1u << q;
+          else zm |= 1u << q;
+        }
+        const int nz = __popc(zm), no = __popc(om);
+        const int n2 = 2 * (nz < no ? nz : no);
+        for (int i = 0; i < npair;) {
+          const PatS<T> A = pat[pair_pattern(i, zm, om)];
+          if (i < n2) {
+            const PatS<T> B = pat[pair_pattern(i + 1, zm, om)];
+            const unsigned char* sp2;
+            if (!acquire(sp, 0) || !acquire(sp2, 1)) {
+              aborted = true;
+              break;
+            }
+            apply_paired<T, VW, RPT, RG, BS>(y, rgoff, rg, reinterpret_cast<const T*>(sp),
+                                             reinterpret_cast<const T*>(sp2), term + A.start, term + B.start,
+                                             A.end - A.start);
+            release2();
+            i += 2;
+          } else {
+            if (!acquire(sp, 0)) {
+              aborted = true;
+              break;
+            }
+            pattern_terms(A, reinterpret_cast<const T*>(sp));
+            release();
+            ++i;
+          }
+        }
+        if (aborted) continue;
+      }
+    }
     // partner tiles; two single-term patterns are consumed together so their
     // shared-memory loads overlap
     if (partners_flat) {
@@ -1109,7 +1239,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         }
       }
     } else
-    for (int p = all_active ? 1 : tiled_next(1, npat, ut, pat); p < npat;) {
+    for (int p = all_active ? npair + 1 : tiled_next(npair + 1, npat, ut, pat); p < npat;) {
       const int pn = all_active ? p + 1 : tiled_next(p + 1, npat, ut, pat);
       const PatS<T> A = pat[p];
       if (A.single & 2u) {
@@ -1168,21 +1298,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
         aborted = true;
         break;
       }
-      const T* P = reinterpret_cast<const T*>(sp);
-      const uint32_t hi_bits = A.high << kTileBits;
-      for (int t = A.start; t < A.end;) {
-        const TermS<T> d = term[t];
-        if (d.co == d.ce && t + 1 < A.end) {
-          const TermS<T> d2 = term[t + 1];
-          if (d2.co == d2.ce) {
-            apply2_uniform<T, VW, RPT, RG, BS>(y, rgoff, P, d.low, d.co, P, d2.low, d2.co);
-            t += 2;
-            continue;
-          }
-        }
-        apply_term<T, VW, RPT, RG, BS, UNI>(y, rgoff, rg, P, d.low, d.low | hi_bits, d.co, d.ce, row0);
-        ++t;
-      }
+      pattern_terms(A, reinterpret_cast<const T*>(sp));
       release();
       p = pn;
     }

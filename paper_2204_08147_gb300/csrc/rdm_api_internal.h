@@ -154,7 +154,7 @@ struct TermImage {
   size_t off_flips = 0, off_diags = 0, off_pat_high = 0, off_pat_start = 0, off_pat_flags = 0,
          off_term_low = 0, off_term_odd = 0, off_term_even = 0, off_dg_low = 0, off_dg_mlo = 0,
          off_dg_hstart = 0, off_dg_thi = 0, off_dg_tc = 0, off_dg_slot = 0, off_tile_order = 0;
-  int n_pat = 0, n_terms = 0, all_active = 1, partners_flat = 0, all_uniform = 1, n_reg0 = 0, n_dg_groups = 0,
+  int n_pat = 0, n_pair = 0, n_terms = 0, all_active = 1, partners_flat = 0, all_uniform = 1, n_reg0 = 0, n_dg_groups = 0,
       n_dg_terms = 0, dg_entries = 0;
   uint32_t dg_dep = 0;
   int dg_off[8] = {};

@@ -163,6 +163,8 @@ RDM_HD inline int tile_diag_stride(int n_entries, int elem) {
 
 struct TiledTerms {
   int n_pat;
+  int n_pair;                 // patterns 1..n_pair: one high spin, the same in-tile hop
+                              // partners, parity-only (consumed in opposite-spin pairs)
   int n_terms;
   int all_active;             // 1: every tile needs every partner pattern
   int partners_flat;          // 1: and each is one uniform term with m_low = 0

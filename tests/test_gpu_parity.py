@@ -737,14 +737,17 @@ def test_device_dense_step_is_used_and_large_t_falls_back(lib):
         ctx.close()
 
 
-@pytest.mark.parametrize("n,n_sys", [(13, 1), (14, 0), (15, 2)])
+@pytest.mark.parametrize("n,n_sys,fields", [(13, 1, 0), (14, 0, 0), (15, 2, 0), (14, 1, 2), (16, 2, 5)])
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
-def test_apply_tiled_bit_exact_hopping_pairs(ctx, lib, n, n_sys, dtype):
+def test_apply_tiled_bit_exact_hopping_pairs(ctx, lib, n, n_sys, fields, dtype):
     """All-to-all XX + YY with J^x = J^y (the long-range XXZ shape: every pair hops only
     antiparallel spins, a coefficient that depends on the parity of the flipped pair) on
     integer couplings: the tiled SpMM's parity-only paths -- one load per pair of
-    register rows, and partner tiles of single high pairs with a tile-uniform
-    coefficient -- equal H x bit for bit."""
+    register rows, partner tiles of single high pairs with a tile-uniform coefficient,
+    and the partner tiles of one high spin consumed in opposite-spin pairs (with an
+    uneven split of down and up spins on most tiles) -- equal H x bit for bit. With
+    `fields` transverse fields on the first sites (the high spins of the tile), those
+    spins' partner groups also carry a single flip and are not paired."""
     torch = _torch()
     rng = np.random.default_rng(n)
     spec = W.long_range_xxz(n, n_sys, 0.0, 1.0, 0.0)
@@ -753,6 +756,7 @@ def test_apply_tiled_bit_exact_hopping_pairs(ctx, lib, n, n_sys, dtype):
     spec.jy[:] = spec.jx
     spec.jz[:] = np.triu(rng.integers(-2, 3, size=(n, n)).astype(np.float64), 1)
     spec.hz[:] = rng.integers(-2, 3, size=n)
+    spec.gx[:fields] = rng.integers(1, 3, size=fields)
     h = spin_ops.sparse_hamiltonian(spec)
     ncols = 8 if dtype == "float32" else 4
     x = rng.integers(-3, 4, size=(1 << n, ncols)).astype(np.float64)
