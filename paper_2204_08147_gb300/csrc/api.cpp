@@ -595,6 +595,7 @@ struct Plan {
   Layout Lg;  // the same memory grouped by d_s columns: the Gram view
   bool single;                        // one block-size-1 recurrence per column
   int n_v, n_v_pad, k, n_beta, nbc;  // nbc: betas per pass-2 sweep
+  int nsc = 0;                        // pass 2: slices per sweep (0: all of them)
   bool gauss;                         // Gaussian bath vectors are generated once into a buffer
   bool store;                         // keep all k+1 Krylov blocks (no second pass)
   size_t tk_bytes;                    // K table of the tiled diagonal (0 if untiled)
@@ -625,7 +626,7 @@ static size_t plan_bytes(const Plan& p) {
   const size_t ng = L.n_groups(), nv = (size_t)L.DS * L.DS;
   const PlanSizes z = plan_sizes(p);
   a.take<char>(L.block_bytes() * (p.store ? (size_t)p.k + 1 : 3));
-  if (!p.store) a.take<char>(L.block_bytes() * p.nbc);
+  if (!p.store) a.take<char>(L.block_bytes() / (size_t)L.n_slices * (size_t)(p.nsc ? p.nsc : L.n_slices) * p.nbc);
   a.take<double>(z.partials);
   a.take<double>((size_t)(p.k + 2) * ng * nv * 3);
   a.take<double>((size_t)p.k * ng * nv * 2);
@@ -715,6 +716,23 @@ static rdm_status make_plan_impl(const HostModel& hm, int n_beta, int n_v, int k
     q.nbc = p.nbc + 1;
     if (plan_bytes(q) > avail) break;
     p = q;
+  }
+  // Fewer betas per sweep than the grid: every sweep repeats the whole recurrence for
+  // every bath vector. Sweeps over groups of slices (of bath vectors) with all betas
+  // repeat none of it, and the same memory holds psi for all betas of fewer slices.
+  if (p.nbc < n_beta && !p.single && p.L.n_slices > 1) {
+    Plan q = p;
+    q.nbc = n_beta;
+    int best = 0;
+    for (int ns = 1; ns < p.L.n_slices; ++ns) {
+      q.nsc = ns;
+      if (plan_bytes(q) > avail) break;
+      best = ns;
+    }
+    if (best > 0) {
+      q.nsc = best;
+      p = q;
+    }
   }
   *out = p;
   return RDM_OK;
@@ -1459,7 +1477,8 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
     char* base = ar.take<char>(L.block_bytes() * nblk);
     for (int i = 0; i < nblk; ++i) blk[i] = base + (size_t)i * L.block_bytes();
   }
-  psi = store ? nullptr : ar.take<char>(L.block_bytes() * p.nbc);
+  psi = store ? nullptr
+              : ar.take<char>(L.block_bytes() / (size_t)L.n_slices * (size_t)(p.nsc ? p.nsc : L.n_slices) * p.nbc);
   psz = plan_sizes(p);
   pstride = (size_t)L.n_slices * L.gridx * L.groups_per_slice() * nv;
   pstride_g = (size_t)Lg.n_slices * Lg.gridx * Lg.groups_per_slice() * nvo;
@@ -1863,33 +1882,82 @@ rdm_status EstimateRun::finish_rest() {
           }));
       }
     } else {
-    // ---- pass 2: recompute W_j (bit-identical) and accumulate psi.
-    st = init_block(blk[0]);
-    if (st != RDM_OK) return st;
-    CK(timed(kKPsiInit, blk_b * (1 + nb), [&] { return launch_psi_init(L, blk[0], psi, d_e, nb, s); }));
-    cur = 0;
-    prv = -1;
-    nxt = 1;
-    for (int j = 1; j < k_eff; ++j) {
-      sa.w = blk[cur];
-      sa.w_prev = prv >= 0 ? blk[prv] : nullptr;
-      sa.z = blk[nxt];
-      sa.mz = MZ(j);
-      sa.cp = CP(j);
-      sa.partials = nullptr;
-      CK(timed(kKSpmm2, blk_b * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(L, kModePass2, sa, s); }));
-      CK(timed(kKOrth2, blk_b * (3 + 2 * nb), [&] {
-        return launch_orth_psi(L, blk[cur], blk[nxt], CW(j), psi, d_e + (size_t)j * p.nbc * cstride, nb, s);
-      }));
-      const int old_prev = prv;
-      prv = cur;
-      cur = nxt;
-      nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
-    }
-    for (int bi = 0; bi < nb; ++bi) {
-      CK(timed(kKGram, blk_b, [&] { return launch_final_gram(Lg, psi + (size_t)bi * L.block_bytes(), partials, s); }));
-      CK(counted([&] { return launch_reduce_gram(Lg, partials, d_gram + (size_t)bi * cstride_g, s); }));
-    }
+      // ---- pass 2: recompute W_j (bit-identical) and accumulate psi, one sweep per
+      // group of nsc slices (the whole block unless the plan splits it).
+      const int nsc = p.nsc > 0 ? p.nsc : L.n_slices;
+      const size_t slice_b = L.block_bytes() / (size_t)L.n_slices;
+      // betas by their last needed step, longest first, so step j updates only the psi
+      // of the betas still active there
+      std::vector<int> ord(nb), kb(nb);
+      std::vector<double> hEc;
+      for (int s0 = 0; s0 < L.n_slices; s0 += nsc) {
+        const int nsl = std::min(nsc, L.n_slices - s0);
+        Layout Ls = L, Lgs = Lg;
+        Ls.n_slices = Lgs.n_slices = nsl;
+        Ls.B = nsl * L.Bs;
+        Lgs.B = nsl * Lg.Bs;
+        const int g0 = s0 * L.groups_per_slice(), ngs = Ls.n_groups();
+        const int g0o = s0 * Lg.groups_per_slice(), ngso = Lgs.n_groups();
+        const size_t off = (size_t)s0 * slice_b, cs = (size_t)ngs * nv, cso = (size_t)ngso * nvo;
+        const double bs = (double)Ls.block_bytes();
+        int ke = 1;
+        for (int bi = 0; bi < nb; ++bi) {
+          kb[bi] = 1;
+          for (int l = g0o; l < std::min(n_v, g0o + ngso); ++l) kb[bi] = std::max(kb[bi], jlast[(size_t)bi * n_v + l]);
+          ke = std::max(ke, kb[bi]);
+          ord[bi] = bi;
+        }
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return kb[x] > kb[y]; });
+        hEc.assign((size_t)k * p.nbc * cs, 0.0);
+        for (int j = 0; j < k; ++j)
+          for (int r = 0; r < nb; ++r)
+            std::copy_n(&hE[(((size_t)j * p.nbc + ord[r]) * ng + g0) * nv], cs, &hEc[((size_t)j * p.nbc + r) * cs]);
+        CK(cudaMemcpyAsync(d_e, hEc.data(), hEc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        h2d += hEc.size() * sizeof(double);
+        {
+          const BathPerm bp = hm.perm();
+          const char* vb = d_vbuf ? d_vbuf + (size_t)(g0 / sub) * (size_t)d_b * L.elem : nullptr;
+          CK(timed(kKInit, bs, [&] {
+            return launch_init_block(Ls, o->vec_dist, seed, o->first_vector + g0 / sub, n_v - g0 / sub, nullptr, vb,
+                                     blk[0] + off, s, sub, &bp);
+          }));
+        }
+        CK(timed(kKPsiInit, bs * (1 + nb), [&] { return launch_psi_init(Ls, blk[0] + off, psi, d_e, nb, s); }));
+        cur = 0;
+        prv = -1;
+        nxt = 1;
+        for (int j = 1; j < ke; ++j) {
+          int na = 0;  // betas still active at step j
+          while (na < nb && kb[ord[na]] > j) ++na;
+          sa.w = blk[cur] + off;
+          sa.w_prev = prv >= 0 ? blk[prv] + off : nullptr;
+          sa.z = blk[nxt] + off;
+          sa.mz = MZ(j) + (size_t)g0 * nv;
+          sa.cp = CP(j) + (size_t)g0 * nv;
+          sa.partials = nullptr;
+          CK(timed(kKSpmm2, bs * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(Ls, kModePass2, sa, s); }));
+          CK(timed(kKOrth2, bs * (3 + 2 * na), [&] {
+            return launch_orth_psi(Ls, blk[cur] + off, blk[nxt] + off, CW(j) + (size_t)g0 * nv, psi,
+                                   d_e + (size_t)j * p.nbc * cs, na, s);
+          }));
+          const int old_prev = prv;
+          prv = cur;
+          cur = nxt;
+          nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+        }
+        for (int r = 0; r < nb; ++r) {
+          CK(timed(kKGram, bs, [&] { return launch_final_gram(Lgs, psi + (size_t)r * Ls.block_bytes(), partials, s); }));
+          CK(counted([&] { return launch_reduce_gram(Lgs, partials, d_gram + (size_t)r * cso, s); }));
+        }
+        CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cso * sizeof(double), cudaMemcpyDeviceToHost, s));
+        d2h += (size_t)nb * cso * sizeof(double);
+        CK(cudaStreamSynchronize(s));
+        for (int r = 0; r < nb; ++r)
+          for (int l = g0o; l < std::min(n_v, g0o + ngso); ++l)
+            for (int v = 0; v < nvo; ++v)
+              gram[((size_t)(b0 + ord[r]) * n_v + l) * nvo + v] = hg[((size_t)r * ngso + (l - g0o)) * nvo + v];
+      }
+      continue;
     }
     CK(cudaMemcpyAsync(hg.data(), d_gram, (size_t)nb * cstride_g * sizeof(double),
                        cudaMemcpyDeviceToHost, s));

@@ -429,6 +429,33 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
     assert e.value.status == lib.ENOMEM
 
 
+def test_slice_sweeps_when_psi_of_all_betas_fits_some_slices(ctx, lib):
+    """A caller workspace with room for the psi of every beta over one of the block's 4
+    slices (bath vectors 4l..4l+3) but not over all: pass 2 sweeps slice by slice with
+    every beta (4 sweeps of a quarter block, instead of 5 full-width sweeps of one beta),
+    and gives the stored-basis result bit for bit."""
+    spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = list(W.beta_grid(5, 0.1, 10.0))
+    ref = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True, passes="store")
+    nbytes = ham.workspace_size(len(betas), 16, 25, precision="fp32", dist="rademacher")
+    block = (1 << 13) * 32 * 4  # 2^13 states x (16 vectors x d_s = 2) float32 columns
+    sweeps = {}
+    for extra in (0, block):
+        ctx.attach_workspace(nbytes + extra)
+        try:
+            ctx.profile(True)
+            got = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True)
+            st = ctx.profile_stats()
+            ctx.profile(False)
+        finally:
+            ctx.detach_workspace()
+        for key in ("rho", "lnZ", "gram_l"):
+            np.testing.assert_array_equal(got[key], ref[key])
+        sweeps[extra] = st["psi_init"]["launches"]
+    assert sweeps == {0: 5, block: 4}
+
+
 # ---------------------------------------------------------------- bath-vector shards
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
