@@ -430,30 +430,45 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
 
 
 def test_slice_sweeps_when_psi_of_all_betas_fits_some_slices(ctx, lib):
-    """A caller workspace with room for the psi of every beta over one of the block's 4
-    slices (bath vectors 4l..4l+3) but not over all: pass 2 sweeps slice by slice with
-    every beta (4 sweeps of a quarter block, instead of 5 full-width sweeps of one beta),
-    and gives the stored-basis result bit for bit."""
+    """Caller workspaces from the default size down to the smallest that runs, in
+    eighths of a block: where psi of every beta fits over some of the block's 4 slices
+    (bath vectors 4l..4l+3) but not over all, pass 2 sweeps over groups of slices with
+    every beta; below that, over groups of betas at full width. Every size gives the
+    stored-basis result bit for bit, and the slice sweeps run fewer pass-2 SpMM bytes
+    than the beta sweeps (no recurrence repeated). The mode is read from the psi_init
+    launches: slice sweeps write (1 + n_beta) blocks in all, beta sweeps one more block
+    per extra sweep."""
     spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
     ham = lib.Hamiltonian(ctx, spec)
     betas = list(W.beta_grid(5, 0.1, 10.0))
     ref = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True, passes="store")
     nbytes = ham.workspace_size(len(betas), 16, 25, precision="fp32", dist="rademacher")
     block = (1 << 13) * 32 * 4  # 2^13 states x (16 vectors x d_s = 2) float32 columns
-    sweeps = {}
-    for extra in (0, block):
-        ctx.attach_workspace(nbytes + extra)
+    spmm2 = {"slices": [], "betas": []}
+    ws = nbytes
+    while ws > block:
+        ctx.attach_workspace(ws)
         try:
             ctx.profile(True)
             got = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True)
             st = ctx.profile_stats()
             ctx.profile(False)
+        except lib.RdmError as e:
+            assert e.status == lib.ENOMEM
+            break
         finally:
             ctx.detach_workspace()
         for key in ("rho", "lnZ", "gram_l"):
             np.testing.assert_array_equal(got[key], ref[key])
-        sweeps[extra] = st["psi_init"]["launches"]
-    assert sweeps == {0: 5, block: 4}
+        sweeps, written = st["psi_init"]["launches"], st["psi_init"]["bytes"] / block
+        if sweeps > 1:
+            mode = "slices" if written == 1 + len(betas) else "betas"
+            if mode == "betas":
+                assert written == sweeps + len(betas)
+            spmm2[mode].append(st["spmm_pass2"]["bytes"])
+        ws -= block // 8
+    assert spmm2["slices"] and spmm2["betas"]
+    assert max(spmm2["slices"]) < min(spmm2["betas"])
 
 
 # ---------------------------------------------------------------- bath-vector shards
