@@ -923,9 +923,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_spmm_tiled(Layout L, SpmmA
       const T* W = reinterpret_cast<const T*>(a.w) + soff;
       const T* Wp = has_prev ? reinterpret_cast<const T*>(a.w_prev) + soff : nullptr;
       uint32_t zm = 0u, om = 0u;  // pairable groups with their high spin down / up here
-      for (int q = 0; q < npair; ++q) {
-        if (ut & pat[1 + q].high) om |= 1u << q;
-        else zm |= 1u << q;
+      for (int i = 0; i < npair; ++i) {
+        if (ut & pat[1 + i].high) om |= 1u << i;
+        else zm |= 1u << i;
       }
       // stage kinds: -1 = own, -2 = W_{j-1}, p >= 1 = partner pattern p
       int kind = -1;
