@@ -1914,36 +1914,58 @@ rdm_status EstimateRun::finish_rest() {
             std::copy_n(&hE[(((size_t)j * p.nbc + ord[r]) * ng + g0) * nv], cs, &hEc[((size_t)j * p.nbc + r) * cs]);
         CK(cudaMemcpyAsync(d_e, hEc.data(), hEc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         h2d += hEc.size() * sizeof(double);
+        // Basis blocks of the sweep: W_i (i = 1, 2, ..) in a ring. With a slice group
+        // smaller than the block, the three full-width blocks of pass 1 (dead by now) hold
+        // more than three blocks of the group: the last mb blocks are kept and psi is
+        // updated from them together every mb steps (the same fma sequence per element),
+        // reading and writing psi once per mb steps.
+        const size_t cb = Ls.block_bytes();
+        const size_t e_smem = (size_t)nb * Ls.groups_per_slice() * nv * L.elem;
+        int mb = (int)std::min<size_t>(kPsiBatchMax, 3 * L.block_bytes() / cb - 2);
+        while (mb > 1 && (size_t)mb * e_smem > ((size_t)160 << 10)) --mb;
+        if (mb < 2) mb = 1;
+        const int ring = mb > 1 ? mb + 2 : 3;
+        auto wblk = [&](int i) -> char* {
+          return mb > 1 ? blk[0] + (size_t)((i - 1) % ring) * cb : blk[(i - 1) % 3] + off;
+        };
+        auto active = [&](int j) {  // betas still active at step j
+          int na = 0;
+          while (na < nb && kb[ord[na]] > j) ++na;
+          return na;
+        };
         {
           const BathPerm bp = hm.perm();
           const char* vb = d_vbuf ? d_vbuf + (size_t)(g0 / sub) * (size_t)d_b * L.elem : nullptr;
           CK(timed(kKInit, bs, [&] {
             return launch_init_block(Ls, o->vec_dist, seed, o->first_vector + g0 / sub, n_v - g0 / sub, nullptr, vb,
-                                     blk[0] + off, s, sub, &bp);
+                                     wblk(1), s, sub, &bp);
           }));
         }
-        CK(timed(kKPsiInit, bs * (1 + nb), [&] { return launch_psi_init(Ls, blk[0] + off, psi, d_e, nb, s); }));
-        cur = 0;
-        prv = -1;
-        nxt = 1;
+        CK(timed(kKPsiInit, bs * (1 + nb), [&] { return launch_psi_init(Ls, wblk(1), psi, d_e, nb, s); }));
+        int j0 = 1;  // first step whose psi update is pending
         for (int j = 1; j < ke; ++j) {
-          int na = 0;  // betas still active at step j
-          while (na < nb && kb[ord[na]] > j) ++na;
-          sa.w = blk[cur] + off;
-          sa.w_prev = prv >= 0 ? blk[prv] + off : nullptr;
-          sa.z = blk[nxt] + off;
+          const int na = active(j);
+          sa.w = wblk(j);
+          sa.w_prev = j >= 2 ? wblk(j - 1) : nullptr;
+          sa.z = wblk(j + 1);
           sa.mz = MZ(j) + (size_t)g0 * nv;
           sa.cp = CP(j) + (size_t)g0 * nv;
           sa.partials = nullptr;
-          CK(timed(kKSpmm2, bs * (prv >= 0 ? 3 : 2), [&] { return launch_spmm(Ls, kModePass2, sa, s); }));
-          CK(timed(kKOrth2, bs * (3 + 2 * na), [&] {
-            return launch_orth_psi(Ls, blk[cur] + off, blk[nxt] + off, CW(j) + (size_t)g0 * nv, psi,
-                                   d_e + (size_t)j * p.nbc * cs, na, s);
+          CK(timed(kKSpmm2, bs * (j >= 2 ? 3 : 2), [&] { return launch_spmm(Ls, kModePass2, sa, s); }));
+          const int nf = mb > 1 ? 0 : na;  // betas updated by the orthogonalisation itself
+          CK(timed(kKOrth2, bs * (3 + 2 * nf), [&] {
+            return launch_orth_psi(Ls, wblk(j), wblk(j + 1), CW(j) + (size_t)g0 * nv, psi,
+                                   d_e + (size_t)j * p.nbc * cs, nf, s);
           }));
-          const int old_prev = prv;
-          prv = cur;
-          cur = nxt;
-          nxt = old_prev >= 0 ? old_prev : 3 - prv - cur;
+          if (mb > 1 && (j - j0 + 1 == mb || j == ke - 1)) {
+            const int m = j - j0 + 1, n0 = active(j0);
+            PsiBatch wb{};
+            for (int a = 0; a < m; ++a) wb.w[a] = wblk(j0 + a + 1);
+            CK(timed(kKPsiBatch, bs * (m + 2 * n0), [&] {
+              return launch_psi_batch(Ls, wb, m, psi, d_e + (size_t)j0 * p.nbc * cs, (size_t)p.nbc * cs, n0, s);
+            }));
+            j0 = j + 1;
+          }
         }
         for (int r = 0; r < nb; ++r) {
           CK(timed(kKGram, bs, [&] { return launch_final_gram(Lgs, psi + (size_t)r * Ls.block_bytes(), partials, s); }));

@@ -1557,6 +1557,56 @@ __global__ void __launch_bounds__(kThreads) k_psi_init(Layout L, const T* __rest
   }
 }
 
+// psi_beta += sum_{a < m} W_a E_{j0+a,beta} (pass 2, m kept basis blocks): each psi
+// element is read and written once for m steps instead of once per step.
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_psi_batch(Layout L, PsiBatch wb, int m, T* psi,
+                                                        const double* e, size_t estride, int nb) {
+  constexpr int NG = VW / DS;
+  constexpr int NVG = DS * DS;
+  const int tpr = L.TPR, rpb = kThreads / tpr;
+  const int lane = threadIdx.x % tpr, rs = threadIdx.x / tpr;
+  const int slice = blockIdx.y;
+  const size_t soff = (size_t)slice * L.D * L.Bs + (size_t)lane * VW;
+  const size_t bstride = (size_t)L.D * L.B;
+  const int gs = L.groups_per_slice(), ngs = L.n_groups();
+  // this slice's E coefficients, [a][beta][group][DS*DS], as T
+  extern __shared__ __align__(16) unsigned char smem_e[];
+  T* sE = reinterpret_cast<T*>(smem_e);
+  const int per = nb * gs * NVG;
+  for (int i = threadIdx.x; i < m * per; i += blockDim.x) {
+    const int a = i / per, rem = i % per, bi = rem / (gs * NVG), r2 = rem % (gs * NVG);
+    sE[i] = (T)e[(size_t)a * estride + (size_t)bi * ngs * NVG + (size_t)slice * gs * NVG + r2];
+  }
+  __syncthreads();
+  for (int64_t s = (int64_t)blockIdx.x * rpb + rs; s < L.D; s += (int64_t)gridDim.x * rpb) {
+    T x[kPsiBatchMax][VW];
+#pragma unroll
+    for (int a = 0; a < kPsiBatchMax; ++a)
+      if (a < m) VecIO<T, VW>::ld(x[a], reinterpret_cast<const T*>(wb.w[a]) + soff + (size_t)s * L.Bs);
+    for (int bi = 0; bi < nb; ++bi) {
+      T* P = psi + bi * bstride + soff + (size_t)s * L.Bs;
+      T p[VW];
+      VecIO<T, VW>::ld_rw(p, P);
+#pragma unroll
+      for (int a = 0; a < kPsiBatchMax; ++a) {
+        if (a >= m) break;
+        const T* eb = sE + ((size_t)(a * nb + bi) * gs + (size_t)lane * NG) * NVG;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int j = 0; j < DS; ++j) {
+            T t = p[g * DS + j];
+#pragma unroll
+            for (int i = 0; i < DS; ++i) t = fma(x[a][g * DS + i], eb[g * NVG + i * DS + j], t);
+            p[g * DS + j] = t;
+          }
+      }
+      VecIO<T, VW>::st(P, p);
+    }
+  }
+}
+
 // Gram partials of one psi block. The Gram is accumulated in float64 whatever the
 // vectors' precision (eq. rho_est): a product of two float32 values is exact in float64,
 // so each fma rounds only the sum. Only the upper triangle is summed; the lower one is
@@ -2239,6 +2289,19 @@ cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const doubl
     k_orth<T, DS, VW, false><<<grid_of(L), kThreads, sm, st>>>(
         L, reinterpret_cast<const T*>(w), reinterpret_cast<T*>(z), cw, nullptr,
         reinterpret_cast<T*>(psi), e, nb);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_batch(const Layout& L, const PsiBatch& wb, int m, void* psi, const double* e,
+                             size_t estride, int nb, cudaStream_t st) {
+  if (m < 1 || m > kPsiBatchMax) return cudaErrorInvalidValue;
+  RDM_DISPATCH(L, {
+    const size_t sm = (size_t)m * nb * L.groups_per_slice() * DS * DS * sizeof(T) + 16;
+    cudaError_t ce = opt_in_smem(reinterpret_cast<const void*>(k_psi_batch<T, DS, VW>));
+    if (ce != cudaSuccess) return ce;
+    k_psi_batch<T, DS, VW><<<grid_of(L), kThreads, sm, st>>>(L, wb, m, reinterpret_cast<T*>(psi), e, estride,
+                                                             nb);
   });
   return cudaGetLastError();
 }

@@ -11,7 +11,8 @@ const char* Profiler::name(int k) {
   static const char* names[kKNumKinds] = {"init_block", "spmm_pass1", "spmm_pass2",
                                           "orth_pass1", "orth_pass2", "psi_init",
                                           "final_gram", "small",      "apply",
-                                          "packed_pass1", "dense_fT", "host_small_dense"};
+                                          "packed_pass1", "dense_fT", "psi_batch",
+                                          "host_small_dense"};
   return (k >= 0 && k < kKNumKinds) ? names[k] : "?";
 }
 

@@ -47,6 +47,7 @@ enum KernelKind {
   kKInit = 0, kKSpmm1, kKSpmm2, kKOrth1, kKOrth2, kKPsiInit, kKGram, kKSmall, kKApply,
   kKPacked,     // the packed first pass of a batch (one cooperative launch)
   kKDense,      // the small dense step on the device (bounds, Chebyshev vectors, combination)
+  kKPsiBatch,   // pass 2: psi updated from several kept basis blocks at once
   kKHostDense,  // not a kernel: host wall time of the small dense step (eigen + coefficients)
   kKNumKinds
 };

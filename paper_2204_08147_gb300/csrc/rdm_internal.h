@@ -242,6 +242,15 @@ cudaError_t launch_small_b(const Layout& L, const double* partials, const double
 // the nb betas of the chunk (psi blocks are consecutive, D*B elements apart).
 cudaError_t launch_orth_psi(const Layout& L, const void* w, void* z, const double* cw, void* psi,
                             const double* e, int nb, cudaStream_t st);
+// Pass 2 with the last m <= kPsiBatchMax blocks of the basis kept: psi_beta +=
+// sum_{a < m} W_a E_{j0+a,beta} for the first nb betas, E of step j0 + a at e + a *
+// estride; per element the same fma sequence as m single steps of launch_orth_psi.
+constexpr int kPsiBatchMax = 8;
+struct PsiBatch {
+  const void* w[kPsiBatchMax];
+};
+cudaError_t launch_psi_batch(const Layout& L, const PsiBatch& wb, int m, void* psi, const double* e,
+                             size_t estride, int nb, cudaStream_t st);
 // Pass 2 start: psi_beta = W_1 E_{1,beta}.
 cudaError_t launch_psi_init(const Layout& L, const void* w, void* psi, const double* e, int nb,
                             cudaStream_t st);
