@@ -8,6 +8,8 @@ Test infrastructure only (see ``oracle/__init__``).
 * ``TensorHamiltonian``: applies the same operator without a matrix, by acting on
   the legs of the state viewed as an N-leg tensor (leg q = site q): X flips a leg,
   Z multiplies it by (+1, -1), and Y_a Y_b = -(X_a Z_a)(X_b Z_b) because Y = i X Z.
+* ``hamiltonian_row``: one row of H from the Pauli action on a single basis vector
+  (for sampled rows of Hamiltonians too large to build or apply whole).
 
 Terms: for every pair a < b, Jx X_a X_b + Jy Y_a Y_b + Jz Z_a Z_b; for every site,
 hz Z_q + gx X_q. A pair with one site in the system (sites < N_s) and one in the
@@ -109,6 +111,42 @@ def subsystem_hamiltonian(spec, which: str) -> np.ndarray:
     for q, axis, c in site_terms(spec, which):
         acc = acc + c * _embed({sites.index(q): PAULI[axis]}, m)
     return np.asarray(acc.real.toarray())
+
+
+def hamiltonian_row(spec, state: int, part: str = "total") -> dict:
+    """Row ``state`` of H as {column: value}: the Pauli terms applied to one basis vector.
+
+    H is real symmetric, so row s equals column s, H|s>. Site q is bit N-1-q of the
+    state index (site 0 leftmost in the Kronecker order) and bit 0 is spin up:
+    Z|b> = (-1)^b |b>, X|b> = |1-b>, Y|b> = i (-1)^b |1-b>, so a pair term
+    X_a X_b flips both bits, Y_a Y_b flips both with the factor i^2 (-1)^(b_a + b_b),
+    Z_a Z_b keeps the state with (-1)^(b_a + b_b). For rows of a Hamiltonian too large
+    to build (sampled checks at full size).
+    """
+    n = spec.n_sites
+    out: dict = {}
+
+    def bit(q):
+        return (state >> (n - 1 - q)) & 1
+
+    def add(col, v):
+        out[col] = out.get(col, 0.0) + v
+
+    for a, b, axis, c in pair_terms(spec, part):
+        flip = (1 << (n - 1 - a)) | (1 << (n - 1 - b))
+        sgn = -1.0 if (bit(a) + bit(b)) % 2 else 1.0
+        if axis == "x":
+            add(state ^ flip, c)
+        elif axis == "y":
+            add(state ^ flip, -c * sgn)
+        else:
+            add(state, c * sgn)
+    for q, axis, c in site_terms(spec, part):
+        if axis == "z":
+            add(state, -c if bit(q) else c)
+        else:
+            add(state ^ (1 << (n - 1 - q)), c)
+    return out
 
 
 class TensorHamiltonian:

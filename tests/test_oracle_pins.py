@@ -470,3 +470,20 @@ def test_block_lanczos_more_accurate_than_single_at_equal_k():
         b = lanczos.Estimator(spec).run([2.0], 6, k, 3, "gauss")
         s = lanczos.Estimator(spec).run([2.0], 6, k, 3, "gauss", block=False)
         assert np.abs(b["rho"] - rho2).max() < np.abs(s["rho"] - rho2).max()
+
+
+@pytest.mark.parametrize("maker", [lambda: W.random_model(7, 2, 5), lambda: W.long_range_xxz(8, 1, 1.0, 0.5, 0.3),
+                                   lambda: W.long_range_tfim(7, 2, 1.5, 0.9, lam=0.4), lambda: W.xxz_chain(8, 1)])
+def test_hamiltonian_row_is_the_kronecker_row(maker):
+    """Every row of the single-row construction (Pauli action on one basis vector) equals
+    the row of the Kronecker-built sparse H, with no extra entries: random anisotropic
+    couplings with fields and lambda, long-range XXZ, long-range TFIM, the NN chain."""
+    spec = maker()
+    h = spin_ops.sparse_hamiltonian(spec).tocsr()
+    for s in range(1 << spec.n_sites):
+        row = spin_ops.hamiltonian_row(spec, s)
+        dense = h.getrow(s).toarray().ravel()
+        got = np.zeros_like(dense)
+        for col, v in row.items():
+            got[col] += v
+        np.testing.assert_allclose(got, dense, atol=1e-13, rtol=0)
