@@ -309,9 +309,13 @@ typedef struct {
  * separated by grid barriers; larger items run as rdm_estimate does. Each work unit of
  * that launch is one block of the plain kernels of its item, so an item's result does
  * not depend on which other items share the batch (bit-identical alone or in any mix).
- * Its launch shape (blocks per SM of the cooperative grid) is chosen by an autotuner:
- * the first batch of each size class times the candidates (1, 2, 4, 8 blocks per SM, as
- * many as fit) and the fastest is kept on the context; the shape changes no result.
+ * Its launch form is chosen by an autotuner: the cooperative grid with 1, 2, 4 or 8
+ * blocks per SM (as many as fit; grid barriers between the phases of a step), or one
+ * block per slice of each item running all its steps with block barriers only (the
+ * recurrences of a slice read nothing of other slices; no co-residency needed). The
+ * first batch of each size class times the candidates and the fastest is kept on the
+ * context; every form runs the same units with the same arithmetic, so the choice
+ * changes no result (rdm_set_packed_form restricts it).
  * Items whose workspaces do not fit the device together run in consecutive
  * sub-batches. Blocking. Returns RDM_OK when every item succeeded, else the first
  * failure (each item's own status is in items[i].status); RDM_EINVAL for a NULL
@@ -321,6 +325,11 @@ rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, int n_items);
 /* The autotuner's state on a context: size classes tuned (*n_keys) and candidate
  * launches timed so far (*tuning_runs). Either pointer may be NULL. */
 rdm_status rdm_packed_tuning(rdm_ctx* ctx, int* n_keys, uint64_t* tuning_runs);
+
+/* Launch forms rdm_estimate_batch's first pass may take: 0 (the default) any, chosen
+ * by the autotuner; 1 only the cooperative grid; 2 only one block per slice. The
+ * tuned choices of the context are cleared. RDM_EINVAL for another value. */
+rdm_status rdm_set_packed_form(rdm_ctx* ctx, int form);
 
 /* Y = H X for a caller-owned device block of n_cols columns stored state-major,
  * vector-minor (element (s, c) at s*n_cols + c), float64 (RDM_FP64) or float32

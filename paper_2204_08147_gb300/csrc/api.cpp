@@ -889,6 +889,21 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   return RDM_OK;
 }
 
+extern "C" rdm_status rdm_set_packed_form(rdm_ctx* ctx, int form) {
+  if (!ctx) {
+    set_error("rdm_set_packed_form: NULL context");
+    return RDM_EINVAL;
+  }
+  if (form < 0 || form > 2) {
+    set_error("rdm_set_packed_form: form must be 0, 1 or 2");
+    return RDM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(ctx->tuning.mu);
+  ctx->packed_form = form;
+  ctx->tuning.blocks_per_sm.clear();
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_set_device_dense(rdm_ctx* ctx, int enable) {
   if (!ctx) {
     set_error("rdm_set_device_dense: NULL context");
@@ -2064,7 +2079,7 @@ rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes
 // Bytes at the front of a batch workspace for one packed launch's descriptors (items,
 // step and prefix tables, barrier words).
 static size_t packed_meta_bytes(int n_items, int k_max) {
-  return ((sizeof(PackedItem) * (size_t)n_items + sizeof(int) * ((size_t)k_max + 2 + 2 * ((size_t)n_items + 1)) +
+  return ((sizeof(PackedItem) * (size_t)n_items + sizeof(int) * ((size_t)k_max + 2 + 3 * ((size_t)n_items + 1)) +
            64 + 255) / 256) * 256;
 }
 
@@ -2077,7 +2092,7 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
   const int n = (int)runs.size();
   const int k_max = runs[0]->plan().k;
   std::vector<PackedItem> items(n);
-  std::vector<int> pre_rows(n + 1, 0), pre_groups(n + 1, 0), active(k_max + 1, 0);
+  std::vector<int> pre_rows(n + 1, 0), pre_groups(n + 1, 0), pre_slices(n + 1, 0), active(k_max + 1, 0);
   size_t smem = 16;
   double bytes = 0.0;
   for (int i = 0; i < n; ++i) {
@@ -2085,6 +2100,7 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
     const Layout& L = items[i].L;
     pre_rows[i + 1] = pre_rows[i] + L.gridx * L.n_slices;
     pre_groups[i + 1] = pre_groups[i] + L.n_groups();
+    pre_slices[i + 1] = pre_slices[i] + L.n_slices;
     smem = std::max(smem, spmm_terms_smem(precision, items[i].sa.n_flip, items[i].sa.n_diag));
     bytes += 6.0 * (double)L.block_bytes() * items[i].k;  // SpMM 3 blocks + orth 3 blocks per step
   }
@@ -2096,12 +2112,14 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
   // host image of the descriptors, one copy
   const size_t o_items = 0, o_active = sizeof(PackedItem) * n;
   const size_t o_rows = o_active + sizeof(int) * (k_max + 1), o_groups = o_rows + sizeof(int) * (n + 1);
-  const size_t o_bar = (o_groups + sizeof(int) * (n + 1) + 15) / 16 * 16;
+  const size_t o_slices = o_groups + sizeof(int) * (n + 1);
+  const size_t o_bar = (o_slices + sizeof(int) * (n + 1) + 15) / 16 * 16;
   std::vector<char> img(o_bar);
   std::memcpy(img.data() + o_items, items.data(), sizeof(PackedItem) * n);
   std::memcpy(img.data() + o_active, active.data(), sizeof(int) * (k_max + 1));
   std::memcpy(img.data() + o_rows, pre_rows.data(), sizeof(int) * (n + 1));
   std::memcpy(img.data() + o_groups, pre_groups.data(), sizeof(int) * (n + 1));
+  std::memcpy(img.data() + o_slices, pre_slices.data(), sizeof(int) * (n + 1));
   CK(cudaMemcpyAsync(meta, img.data(), img.size(), cudaMemcpyHostToDevice, s));
   PackedPlan pp{};
   pp.items = reinterpret_cast<const PackedItem*>(meta + o_items);
@@ -2110,6 +2128,7 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
   pp.active = reinterpret_cast<const int*>(meta + o_active);
   pp.pre_rows = reinterpret_cast<const int*>(meta + o_rows);
   pp.pre_groups = reinterpret_cast<const int*>(meta + o_groups);
+  pp.pre_slices = reinterpret_cast<const int*>(meta + o_slices);
   pp.bar = reinterpret_cast<uint32_t*>(meta + o_bar);
   // the pageable host image must outlive its copy
   CK(cudaStreamSynchronize(s));
@@ -2123,10 +2142,13 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
   }
   const int units = std::max(pre_rows[n], pre_groups[n]);
   auto grid_for = [&](int bpsm) { return std::max(1, std::min(bpsm * sms, units)); };
-  auto launch = [&](int grid) -> cudaError_t {
+  // bpsm > 0: the cooperative launch on bpsm blocks per SM; kLocal: one block per slice
+  constexpr int kLocal = -1;
+  auto launch = [&](int bpsm) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(pp.bar, 0, 3 * sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = launch_pass1_packed(precision, ds, pp, grid, smem, s);
-    return e;
+    if (e != cudaSuccess) return e;
+    if (bpsm == kLocal) return launch_pass1_local(precision, ds, pp, pre_slices[n], smem, s);
+    return launch_pass1_packed(precision, ds, pp, grid_for(bpsm), smem, s);
   };
   // Autotuner: key = (precision, d_s, size class = log2 of the block-sized units of the
   // batch, in steps of 3 (a factor 8)).
@@ -2138,21 +2160,30 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
   {
     std::lock_guard<std::mutex> lk(ctx->tuning.mu);
     auto f = ctx->tuning.blocks_per_sm.find(key);
-    if (f != ctx->tuning.blocks_per_sm.end()) bpsm = std::min(f->second, max_bpsm);
+    if (f != ctx->tuning.blocks_per_sm.end()) bpsm = f->second == kLocal ? kLocal : std::min(f->second, max_bpsm);
   }
   if (bpsm == 0) {
     // Time each candidate once on this batch (the first pass is idempotent: it only
-    // reads the starting block and M_1, Cp_1), keep the fastest for the key.
+    // reads the starting block and M_1, Cp_1), keep the fastest for the key. Both
+    // launch forms run the same units with the same arithmetic: the choice does not
+    // change a result.
     std::vector<int> cand;
-    for (int c : {1, 2, 4, 8})
-      if (c <= max_bpsm && (cand.empty() || grid_for(c) > grid_for(cand.back()))) cand.push_back(c);
+    int form = 0;
+    {
+      std::lock_guard<std::mutex> lk(ctx->tuning.mu);
+      form = ctx->packed_form;
+    }
+    if (form != 2)
+      for (int c : {1, 2, 4, 8})
+        if (c <= max_bpsm && (cand.empty() || grid_for(c) > grid_for(cand.back()))) cand.push_back(c);
+    if (form != 1) cand.push_back(kLocal);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.0f;
     for (int c : cand) {
       CK(cudaEventRecord(e0, s));
-      CK(launch(grid_for(c)));
+      CK(launch(c));
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0.0f;
@@ -2169,7 +2200,7 @@ static rdm_status run_packed(rdm_ctx* ctx, cudaStream_t s, std::vector<EstimateR
     ctx->tuning.tuning_runs += cand.size();
   }
   const int ev = prof ? prof->begin(kKPacked, s, true) : -1;
-  const cudaError_t le = launch(grid_for(bpsm));
+  const cudaError_t le = launch(bpsm);
   if (prof) prof->end(kKPacked, ev, s, bytes);
   CK(le);
   uint32_t bar_err = 0;

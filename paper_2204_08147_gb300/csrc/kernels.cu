@@ -2112,6 +2112,52 @@ __global__ void __launch_bounds__(kThreads) k_pass1_packed(PackedPlan pp) {
   }
 }
 
+// The first pass of k_pass1_packed for one slice of one item per block: the recurrences
+// of a slice's bath vectors read and write nothing of other slices, so the block runs
+// every phase of every step for its slice alone -- the same row-block units and group
+// units as the packed launch, in order, with block barriers between phases.
+template <typename T, int DS, int VW>
+__global__ void __launch_bounds__(kThreads) k_pass1_local(PackedPlan pp) {
+  constexpr int NVG = DS * DS;
+  const int u = blockIdx.x;
+  const int i = packed_item_of(pp.pre_slices, pp.n_items, u);
+  const PackedItem& it = pp.items[i];
+  const int sl = u - pp.pre_slices[i];
+  const size_t bb = it.L.block_bytes(), cs = (size_t)it.L.n_groups() * NVG;
+  const int gx = it.L.gridx, gs = it.L.groups_per_slice();
+  const TermsSmem<T> terms = load_terms<T>(it.sa.flips, it.sa.n_flip, it.sa.diags, it.sa.n_diag);
+  for (int j = 1; j <= it.k; ++j) {
+    SpmmArgs a = it.sa;
+    a.w = it.blk + (size_t)(j - 1) * bb;
+    a.w_prev = j > 1 ? it.blk + (size_t)(j - 2) * bb : nullptr;
+    a.z = it.blk + (size_t)j * bb;
+    a.mz = it.coef + (size_t)j * cs;
+    a.cp = it.coef + (size_t)(it.k + 2) * cs + (size_t)j * cs;
+    for (int bx = 0; bx < gx; ++bx) {
+      spmm_block<T, DS, VW, kModePass1, true>(it.L, a, terms, bx, sl, gx);
+      __syncthreads();
+    }
+    for (int g = 0; g < gs; ++g) {
+      small_a_group<DS>(it.L, it.sa.partials, it.coef + (size_t)j * cs, it.ta + (size_t)(j - 1) * cs,
+                        it.coef + (size_t)2 * (it.k + 2) * cs + (size_t)j * cs, it.flags, sl * gs + g);
+      __syncthreads();
+    }
+    for (int bx = 0; bx < gx; ++bx) {
+      orth_block<T, DS, VW, true, true>(it.L, reinterpret_cast<const T*>(it.blk + (size_t)(j - 1) * bb),
+                                        reinterpret_cast<T*>(it.blk + (size_t)j * bb),
+                                        it.coef + (size_t)2 * (it.k + 2) * cs + (size_t)j * cs, it.sa.partials,
+                                        nullptr, nullptr, 0, bx, sl, gx);
+      __syncthreads();
+    }
+    for (int g = 0; g < gs; ++g) {
+      small_b_group<DS>(it.L, it.sa.partials, it.coef + (size_t)j * cs, it.tb + (size_t)(j - 1) * cs,
+                        it.coef + (size_t)(j + 1) * cs, it.coef + (size_t)(it.k + 2) * cs + (size_t)(j + 1) * cs,
+                        it.thr_abs_sq, it.thr_rel_sq, it.n_rec, it.flags, sl * gs + g);
+      __syncthreads();
+    }
+  }
+}
+
 inline dim3 grid_of(const Layout& L) { return dim3((unsigned)L.gridx, (unsigned)L.n_slices); }
 
 template <typename T>
@@ -2361,6 +2407,26 @@ int packed_max_blocks_per_sm(int precision, int ds, size_t smem) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess) return 0;
   return n;
+}
+
+template <typename T, int DS, int VW>
+static cudaError_t local_kernel_info(const void** fn) {
+  *fn = reinterpret_cast<const void*>(k_pass1_local<T, DS, VW>);
+  return opt_in_smem(*fn);
+}
+
+cudaError_t launch_pass1_local(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,
+                               cudaStream_t st) {
+  Layout L{};
+  L.precision = precision;
+  L.DS = ds;
+  const void* fn = nullptr;
+  cudaError_t e = cudaErrorInvalidValue;
+  RDM_DISPATCH(L, e = (local_kernel_info<T, DS, VW>(&fn)));
+  if (e != cudaSuccess) return e;
+  PackedPlan arg = pp;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, smem, st);
 }
 
 cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,

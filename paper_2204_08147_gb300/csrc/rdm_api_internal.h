@@ -84,6 +84,7 @@ struct rdm_ctx {
   bool graphs = true;  // replay repeated pass-1 configurations from CUDA graphs
   bool bath_order = true;  // rdm_build_hamiltonian reorders bath bits for the tiled SpMM
   int device_dense = 1;  // small dense step: 0 host, 1 device for grids of >= 8 betas, 2 device
+  int packed_form = 0;   // packed first pass: 0 autotuned, 1 cooperative grid only, 2 per-slice only
   rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete

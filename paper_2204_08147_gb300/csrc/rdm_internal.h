@@ -292,6 +292,7 @@ struct PackedPlan {
   const int* active;
   const int* pre_rows;
   const int* pre_groups;
+  const int* pre_slices;  // prefix sums of the items' slices (the slice-local launch)
   uint32_t* bar;
 };
 // Blocks of the packed kernel that fit one SM with `smem` dynamic bytes (0: unsupported).
@@ -299,6 +300,11 @@ int packed_max_blocks_per_sm(int precision, int ds, size_t smem);
 // Cooperative launch of the packed first pass on `grid` blocks (all co-resident).
 cudaError_t launch_pass1_packed(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,
                                 cudaStream_t st);
+// The same first pass with one block per (item, slice), pre_slices[n_items] blocks: each
+// runs all k steps of its slice's recurrences with block barriers (no grid barrier, no
+// co-residency needed); the units and their arithmetic are those of the packed launch.
+cudaError_t launch_pass1_local(int precision, int ds, const PackedPlan& pp, int grid, size_t smem,
+                               cudaStream_t st);
 // Dynamic shared memory of the untiled SpMM's term tables.
 size_t spmm_terms_smem(int precision, int n_flip, int n_diag);
 

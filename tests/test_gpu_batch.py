@@ -144,3 +144,24 @@ def test_batch_device_dense_steps_in_one_launch(lib):
             np.testing.assert_allclose(out["rho"], single["rho"], atol=tol, rtol=0)
     finally:
         ctx.close()
+
+
+def test_batch_launch_forms_are_bit_identical(lib):
+    """The packed first pass as the cooperative grid (grid barriers between phases) and
+    as one block per slice (block barriers only): the same units with the same arithmetic,
+    so every item's result is the same bit for bit; an unknown form is rejected."""
+    ctx = lib.Context(0)
+    try:
+        jobs = _jobs(lib, ctx)
+        outs = {}
+        for form in (1, 2):
+            ctx.set_packed_form(form)
+            outs[form] = ctx.estimate_batch(jobs, full=True)
+        for a, b in zip(outs[1], outs[2]):
+            for key in ("rho", "lnZ", "gram_l", "t_a", "t_b"):
+                np.testing.assert_array_equal(a[key], b[key])
+        with pytest.raises(lib.RdmError) as e:
+            ctx.set_packed_form(3)
+        assert e.value.status == lib.EINVAL
+    finally:
+        ctx.close()
