@@ -691,6 +691,7 @@ def small_chain_bench(rdm, ctx, n_solves: int = 50) -> dict:
             "us_per_solve_p50": 1e6 * float(np.percentile(lat, 50)),
             "us_per_solve_p99": 1e6 * float(np.percentile(lat, 99)),
             "launches_per_solve": sum(s["launches"] for s in stats.values()) / n_prof,
+            "kernel_us_per_solve": {k: round(1e3 * v["ms"] / n_prof, 1) for k, v in stats.items() if v["launches"]},
             "host_small_dense_us_per_solve": 1e3 * host["ms"] / n_prof if host else None,
             "packed_us_per_solve_p50": 1e6 * float(np.percentile(lat_b, 50)),
             "packed_us_per_solve_p99": 1e6 * float(np.percentile(lat_b, 99))}
