@@ -326,6 +326,15 @@ rdm_status rdm_estimate_batch(rdm_ctx* ctx, rdm_batch_item* items, int n_items);
  * launches timed so far (*tuning_runs). Either pointer may be NULL. */
 rdm_status rdm_packed_tuning(rdm_ctx* ctx, int* n_keys, uint64_t* tuning_runs);
 
+/* Which SpMM rdm_estimate's recurrences use: 0 (the default) the tiled kernel (bulk
+ * copies of 1024-state tiles into a shared-memory ring, 152 persistent blocks) when the
+ * layout allows it and the block has at least 152 tiles in all, else the plain kernel
+ * (a block per row range and slice; tiny problems leave most persistent blocks idle);
+ * 1 the tiled kernel whenever the layout allows it; 2 always the plain kernel. Results
+ * agree within rounding (float64: ~1e-15 relative). rdm_apply_hamiltonian always takes
+ * the tiled kernel where it can. RDM_EINVAL for another value. */
+rdm_status rdm_set_spmm_form(rdm_ctx* ctx, int form);
+
 /* Launch forms rdm_estimate_batch's first pass may take: 0 (the default) any, chosen
  * by the autotuner; 1 only the cooperative grid; 2 only one block per slice. The
  * tuned choices of the context are cleared. RDM_EINVAL for another value. */

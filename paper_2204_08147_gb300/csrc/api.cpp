@@ -889,6 +889,19 @@ extern "C" rdm_status rdm_build_hamiltonian(rdm_ctx* ctx, const rdm_model* model
   return RDM_OK;
 }
 
+extern "C" rdm_status rdm_set_spmm_form(rdm_ctx* ctx, int form) {
+  if (!ctx) {
+    set_error("rdm_set_spmm_form: NULL context");
+    return RDM_EINVAL;
+  }
+  if (form < 0 || form > 2) {
+    set_error("rdm_set_spmm_form: form must be 0, 1 or 2");
+    return RDM_EINVAL;
+  }
+  ctx->spmm_form = form;
+  return RDM_OK;
+}
+
 extern "C" rdm_status rdm_set_packed_form(rdm_ctx* ctx, int form) {
   if (!ctx) {
     set_error("rdm_set_packed_form: NULL context");
@@ -1443,6 +1456,9 @@ class EstimateRun {
 };
 
 constexpr size_t kPackedMaxBlock = size_t(64) << 20;
+// Estimates whose blocks have fewer 1024-state tiles (all slices together) run the plain
+// SpMM (rdm_set_spmm_form).
+constexpr int64_t kTiledMinTiles = 152;
 // Below this many betas the host's eigendecomposition path is faster than the device
 // small dense step for a single estimate (its per-beta rotations are what the device
 // step saves; its float64 multisection is latency-bound on few recurrences).
@@ -1530,14 +1546,21 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
   sa.diags = ham->d_diags;
   sa.n_diag = (int)hm.diags.size();
   sa.tiled = ham->tiled;
-  sa.tile_k = p.tk_bytes ? d_tk : nullptr;
+  {
+    // The tiled SpMM's persistent blocks walk the tiles of all slices; with fewer tiles
+    // than SMs most of them idle, and the plain kernel (a block per row range and
+    // slice) is faster.
+    const int64_t tiles = p.tk_bytes ? ((int64_t)L.n_slices << (L.n_bits - kTileBits)) : 0;
+    const int form = ham->ctx->spmm_form;
+    sa.tile_k = p.tk_bytes && (form == 1 || (form == 0 && tiles >= kTiledMinTiles)) ? d_tk : nullptr;
+  }
   sa.err = d_flags + 1;
 
   blk_b = (double)L.block_bytes();
   h2d = d2h = 0;
 
   // Once per estimate: the per-tile diagonal table and (Gaussian case) the bath vectors.
-  if (p.tk_bytes) CK(counted([&] { return launch_tile_diag(L, ham->tiled.dg, d_tk, s); }));
+  if (sa.tile_k) CK(counted([&] { return launch_tile_diag(L, ham->tiled.dg, d_tk, s); }));
   if (p.gauss) {
     CK(counted([&] {
       return launch_gauss_norms(d_b, n_v, seed, o->first_vector, d_norm + p.n_v_pad, d_norm, s, d_graw);

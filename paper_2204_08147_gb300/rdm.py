@@ -109,6 +109,7 @@ _sig("rdm_estimate_batch", C.c_int, _vp, C.POINTER(BatchItem), C.c_int)
 _sig("rdm_set_bath_order", C.c_int, _vp, C.c_int)
 _sig("rdm_set_device_dense", C.c_int, _vp, C.c_int)
 _sig("rdm_set_packed_form", C.c_int, _vp, C.c_int)
+_sig("rdm_set_spmm_form", C.c_int, _vp, C.c_int)
 _sig("rdm_bath_order", C.c_int, C.POINTER(Model), C.POINTER(C.c_int), C.POINTER(C.c_double),
      C.POINTER(C.c_double))
 _sig("rdm_packed_tuning", C.c_int, _vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64))
@@ -242,6 +243,11 @@ class Context:
         """Where the small dense step (f(T) E1 per bath vector and beta) runs: 0/False the
         host, 1/True the device for grids of >= 8 betas (default), 2 always the device."""
         _check(_lib.rdm_set_device_dense(self.h, int(mode)), "rdm_set_device_dense")
+
+    def set_spmm_form(self, form: int = 0):
+        """SpMM of the estimator: 0 tiled from 152 tiles on (default), 1 tiled whenever the
+        layout allows, 2 the plain kernel."""
+        _check(_lib.rdm_set_spmm_form(self.h, int(form)), "rdm_set_spmm_form")
 
     def set_packed_form(self, form: int = 0):
         """Launch forms of estimate_batch's packed first pass: 0 autotuned (default), 1 the

@@ -18,7 +18,11 @@ TOL32 = 1e-4
 
 @pytest.fixture(scope="module")
 def ctx(lib):
+    """A context whose estimates take the tiled SpMM wherever the layout allows it (the
+    small test problems would otherwise run the plain kernel, which the default form
+    picks below 152 tiles), so the estimator's tiled modes are checked at every size."""
     c = lib.Context(0)
+    c.set_spmm_form(1)
     yield c
     c.close()
 
@@ -808,3 +812,28 @@ def test_apply_tiled_bit_exact_hopping_pairs(ctx, lib, n, n_sys, fields, dtype):
     ham.apply(xd, yd)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(yd.double().cpu().numpy(), h @ x)
+
+
+def test_spmm_forms_agree_and_the_default_follows_the_tile_count(lib):
+    """The estimator with the tiled SpMM (form 1), the plain one (form 2) and the default
+    (form 0): the same estimate within float64 rounding; the default is the plain kernel
+    for a block of 8 tiles (the c1 chain, one tile per slice) and the tiled one for 512
+    tiles (N = 16, 8 slices), bit for bit."""
+    ctx = lib.Context(0)
+    try:
+        for spec, n_v, tiled in ((W.config_c1()["spec"], 16, False), (W.long_range_xxz(16, 1, 1.0, 1.0, 0.1), 16, True)):
+            ham = lib.Hamiltonian(ctx, spec)
+            outs = {}
+            for form in (0, 1, 2):
+                ctx.set_spmm_form(form)
+                outs[form] = ham.estimate([0.5, 1.0], n_v, 30, 7, precision="fp64", dist="rademacher", full=True)
+            np.testing.assert_allclose(outs[1]["rho"], outs[2]["rho"], atol=1e-13, rtol=0)
+            same = outs[1] if tiled else outs[2]
+            for key in ("rho", "gram_l", "t_a", "t_b"):
+                np.testing.assert_array_equal(outs[0][key], same[key])
+            ham.close()
+        with pytest.raises(lib.RdmError) as e:
+            ctx.set_spmm_form(3)
+        assert e.value.status == lib.EINVAL
+    finally:
+        ctx.close()
