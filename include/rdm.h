@@ -328,7 +328,7 @@ rdm_status rdm_packed_tuning(rdm_ctx* ctx, int* n_keys, uint64_t* tuning_runs);
 
 /* Which SpMM rdm_estimate's recurrences use: 0 (the default) the tiled kernel (bulk
  * copies of 1024-state tiles into a shared-memory ring, 152 persistent blocks) when the
- * layout allows it and the block has at least 152 tiles in all, else the plain kernel
+ * layout allows it and the block has at least 32 tiles in all, else the plain kernel
  * (a block per row range and slice; tiny problems leave most persistent blocks idle);
  * 1 the tiled kernel whenever the layout allows it; 2 always the plain kernel. Results
  * agree within rounding (float64: ~1e-15 relative). rdm_apply_hamiltonian always takes

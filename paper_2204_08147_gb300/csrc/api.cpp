@@ -1458,7 +1458,7 @@ class EstimateRun {
 constexpr size_t kPackedMaxBlock = size_t(64) << 20;
 // Estimates whose blocks have fewer 1024-state tiles (all slices together) run the plain
 // SpMM (rdm_set_spmm_form).
-constexpr int64_t kTiledMinTiles = 152;
+constexpr int64_t kTiledMinTiles = 32;
 // Below this many betas the host's eigendecomposition path is faster than the device
 // small dense step for a single estimate (its per-beta rotations are what the device
 // step saves; its float64 multisection is latency-bound on few recurrences).
@@ -1547,9 +1547,11 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
   sa.n_diag = (int)hm.diags.size();
   sa.tiled = ham->tiled;
   {
-    // The tiled SpMM's persistent blocks walk the tiles of all slices; with fewer tiles
-    // than SMs most of them idle, and the plain kernel (a block per row range and
-    // slice) is faster.
+    // The tiled SpMM's persistent blocks walk the tiles of all slices; with only a few
+    // tiles most of them idle and its fixed cost per launch (about 25 us: tables into
+    // shared memory, the first copies, the partial sums) dominates, and the plain kernel
+    // (a block per row range and slice) is faster. Measured on GB300: plain faster at
+    // 8 tiles (c1: 12 vs 31 us per launch), tiled faster from 64 tiles on.
     const int64_t tiles = p.tk_bytes ? ((int64_t)L.n_slices << (L.n_bits - kTileBits)) : 0;
     const int form = ham->ctx->spmm_form;
     sa.tile_k = p.tk_bytes && (form == 1 || (form == 0 && tiles >= kTiledMinTiles)) ? d_tk : nullptr;

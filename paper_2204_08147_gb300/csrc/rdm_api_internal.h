@@ -85,7 +85,7 @@ struct rdm_ctx {
   bool bath_order = true;  // rdm_build_hamiltonian reorders bath bits for the tiled SpMM
   int device_dense = 1;  // small dense step: 0 host, 1 device for grids of >= 8 betas, 2 device
   int packed_form = 0;   // packed first pass: 0 autotuned, 1 cooperative grid only, 2 per-slice only
-  int spmm_form = 0;     // estimator SpMM: 0 tiled from kTiledMinTiles tiles, 1 tiled, 2 untiled
+  int spmm_form = 0;     // estimator SpMM: 0 tiled from 32 tiles on, 1 tiled, 2 untiled
   rdm::PackedTuning tuning;
   rdm_ctx();
   ~rdm_ctx();  // defined where ServeState is complete

@@ -245,7 +245,7 @@ class Context:
         _check(_lib.rdm_set_device_dense(self.h, int(mode)), "rdm_set_device_dense")
 
     def set_spmm_form(self, form: int = 0):
-        """SpMM of the estimator: 0 tiled from 152 tiles on (default), 1 tiled whenever the
+        """SpMM of the estimator: 0 tiled from 32 tiles on (default), 1 tiled whenever the
         layout allows, 2 the plain kernel."""
         _check(_lib.rdm_set_spmm_form(self.h, int(form)), "rdm_set_spmm_form")
 

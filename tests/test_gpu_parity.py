@@ -20,7 +20,7 @@ TOL32 = 1e-4
 def ctx(lib):
     """A context whose estimates take the tiled SpMM wherever the layout allows it (the
     small test problems would otherwise run the plain kernel, which the default form
-    picks below 152 tiles), so the estimator's tiled modes are checked at every size."""
+    picks below 32 tiles), so the estimator's tiled modes are checked at every size."""
     c = lib.Context(0)
     c.set_spmm_form(1)
     yield c
