@@ -1553,7 +1553,7 @@ rdm_status EstimateRun::prepare(char* ws, size_t ws_bytes) {
     // (a block per row range and slice) is faster. Measured on GB300: plain faster at
     // 8 tiles (c1: 12 vs 31 us per launch), tiled faster from 64 tiles on.
     const int64_t tiles = p.tk_bytes ? ((int64_t)L.n_slices << (L.n_bits - kTileBits)) : 0;
-    const int form = ham->ctx->spmm_form;
+    const int form = ham->ctx ? ham->ctx->spmm_form : 0;  // (the serving loop's own Hamiltonians have none)
     sa.tile_k = p.tk_bytes && (form == 1 || (form == 0 && tiles >= kTiledMinTiles)) ? d_tk : nullptr;
   }
   sa.err = d_flags + 1;
