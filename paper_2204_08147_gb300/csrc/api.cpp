@@ -201,6 +201,22 @@ void order_bath_bits(HostModel* h) {
     }
     if (symmetric) return;
   }
+  // The search below depends only on the bath size and the multiset of (mask,
+  // parity-only) pairs: a structure seen before (a serving stream's chains of one length
+  // with other couplings) takes the order found then.
+  static std::mutex cache_mu;
+  static std::map<std::vector<uint64_t>, std::vector<uint8_t>> cache;  // empty: keep the order
+  std::vector<uint64_t> key{(uint64_t)nb | ((uint64_t)h->n << 8)};
+  for (size_t t = 0; t < m.size(); ++t) key.push_back((uint64_t)m[t] | ((uint64_t)po[t] << 32));
+  std::sort(key.begin() + 1, key.end());
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    auto f = cache.find(key);
+    if (f != cache.end()) {
+      if (!f->second.empty()) *h = permute_bath(*h, f->second);
+      return;
+    }
+  }
   double best = c0;
   uint64_t x = 0x9E3779B97F4A7C15ull;
   auto next = [&]() {
@@ -230,6 +246,11 @@ void order_bath_bits(HostModel* h) {
       best = c_run;
       best_order = cur;
     }
+  }
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    if (cache.size() >= 256) cache.clear();
+    cache[key] = best < c0 ? best_order : std::vector<uint8_t>{};
   }
   if (best < c0) *h = permute_bath(*h, best_order);
 }

@@ -272,3 +272,16 @@ def test_bath_order_search_skipped_for_permutation_symmetric_couplings(rdm):
         assert order == list(range(spec.n_sites)) and before == after > 0.0
     order, before, after = rdm.bath_order(W.xxz_chain(20, 1))
     assert sorted(order) == list(range(20)) and after <= before
+
+
+def test_bath_order_reused_for_a_repeated_structure(rdm):
+    """The order search depends only on the bath size and the set of (flip mask,
+    parity-only) pairs: a model with the same structure and other couplings (a serving
+    stream's chains or ladders) takes the order found before, at once."""
+    import time
+    import workloads as W
+    first = rdm.bath_order(W.spin_ladder(9, 2, numbering="leg"))
+    t = time.perf_counter()
+    again = rdm.bath_order(W.spin_ladder(9, 2, j_leg=0.6, j_rung=1.3, numbering="leg"))
+    assert time.perf_counter() - t < 0.02
+    assert again == first and first[2] < first[1]
