@@ -619,6 +619,26 @@ __device__ __forceinline__ void pair_rows(T (&y)[RPT][VW], const T* P, int x, in
   if constexpr (K >= RPT) return;
   const T c = co != (T)0 ? co : ce;
   const uint32_t want = co != (T)0 ? 1u : 0u;  // the parity with the nonzero coefficient
+  if (mh == (uint32_t)K) {
+    // one register-row bit in the mask: every pair (m, m ^ K) with m & K = 0 has its
+    // active row on the same side, so the side, its coefficients and the partner
+    // offset are chosen once
+    const bool lo = p0 == want;
+    const T cl = lo ? c : (T)0, ch = lo ? (T)0 : c;
+    const int xs = lo ? x : (x ^ (K * kStep));
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      if (m & K) continue;
+      T xp[VW];
+      VecIO<T, VW>::ld_rw(xp, P + (xs ^ (m * kStep)));
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        y[m][v] = fma(cl, xp[v], y[m][v]);
+        y[m ^ K][v] = fma(ch, xp[v], y[m ^ K][v]);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < RPT; ++m) {
     if (m & K) continue;
@@ -670,8 +690,11 @@ __device__ __forceinline__ void apply_term(T (&y)[RPT][VW], int rgoff, int rg, c
     const uint32_t mh = (mparity / (uint32_t)RG) & (uint32_t)(RPT - 1);
     const uint32_t p0 = (uint32_t)__popc((row0 + (uint32_t)rg) & mparity) & 1u;
     if (mh == 0u) {
+      // the same coefficient for all of this thread's rows; where it differs across the
+      // warp's lanes they all run the term (a zero coefficient on the others) rather
+      // than diverge, and a warp none of whose lanes has it skips the term
       const T c = p0 ? co : ce;
-      if (c != (T)0) {
+      if (__any_sync(0xffffffffu, c != (T)0)) {
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
           T xp[VW];
