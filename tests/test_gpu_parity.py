@@ -433,19 +433,22 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
     assert e.value.status == lib.ENOMEM
 
 
-@pytest.mark.parametrize("n_v,prec,dist", [(16, "fp32", "rademacher"), (14, "fp32", "gauss"), (13, "fp64", "gauss")])
-def test_slice_sweeps_when_psi_of_all_betas_fits_some_slices(ctx, lib, n_v, prec, dist):
+@pytest.mark.parametrize("n_sys,n_v,prec,dist", [(1, 16, "fp32", "rademacher"), (1, 14, "fp32", "gauss"),
+                                                 (1, 13, "fp64", "gauss"), (2, 7, "fp32", "gauss"),
+                                                 (2, 5, "fp64", "rademacher")])
+def test_slice_sweeps_when_psi_of_all_betas_fits_some_slices(ctx, lib, n_sys, n_v, prec, dist):
     """Caller workspaces from the default size down to the smallest that runs, in
     eighths of a block: where psi of every beta fits over some of the block's slices
     (32-byte rows: 4 bath vectors of d_s = 2 per float32 slice, 2 per float64 slice) but
     not over all, pass 2 sweeps over groups of slices with every beta; below that, over
     groups of betas at full width. Every size gives the stored-basis result bit for bit,
     and the slice sweeps run fewer pass-2 SpMM bytes than the beta sweeps (no recurrence
-    repeated). Also with a padded last slice (n_v = 14, 13) and Gaussian vectors (each
-    slice group reads its own rows of the generated vectors). The mode is read from the
+    repeated). Also with a padded last slice (n_v = 14, 13, 7), Gaussian vectors (each
+    slice group reads its own rows of the generated vectors) and d_s = 4 (float64: one
+    bath vector fills a row). The mode is read from the
     psi_init launches: slice sweeps write (1 + n_beta) blocks in all, beta sweeps one
     more block per extra sweep."""
-    spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
+    spec = W.long_range_xxz(13, n_sys, 1.0, 1.0, 0.1)
     ham = lib.Hamiltonian(ctx, spec)
     # more betas than slices, so that below some size psi of every beta over one slice
     # no longer fits while one beta's at full width does; the small dense step on the
@@ -454,15 +457,15 @@ def test_slice_sweeps_when_psi_of_all_betas_fits_some_slices(ctx, lib, n_v, prec
     betas = list(W.beta_grid(9, 0.1, 10.0))
     ctx.set_device_dense(0)
     try:
-        _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist)
+        _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist, 1 << n_sys)
     finally:
         ctx.set_device_dense(1)
 
 
-def _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist):
+def _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist, d_s):
     ref = ham.estimate(betas, n_v, 25, 8, precision=prec, dist=dist, full=True, passes="store")
     nbytes = ham.workspace_size(len(betas), n_v, 25, precision=prec, dist=dist)
-    per_row = 4 if prec == "fp32" else 2  # bath vectors of d_s = 2 in one 32-byte row
+    per_row = (8 if prec == "fp32" else 4) // d_s  # bath vectors in one 32-byte row
     block = (1 << 13) * (-(-n_v // per_row)) * 32  # 2^13 states x padded slices x 32 bytes
     spmm2 = {"slices": [], "betas": []}
     ws = nbytes
