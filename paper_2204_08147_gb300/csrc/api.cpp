@@ -2110,9 +2110,131 @@ rdm_status EstimateRun::finish_rest() {
   return RDM_OK;
 }
 
+// Bath vectors per shard when an estimate's vectors run in consecutive shards that each
+// keep their whole Krylov basis: the estimator is a sum over bath vectors (eq.
+// trace_est), so shards of whole slices run one after another in the same workspace,
+// each with one pass of the recurrence and the stored-basis Gram, instead of two passes
+// over all of them. Chosen when the whole basis does not fit in `avail` but a shard's
+// does (the largest such shard); 0 otherwise.
+static int store_shard_vectors(const HostModel& h, int n_beta, int n_v, int k, const rdm_opts* o, size_t avail,
+                               double beta_max, Plan* shard_plan) {
+  if (o->passes != RDM_PASSES_AUTO || o->recurrence != RDM_BLOCK) return 0;
+  const std::string saved = rdm_last_error();  // the trial plans below may fail quietly
+  rdm_opts q = *o;
+  q.passes = RDM_PASSES_STORE;
+  Plan p;
+  int n_found = 0;
+  Layout L;
+  int pad = 0;
+  if (make_plan(h, n_beta, n_v, k, &q, avail, &p, beta_max) != RDM_OK &&
+      plan_layout(h, n_v, o->precision, &L, &pad) == RDM_OK) {
+    const int vps = L.groups_per_slice();  // bath vectors per slice
+    for (int ns = L.n_slices - 1; ns >= 1 && n_found == 0; --ns) {
+      const int n_sh = ns * vps;
+      if (n_sh >= n_v) continue;
+      if (make_plan(h, n_beta, n_sh, k, &q, avail, &p, beta_max) == RDM_OK) {
+        if (shard_plan) *shard_plan = p;
+        n_found = n_sh;
+      }
+    }
+  }
+  set_error("%s", saved.c_str());
+  return n_found;
+}
+
+// The shards of store_shard_vectors, folded as the whole run: shard r's Gram sums are
+// relative to its own shift E0_r, so each is scaled by exp(-beta (E0_r - E0)) with E0
+// the smallest of them (Sec. 3.2), then normalised as eq. rho_est.
+static rdm_status estimate_shards(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes, const double* betas,
+                                  int n_beta, int n_v, int k, uint64_t seed, const rdm_opts* o, rdm_result* out,
+                                  Profiler* prof, int n_sh) {
+  const HostModel& hm = ham->model;
+  const int dso = 1 << hm.ns, nvo = dso * dso;
+  const double d_b = std::ldexp(1.0, hm.n - hm.ns);
+  std::vector<double> gram((size_t)n_beta * n_v * nvo), quad(gram.size()), e0s;
+  std::vector<int> offs;
+  rdm_opts q = *o;
+  q.passes = RDM_PASSES_STORE;
+  uint32_t flags = 0;
+  uint64_t h2d = 0, d2h = 0;
+  for (int off = 0; off < n_v; off += n_sh) {
+    const int cnt = std::min(n_sh, n_v - off);
+    q.first_vector = o->first_vector + off;
+    std::vector<double> rho((size_t)n_beta * nvo), lnz(n_beta), g((size_t)n_beta * cnt * nvo), qd(g.size());
+    rdm_result r{};
+    r.rho = rho.data();
+    r.ln_z = lnz.data();
+    r.gram_l = g.data();
+    r.quad_l = qd.data();
+    r.t_a = out->t_a ? out->t_a + (size_t)off * k * nvo : nullptr;
+    r.t_b = out->t_b ? out->t_b + (size_t)off * k * nvo : nullptr;
+    EstimateRun run(ham, s, betas, n_beta, cnt, k, seed, &q, &r, prof);
+    rdm_status st = run.prepare(ws, ws_bytes);
+    if (st == RDM_OK) st = run.pass1();
+    if (st == RDM_OK) st = run.finish();
+    if (st != RDM_OK) return st;
+    e0s.push_back(r.e0);
+    offs.push_back(off);
+    flags |= r.flags;
+    h2d += r.h2d_bytes;
+    d2h += r.d2h_bytes;
+    for (int bi = 0; bi < n_beta; ++bi)
+      for (int l = 0; l < cnt; ++l)
+        for (int v = 0; v < nvo; ++v) {
+          gram[((size_t)bi * n_v + off + l) * nvo + v] = g[((size_t)bi * cnt + l) * nvo + v];
+          quad[((size_t)bi * n_v + off + l) * nvo + v] = qd[((size_t)bi * cnt + l) * nvo + v];
+        }
+  }
+  const double e0 = *std::min_element(e0s.begin(), e0s.end());
+  for (size_t r = 0; r < offs.size(); ++r) {
+    const int cnt = std::min(n_sh, n_v - offs[r]);
+    for (int bi = 0; bi < n_beta; ++bi) {
+      const double f = std::exp(-betas[bi] * (e0s[r] - e0));
+      for (int l = 0; l < cnt; ++l)
+        for (int v = 0; v < nvo; ++v) {
+          gram[((size_t)bi * n_v + offs[r] + l) * nvo + v] *= f;
+          quad[((size_t)bi * n_v + offs[r] + l) * nvo + v] *= f;
+        }
+    }
+  }
+  auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {
+    bool ok = true;
+    for (int bi = 0; bi < n_beta; ++bi) {
+      std::vector<double> sum(nvo, 0.0);
+      for (int l = 0; l < n_v; ++l)
+        for (int v = 0; v < nvo; ++v) sum[v] += g[((size_t)bi * n_v + l) * nvo + v];
+      double tr = 0.0;
+      for (int i = 0; i < dso; ++i) tr += sum[i * dso + i];
+      ok = ok && std::isfinite(tr) && tr > 0;
+      for (int i = 0; i < dso; ++i)
+        for (int jj = 0; jj < dso; ++jj)
+          rho[(size_t)bi * nvo + i * dso + jj] = 0.5 * (sum[i * dso + jj] + sum[jj * dso + i]) / tr;
+      if (lnz) lnz[bi] = std::log(d_b * tr / n_v) - betas[bi] * e0;
+    }
+    return ok;
+  };
+  const bool gram_main = o->form == RDM_GRAM;
+  const bool ok = finish(gram_main ? gram : quad, out->rho, out->ln_z);
+  if (out->rho_other) finish(gram_main ? quad : gram, out->rho_other, nullptr);
+  if (out->gram_l) std::copy(gram.begin(), gram.end(), out->gram_l);
+  if (out->quad_l) std::copy(quad.begin(), quad.end(), out->quad_l);
+  out->e0 = e0;
+  out->flags = flags;
+  out->h2d_bytes = h2d;
+  out->d2h_bytes = d2h;
+  if (!ok) {
+    set_error("the estimated tr(sum_l G_l) is not a positive finite number (underflow or breakdown)");
+    return RDM_ENUMERIC;
+  }
+  return RDM_OK;
+}
+
 rdm_status estimate_impl(rdm_ham* ham, cudaStream_t s, char* ws, size_t ws_bytes,
                          const double* betas, int n_beta, int n_v, int k, uint64_t seed,
                          const rdm_opts* o, rdm_result* out, Profiler* prof) {
+  const int n_sh =
+      store_shard_vectors(ham->model, n_beta, n_v, k, o, ws_bytes, max_beta(betas, n_beta), nullptr);
+  if (n_sh > 0) return estimate_shards(ham, s, ws, ws_bytes, betas, n_beta, n_v, k, seed, o, out, prof, n_sh);
   EstimateRun run(ham, s, betas, n_beta, n_v, k, seed, o, out, prof);
   rdm_status st = run.prepare(ws, ws_bytes);
   if (st == RDM_OK) st = run.pass1();
@@ -2533,8 +2655,13 @@ extern "C" rdm_status rdm_estimate(rdm_ham* ham, const double* betas, int n_beta
   CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t usable = (size_t)(0.85 * (double)(free_b + ctx->own_bytes));
   rdm_status pst = RDM_OK;
-  const size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst, max_beta(betas, n_beta));
+  size_t need = estimate_bytes(ham->model, n_beta, n_v, k, opts, usable, &pst, max_beta(betas, n_beta));
   if (need == 0) return pst != RDM_OK ? pst : RDM_ENOMEM;  // make_plan set the message
+  {
+    Plan sp;  // shards that keep their basis take the workspace of one shard's plan
+    if (store_shard_vectors(ham->model, n_beta, n_v, k, opts, usable, max_beta(betas, n_beta), &sp) > 0)
+      need = plan_bytes(sp);
+  }
   const rdm_status gst = grow_own_workspace(ctx, need, usable);
   if (gst != RDM_OK) return gst;
   return estimate_impl(ham, ctx->stream, ctx->own_ws, ctx->own_bytes, betas, n_beta, n_v, k, seed,

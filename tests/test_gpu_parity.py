@@ -419,7 +419,7 @@ def test_beta_chunks_in_a_small_workspace(ctx, lib):
     nbytes = ham.workspace_size(len(betas), 16, 25, precision="fp32", dist="rademacher")
     ctx.attach_workspace(nbytes)
     try:
-        got = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True)
+        got = ham.estimate(betas, 16, 25, 8, precision="fp32", dist="rademacher", full=True, passes="recompute")
     finally:
         ctx.detach_workspace()
     for key in ("rho", "lnZ", "gram_l"):
@@ -473,7 +473,7 @@ def _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist, d_s):
         ctx.attach_workspace(ws)
         try:
             ctx.profile(True)
-            got = ham.estimate(betas, n_v, 25, 8, precision=prec, dist=dist, full=True)
+            got = ham.estimate(betas, n_v, 25, 8, precision=prec, dist=dist, full=True, passes="recompute")
             st = ctx.profile_stats()
             ctx.profile(False)
         except lib.RdmError as e:
@@ -492,6 +492,45 @@ def _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist, d_s):
         ws -= block // 8
     assert spmm2["slices"] and spmm2["betas"]
     assert max(spmm2["slices"]) < min(spmm2["betas"])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-12)])
+def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
+    """passes="auto" with a caller workspace too small for the whole Krylov basis but
+    large enough for that of a group of slices: the bath vectors run in consecutive
+    shards that each keep their basis (one pass of the recurrence, no pass-2 launch),
+    folded on the host with each shard's shift. Against the stored-basis run of all
+    vectors: the same T_l and E0 (the recurrences of a slice do not depend on the others;
+    the SpMM's partial sums may group differently), rho* and the per-vector Grams within
+    rounding (the shards' shifts differ), and fewer SpMM launches than the recompute
+    mode in the same workspace."""
+    spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
+    ham = lib.Hamiltonian(ctx, spec)
+    betas = list(W.beta_grid(5, 0.1, 10.0))
+    n_v, k = 16, 25
+    ref = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", full=True, passes="store")
+    store_bytes = ham.workspace_size(len(betas), n_v, k, precision=prec, dist="gauss", passes="store")
+    launches = {}
+    for passes in ("auto", "recompute"):
+        ctx.attach_workspace(int(store_bytes * 0.6))
+        try:
+            ctx.profile(True)
+            got = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", full=True, passes=passes)
+            st = ctx.profile_stats()
+            ctx.profile(False)
+        finally:
+            ctx.detach_workspace()
+        launches[passes] = st["spmm_pass1"]["launches"] + st.get("spmm_pass2", {"launches": 0})["launches"]
+        if passes == "auto":
+            assert st.get("psi_init", {"launches": 0})["launches"] == 0
+            scale = np.abs(ref["t_a"]).max()
+            np.testing.assert_allclose(got["t_a"], ref["t_a"], atol=tol * scale, rtol=0)
+            np.testing.assert_allclose(got["t_b"], ref["t_b"], atol=tol * scale, rtol=0)
+            assert abs(got["e0"] - ref["e0"]) <= tol * scale
+        np.testing.assert_allclose(got["rho"], ref["rho"], atol=tol, rtol=0)
+        np.testing.assert_allclose(got["lnZ"], ref["lnZ"], atol=10 * tol, rtol=0)
+        np.testing.assert_allclose(got["gram_l"], ref["gram_l"], atol=tol * np.abs(ref["gram_l"]).max(), rtol=0)
+    assert launches["auto"] < launches["recompute"]
 
 
 # ---------------------------------------------------------------- bath-vector shards
