@@ -502,7 +502,7 @@ def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
     folded on the host with each shard's shift. Against the stored-basis run of all
     vectors: the same T_l and E0 (the recurrences of a slice do not depend on the others;
     the SpMM's partial sums may group differently), rho* and the per-vector Grams within
-    rounding (the shards' shifts differ), and fewer SpMM launches than the recompute
+    rounding (the shards' shifts differ), and about half the SpMM bytes of the recompute
     mode in the same workspace."""
     spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
     ham = lib.Hamiltonian(ctx, spec)
@@ -520,7 +520,7 @@ def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
             ctx.profile(False)
         finally:
             ctx.detach_workspace()
-        launches[passes] = st["spmm_pass1"]["launches"] + st.get("spmm_pass2", {"launches": 0})["launches"]
+        launches[passes] = st["spmm_pass1"]["bytes"] + st.get("spmm_pass2", {"bytes": 0.0})["bytes"]
         if passes == "auto":
             assert st.get("psi_init", {"launches": 0})["launches"] == 0
             scale = np.abs(ref["t_a"]).max()
@@ -530,7 +530,7 @@ def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
         np.testing.assert_allclose(got["rho"], ref["rho"], atol=tol, rtol=0)
         np.testing.assert_allclose(got["lnZ"], ref["lnZ"], atol=10 * tol, rtol=0)
         np.testing.assert_allclose(got["gram_l"], ref["gram_l"], atol=tol * np.abs(ref["gram_l"]).max(), rtol=0)
-    assert launches["auto"] < launches["recompute"]
+    assert launches["auto"] < 0.6 * launches["recompute"]
 
 
 # ---------------------------------------------------------------- bath-vector shards
