@@ -99,11 +99,16 @@ typedef struct {
 
 /* How the Gram form obtains Q_1..Q_k (Algorithm 1 returns them all):
  *   RDM_PASSES_AUTO:      store them if k+1 Krylov blocks fit the device memory the
- *                         call may use, else recompute;
+ *                         call may use; else, if those of a group of slices (bath
+ *                         vectors) fit, rdm_estimate runs the bath vectors in consecutive
+ *                         shards that each store their basis (one pass of the recurrence)
+ *                         and folds them on the host with each shard's shift E0_r, as a
+ *                         run split over GPUs is folded (results agree with one run to
+ *                         rounding); else recompute;
  *   RDM_PASSES_STORE:     keep every block of pass 1 (k+1 blocks of D x B);
  *   RDM_PASSES_RECOMPUTE: keep 3 blocks and run the recurrence a second time with
  *                         the stored coefficients (bit-identical blocks).
- * Both give bit-identical results. */
+ * STORE and RECOMPUTE give bit-identical results. */
 enum { RDM_PASSES_AUTO = 0, RDM_PASSES_STORE = 1, RDM_PASSES_RECOMPUTE = 2 };
 
 /* The Lanczos recurrences per bath vector:
