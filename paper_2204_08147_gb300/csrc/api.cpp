@@ -637,7 +637,7 @@ static PlanSizes plan_sizes(const Plan& p) {
   // (the packed first pass runs the untiled grid on a tiled layout: room for both)
   const size_t prec = (size_t)L.n_slices * std::max(L.gridx, untiled_gridx(L)) * L.groups_per_slice() * L.DS * L.DS;
   const size_t pview = (size_t)G.n_slices * G.gridx * G.groups_per_slice() * G.DS * G.DS;
-  return PlanSizes{std::max(prec, pview) * 4, (size_t)p.k * p.nbc * std::max(rec, view),
+  return PlanSizes{std::max(prec, pview) * 8, (size_t)p.k * p.nbc * std::max(rec, view),
                    (size_t)p.nbc * std::max(rec, view)};
 }
 

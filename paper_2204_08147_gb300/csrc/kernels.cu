@@ -1679,6 +1679,9 @@ __global__ void __launch_bounds__(kThreads) k_final_gram(Layout L, const T* __re
 // the partial sums of psi_beta^T psi_beta, for up to kGramBetas betas per launch.
 // W_j = W1 + (j-1) * D * B elements; e: [j][beta (stride nbs)][group][DS*DS].
 constexpr int kGramBetas = 4;
+// With d_s <= 2 a beta's psi and Gram partials take few registers: twice the betas per
+// launch, half the passes over the stored basis.
+constexpr int kGramBetasWide = 8;
 
 template <typename T, int DS>
 struct RowVec;  // DS consecutive coefficients as one shared-memory load
@@ -2479,6 +2482,15 @@ cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const dou
     if (ce == cudaSuccess)
       ce = opt_in_smem(reinterpret_cast<const void*>(k_gram_stored<T, DS, VW, kGramBetas>));
     if (ce != cudaSuccess) return ce;
+    if constexpr (DS <= 2) {
+      if (nb > kGramBetas) {
+        ce = opt_in_smem(reinterpret_cast<const void*>(k_gram_stored<T, DS, VW, kGramBetasWide>));
+        if (ce != cudaSuccess) return ce;
+        k_gram_stored<T, DS, VW, kGramBetasWide><<<grid_of(L), kThreads, sm, st>>>(
+            L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
+        return cudaGetLastError();
+      }
+    }
     if (nb == 1)
       k_gram_stored<T, DS, VW, 1><<<grid_of(L), kThreads, sm, st>>>(
           L, reinterpret_cast<const T*>(w1), k, e, nbs, b0, nb, partials, pstride);
@@ -2495,7 +2507,7 @@ cudaError_t launch_gram_stored(const Layout& L, const void* w1, int k, const dou
 int gram_stored_max_betas(const Layout& L, int k) {
   const size_t per = (size_t)k * L.groups_per_slice() * L.DS * L.DS * L.elem;
   int nb = (int)((160 * 1024) / (per ? per : 1));
-  return std::max(0, std::min(nb, kGramBetas));
+  return std::max(0, std::min(nb, L.DS <= 2 ? kGramBetasWide : kGramBetas));
 }
 
 cudaError_t launch_reduce_gram(const Layout& L, const double* partials, double* gram,
