@@ -625,7 +625,8 @@ struct Plan {
 };
 
 // Float64 counts of the arrays whose size depends on the grouping: reduction partials
-// (4 slots), the E coefficients of a beta chunk and the Gram results of a chunk, each
+// (8 slots: one per beta of a stored-basis Gram launch), the E coefficients of a beta
+// chunk and the Gram results of a chunk, each
 // large enough for the recurrences' layout and for the Gram view.
 struct PlanSizes {
   size_t partials, e, gram;
