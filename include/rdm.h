@@ -167,8 +167,11 @@ void rdm_destroy(rdm_ctx* ctx);
  * more, kept between calls, freed by rdm_destroy). */
 rdm_status rdm_set_workspace(rdm_ctx* ctx, void* device_ptr, size_t bytes);
 
-/* Bytes of device scratch rdm_estimate needs for these sizes (3 Krylov blocks,
- * the psi accumulators of one beta chunk, reduction partials, coefficients). */
+/* Bytes of device scratch rdm_estimate needs for these sizes: with opts->passes
+ * RDM_PASSES_STORE all k+1 Krylov blocks; otherwise the smallest recompute plan (3
+ * Krylov blocks, the psi accumulators of one beta, reduction partials, coefficients).
+ * A larger workspace lets rdm_estimate take more betas per pass-2 sweep, sweep slice
+ * groups with every beta, keep the basis of one-pass shards or the whole basis. */
 rdm_status rdm_workspace_size(const rdm_ham* ham, int n_beta, int n_v, int k,
                               const rdm_opts* opts, size_t* bytes);
 
