@@ -265,7 +265,10 @@ rdm_status rdm_system_hamiltonian(const rdm_model* model, double* hs_out);
  * tiled SpMM copies per tile (flip masks are grouped by their bits above the tile's
  * 10 in-tile bits; sites coupled to many others belong in the tile), found by a
  * deterministic local search over transpositions of bath sites from the coupling graph
- * (the ladder of Sec. 5.2 goes from 15 to 11-12 partner tiles). Only the device layout
+ * (the ladder of Sec. 5.2 numbered leg by leg goes from 13.5 to 8.5 partner tiles),
+ * skipped when no order can differ (the set of flip masks maps onto itself under every
+ * swap of neighbouring bath sites: a field on every site, all-to-all couplings) and
+ * kept per structure for models that repeat one with other couplings. Only the device layout
  * changes: rdm_estimate draws the bath vectors in the caller's bath order, so results
  * equal those of the caller's order up to rounding, and rdm_apply_hamiltonian /
  * rdm_starting_block keep the caller's state order. The paper has no counterpart.
