@@ -444,11 +444,15 @@ rdm_status rdm_function_of_t_batch(int n_mat, int n, int p, const double* t, int
 rdm_status rdm_symmetric_eig(int n, const double* a, double* w, double* v);
 
 /* ---------------------------------------------------------------- serving
- * A request loop on the context: requests are queued, admitted while their
- * device footprint fits the context's budget, and run concurrently (each on its
- * own stream), so requests that arrive while others run overlap with them. The
- * result arrays of a request must stay valid until rdm_poll/rdm_wait reports
- * completion. */
+ * A request loop on the context (continuous batching): requests are queued, admitted
+ * while their device footprint fits the context's budget, and run concurrently by up
+ * to max_inflight workers, each on its own stream, so requests that arrive while
+ * others run overlap with them. A request small enough for the packed first pass
+ * (its basis stored, at most a quarter of the budget) joins the other queued such
+ * requests a worker takes along, and they run as one rdm_estimate_batch (first passes
+ * in one launch); others run as rdm_estimate. Each request's result is the same served
+ * alone or in any mix (bit for bit for the packed requests). The result arrays of a
+ * request must stay valid until rdm_poll/rdm_wait reports completion. */
 
 /* hbm_budget_bytes: device bytes the loop may hold for requests at once;
  * max_inflight: how many requests may run concurrently (>= 1). */
