@@ -1813,6 +1813,28 @@ rdm_status EstimateRun::finish() {
   return finish_rest();
 }
 
+// eq. rho_est and ln Z_t from per-vector Grams g[beta][l][i][j] relative to the shift
+// e0: rho*(beta) = the symmetric part of sum_l G_l over its trace, ln Z_t = ln(d_b tr /
+// n_v) - beta e0. False when a trace is not a positive finite number.
+static bool normalise_grams(const std::vector<double>& g, int n_beta, int n_v, int dso, double d_b,
+                            const double* betas, double e0, double* rho, double* lnz) {
+  const int nvo = dso * dso;
+  bool ok = true;
+  for (int bi = 0; bi < n_beta; ++bi) {
+    std::vector<double> sum(nvo, 0.0);
+    for (int l = 0; l < n_v; ++l)
+      for (int v = 0; v < nvo; ++v) sum[v] += g[((size_t)bi * n_v + l) * nvo + v];
+    double tr = 0.0;
+    for (int i = 0; i < dso; ++i) tr += sum[i * dso + i];
+    ok = ok && std::isfinite(tr) && tr > 0;
+    for (int i = 0; i < dso; ++i)
+      for (int jj = 0; jj < dso; ++jj)
+        rho[(size_t)bi * nvo + i * dso + jj] = 0.5 * (sum[i * dso + jj] + sum[jj * dso + i]) / tr;
+    if (lnz) lnz[bi] = std::log(d_b * tr / n_v) - betas[bi] * e0;
+  }
+  return ok;
+}
+
 rdm_status EstimateRun::finish_rest() {
   rdm_status st = RDM_OK;
   const int n = k * ds;
@@ -2065,20 +2087,7 @@ rdm_status EstimateRun::finish_rest() {
 
   // ---- normalisation (eq. rho_est) and ln Z_t.
   auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {
-    bool ok = true;
-    for (int bi = 0; bi < n_beta; ++bi) {
-      std::vector<double> sum(nvo, 0.0);
-      for (int l = 0; l < n_v; ++l)
-        for (int v = 0; v < nvo; ++v) sum[v] += g[((size_t)bi * n_v + l) * nvo + v];
-      double tr = 0.0;
-      for (int i = 0; i < dso; ++i) tr += sum[i * dso + i];
-      ok = ok && std::isfinite(tr) && tr > 0;
-      for (int i = 0; i < dso; ++i)
-        for (int jj = 0; jj < dso; ++jj)
-          rho[(size_t)bi * nvo + i * dso + jj] = 0.5 * (sum[i * dso + jj] + sum[jj * dso + i]) / tr;
-      if (lnz) lnz[bi] = std::log((double)d_b * tr / n_v) - betas[bi] * e0;
-    }
-    return ok;
+    return normalise_grams(g, n_beta, n_v, dso, (double)d_b, betas, e0, rho, lnz);
   };
   const bool gram_main = o->form == RDM_GRAM;
   bool ok = finish(gram_main ? gram : quad, out->rho, out->ln_z);
@@ -2199,20 +2208,7 @@ static rdm_status estimate_shards(rdm_ham* ham, cudaStream_t s, char* ws, size_t
     }
   }
   auto finish = [&](const std::vector<double>& g, double* rho, double* lnz) -> bool {
-    bool ok = true;
-    for (int bi = 0; bi < n_beta; ++bi) {
-      std::vector<double> sum(nvo, 0.0);
-      for (int l = 0; l < n_v; ++l)
-        for (int v = 0; v < nvo; ++v) sum[v] += g[((size_t)bi * n_v + l) * nvo + v];
-      double tr = 0.0;
-      for (int i = 0; i < dso; ++i) tr += sum[i * dso + i];
-      ok = ok && std::isfinite(tr) && tr > 0;
-      for (int i = 0; i < dso; ++i)
-        for (int jj = 0; jj < dso; ++jj)
-          rho[(size_t)bi * nvo + i * dso + jj] = 0.5 * (sum[i * dso + jj] + sum[jj * dso + i]) / tr;
-      if (lnz) lnz[bi] = std::log(d_b * tr / n_v) - betas[bi] * e0;
-    }
-    return ok;
+    return normalise_grams(g, n_beta, n_v, dso, d_b, betas, e0, rho, lnz);
   };
   const bool gram_main = o->form == RDM_GRAM;
   const bool ok = finish(gram_main ? gram : quad, out->rho, out->ln_z);
