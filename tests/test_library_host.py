@@ -285,3 +285,11 @@ def test_bath_order_reused_for_a_repeated_structure(rdm):
     again = rdm.bath_order(W.spin_ladder(9, 2, j_leg=0.6, j_rung=1.3, numbering="leg"))
     assert time.perf_counter() - t < 0.02
     assert again == first and first[2] < first[1]
+
+
+def test_context_knobs_reject_a_null_context(rdm):
+    """The launch-form and mode setters validate their context before touching it."""
+    for name in ("rdm_set_spmm_form", "rdm_set_packed_form", "rdm_set_device_dense", "rdm_set_bath_order",
+                 "rdm_set_graphs"):
+        st = getattr(rdm._lib, name)(None, 0)
+        assert st == rdm.EINVAL, name
