@@ -494,8 +494,9 @@ def _slice_sweep_scan(ctx, lib, ham, betas, n_v, prec, dist, d_s):
     assert max(spmm2["slices"]) < min(spmm2["betas"])
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-12)])
-def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
+@pytest.mark.parametrize("prec,tol,n_v,form", [("fp32", 2e-6, 16, "gram"), ("fp64", 1e-12, 16, "gram"),
+                                               ("fp32", 2e-6, 14, "quadrature")])
+def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol, n_v, form):
     """passes="auto" with a caller workspace too small for the whole Krylov basis but
     large enough for that of a group of slices: the bath vectors run in consecutive
     shards that each keep their basis (one pass of the recurrence, no pass-2 launch),
@@ -503,19 +504,21 @@ def test_one_pass_shards_when_a_shards_basis_fits(ctx, lib, prec, tol):
     vectors: the same T_l and E0 (the recurrences of a slice do not depend on the others;
     the SpMM's partial sums may group differently), rho* and the per-vector Grams within
     rounding (the shards' shifts differ), and about half the SpMM bytes of the recompute
-    mode in the same workspace."""
+    mode in the same workspace. Also with a padded last shard (n_v = 14) and the
+    quadrature form as the reported one."""
     spec = W.long_range_xxz(13, 1, 1.0, 1.0, 0.1)
     ham = lib.Hamiltonian(ctx, spec)
     betas = list(W.beta_grid(5, 0.1, 10.0))
-    n_v, k = 16, 25
-    ref = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", full=True, passes="store")
+    k = 25
+    ref = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", form=form, full=True, passes="store")
     store_bytes = ham.workspace_size(len(betas), n_v, k, precision=prec, dist="gauss", passes="store")
     launches = {}
     for passes in ("auto", "recompute"):
         ctx.attach_workspace(int(store_bytes * 0.6))
         try:
             ctx.profile(True)
-            got = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", full=True, passes=passes)
+            got = ham.estimate(betas, n_v, k, 8, precision=prec, dist="gauss", form=form, full=True,
+                               passes=passes)
             st = ctx.profile_stats()
             ctx.profile(False)
         finally:
